@@ -1,0 +1,382 @@
+"""Seeded synthetic Sim(3) essential graphs (the only input source shared by the
+CUDA path, the oracle, the tests and the benchmark).
+
+The paper evaluates loop closing on EuRoC and TUM-VI sequences (Sec. V-A) and
+optimises the essential graph after a loop is accepted (Sec. III-B, Sec. IV-F),
+but prints neither graph sizes nor graph statistics.  These generators stand in
+for those essential graphs with trajectories of the same shape:
+
+* ``circle``     200 keyframes on a 10 m circle, one loop (last -> first);
+* ``figure8``    drone-flight-shaped (EuRoC-like) 3-D figure-8, two laps;
+* ``corridor``   handheld-sequence-shaped (TUM-VI-like) random walk along
+                 corridors of a 50 m x 50 m grid with many revisits.
+
+Conventions (shared with the solver, stated here so the module stands alone):
+a pose S = (q, t, s) maps world points to the camera frame, x_c = s R(q) x_w + t,
+stored as 8 float64 values (qx, qy, qz, qw, tx, ty, tz, s).  An edge (i, j)
+carries the measured relative transform Z_ij ~ S_j S_i^-1.
+
+Drift model: the initial estimate is the chain of ground-truth relative steps,
+each left-multiplied by a noise transform N = (q_n, t_n, s_n) with
+q_n = normalise([n_rot / 2, 1]), t_n = n_trans, s_n = exp(n_ls) and
+n ~ Normal(0, diag(sig_rot^2 I3, sig_trans^2 I3, sig_ls^2)).  Spanning-tree and
+covisibility measurements come from the drifted estimate (they are consistent
+with it, as after ORB-SLAM-style loop correction), loop measurements from the
+ground truth; optional i.i.d. measurement noise of the same form perturbs every
+edge.
+
+This module holds problem construction only (quaternion products to compose
+poses).  It contains none of the solver's arithmetic: no exp/log maps, no
+residuals, no Jacobians, no normal equations.  Randomness comes only from
+``numpy.random.Generator(PCG64(seed))``.
+"""
+from __future__ import annotations
+
+import dataclasses
+import numpy as np
+
+__all__ = [
+    "PoseGraph", "make_graph", "make_config", "make_batch", "CONFIGS",
+    "compose", "inverse", "quat_mul", "quat_rotate",
+]
+
+
+# --------------------------------------------------------------------------
+# Plain quaternion / similarity-transform composition (problem construction).
+# --------------------------------------------------------------------------
+def quat_mul(a, b):
+    """Hamilton product of (..., 4) quaternions stored (x, y, z, w)."""
+    ax, ay, az, aw = a[..., 0], a[..., 1], a[..., 2], a[..., 3]
+    bx, by, bz, bw = b[..., 0], b[..., 1], b[..., 2], b[..., 3]
+    return np.stack([
+        aw * bx + ax * bw + ay * bz - az * by,
+        aw * by - ax * bz + ay * bw + az * bx,
+        aw * bz + ax * by - ay * bx + az * bw,
+        aw * bw - ax * bx - ay * by - az * bz,
+    ], axis=-1)
+
+
+def quat_rotate(q, v):
+    """Rotate (..., 3) vectors by unit quaternions (..., 4)."""
+    u = q[..., :3]
+    w = q[..., 3:4]
+    t = 2.0 * np.cross(u, v)
+    return v + w * t + np.cross(u, t)
+
+
+def compose(a, b):
+    """a * b for poses stored (..., 8): (R_a R_b, s_a R_a t_b + t_a, s_a s_b)."""
+    q = quat_mul(a[..., 0:4], b[..., 0:4])
+    t = a[..., 7:8] * quat_rotate(a[..., 0:4], b[..., 4:7]) + a[..., 4:7]
+    s = a[..., 7:8] * b[..., 7:8]
+    return np.concatenate([q, t, s], axis=-1)
+
+
+def inverse(a):
+    """a^-1 = (R^T, -R^T t / s, 1 / s) for poses stored (..., 8)."""
+    qi = a[..., 0:4] * np.array([-1.0, -1.0, -1.0, 1.0])
+    t = -quat_rotate(qi, a[..., 4:7]) / a[..., 7:8]
+    return np.concatenate([qi, t, 1.0 / a[..., 7:8]], axis=-1)
+
+
+def _prefix_compose(steps, first):
+    """P_0 = first, P_k = steps[k] * P_{k-1} for k >= 1 (steps[0] unused).
+
+    Evaluated as a Hillis-Steele scan of the associative product so that
+    large graphs are built with O(log N) vectorised passes."""
+    n = steps.shape[0]
+    acc = steps.copy()
+    acc[0] = first
+    shift = 1
+    while shift < n:
+        nxt = acc.copy()
+        nxt[shift:] = compose(acc[shift:], acc[:-shift])
+        acc = nxt
+        shift *= 2
+    q = acc[:, 0:4]
+    acc[:, 0:4] = q / np.linalg.norm(q, axis=1, keepdims=True)
+    return acc
+
+
+def _noise(rng, n, sig_rot, sig_trans, sig_ls):
+    """n noise transforms (q_n, t_n, s_n) as documented in the module header."""
+    nr = rng.normal(0.0, sig_rot, size=(n, 3))
+    nt = rng.normal(0.0, sig_trans, size=(n, 3))
+    ns = rng.normal(0.0, sig_ls, size=(n, 1))
+    q = np.concatenate([0.5 * nr, np.ones((n, 1))], axis=1)
+    q /= np.linalg.norm(q, axis=1, keepdims=True)
+    return np.concatenate([q, nt, np.exp(ns)], axis=1)
+
+
+def _rotmat_to_quat(R):
+    """Rotation matrices (..., 3, 3) -> unit quaternions (x, y, z, w)."""
+    R = np.asarray(R, dtype=np.float64)
+    m00, m11, m22 = R[..., 0, 0], R[..., 1, 1], R[..., 2, 2]
+    tr = m00 + m11 + m22
+    out = np.empty(R.shape[:-2] + (4,))
+    cand = np.stack([tr, m00, m11, m22], axis=-1)
+    k = np.argmax(cand, axis=-1)
+    for case in range(4):
+        sel = k == case
+        if not np.any(sel):
+            continue
+        Rs = R[sel]
+        if case == 0:
+            r = np.sqrt(1.0 + tr[sel]) * 2.0
+            q = np.stack([(Rs[:, 2, 1] - Rs[:, 1, 2]) / r, (Rs[:, 0, 2] - Rs[:, 2, 0]) / r,
+                          (Rs[:, 1, 0] - Rs[:, 0, 1]) / r, 0.25 * r], axis=-1)
+        elif case == 1:
+            r = np.sqrt(1.0 + Rs[:, 0, 0] - Rs[:, 1, 1] - Rs[:, 2, 2]) * 2.0
+            q = np.stack([0.25 * r, (Rs[:, 0, 1] + Rs[:, 1, 0]) / r,
+                          (Rs[:, 0, 2] + Rs[:, 2, 0]) / r, (Rs[:, 2, 1] - Rs[:, 1, 2]) / r], axis=-1)
+        elif case == 2:
+            r = np.sqrt(1.0 + Rs[:, 1, 1] - Rs[:, 0, 0] - Rs[:, 2, 2]) * 2.0
+            q = np.stack([(Rs[:, 0, 1] + Rs[:, 1, 0]) / r, 0.25 * r,
+                          (Rs[:, 1, 2] + Rs[:, 2, 1]) / r, (Rs[:, 0, 2] - Rs[:, 2, 0]) / r], axis=-1)
+        else:
+            r = np.sqrt(1.0 + Rs[:, 2, 2] - Rs[:, 0, 0] - Rs[:, 1, 1]) * 2.0
+            q = np.stack([(Rs[:, 0, 2] + Rs[:, 2, 0]) / r, (Rs[:, 1, 2] + Rs[:, 2, 1]) / r,
+                          0.25 * r, (Rs[:, 1, 0] - Rs[:, 0, 1]) / r], axis=-1)
+        out[sel] = q
+    out *= np.where(out[..., 3:4] < 0, -1.0, 1.0)
+    return out / np.linalg.norm(out, axis=-1, keepdims=True)
+
+
+def _poses_from_path(centres, forward):
+    """World->camera poses (scale 1) of cameras at ``centres`` looking along
+    ``forward`` with world +z as up."""
+    f = forward / np.linalg.norm(forward, axis=1, keepdims=True)
+    up = np.array([0.0, 0.0, 1.0])
+    x = np.cross(f, up)
+    bad = np.linalg.norm(x, axis=1) < 1e-6
+    x[bad] = np.array([1.0, 0.0, 0.0])
+    x /= np.linalg.norm(x, axis=1, keepdims=True)
+    y = np.cross(f, x)
+    R_wc = np.stack([x, y, f], axis=-1)          # columns: camera axes in world
+    R_cw = np.transpose(R_wc, (0, 2, 1))
+    q = _rotmat_to_quat(R_cw)
+    t = -np.einsum("nij,nj->ni", R_cw, centres)
+    return np.concatenate([q, t, np.ones((len(centres), 1))], axis=1)
+
+
+# --------------------------------------------------------------------------
+# Trajectories
+# --------------------------------------------------------------------------
+def _circle(n, radius=10.0):
+    phi = np.linspace(0.0, 2.0 * np.pi, n, endpoint=False)
+    c = np.stack([radius * np.cos(phi), radius * np.sin(phi), np.zeros(n)], axis=1)
+    f = np.stack([-np.sin(phi), np.cos(phi), np.zeros(n)], axis=1)
+    return c, f
+
+
+def _figure8(n, laps=2.0, half_width=10.0, height=1.5):
+    phi = np.linspace(0.0, 2.0 * np.pi * laps, n, endpoint=False)
+    c = np.stack([half_width * np.sin(phi), half_width * np.sin(phi) * np.cos(phi),
+                  1.0 + height * np.sin(2.0 * phi)], axis=1)
+    f = np.stack([half_width * np.cos(phi), half_width * np.cos(2.0 * phi),
+                  2.0 * height * np.cos(2.0 * phi)], axis=1)
+    return c, f
+
+
+def _corridor(n, rng, size=50.0, spacing=5.0, step=1.0):
+    """Random walk at ``step`` metres per keyframe along the lines of a grid
+    of corridors ``spacing`` apart, turning at random at grid nodes (no
+    U-turns unless at a wall)."""
+    per_seg = int(round(spacing / step))
+    nodes = int(round(size / spacing))
+    dirs = np.array([[1, 0], [0, 1], [-1, 0], [0, -1]])
+    node = np.array([nodes // 2, nodes // 2])
+    d = 0
+    pts, fwd = [], []
+    while len(pts) < n:
+        opts = []
+        for k in range(4):
+            if k == (d + 2) % 4:
+                continue
+            nxt = node + dirs[k]
+            if 0 <= nxt[0] <= nodes and 0 <= nxt[1] <= nodes:
+                opts.append(k)
+        if not opts:
+            opts = [(d + 2) % 4]
+        d = int(opts[rng.integers(len(opts))])
+        for s in range(per_seg):
+            p = (node + dirs[d] * (s / per_seg)) * spacing
+            pts.append([p[0], p[1], 1.2])
+            fwd.append([dirs[d][0], dirs[d][1], 0.0])
+        node = node + dirs[d]
+    c = np.array(pts[:n], dtype=np.float64)
+    f = np.array(fwd[:n], dtype=np.float64)
+    # look slightly ahead-and-sideways so the cameras are not exactly planar
+    f = f + np.array([0.0, 0.0, 0.05])
+    return c, f
+
+
+# --------------------------------------------------------------------------
+# Graph assembly
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class PoseGraph:
+    """A Sim(3) essential graph in the solver's input layout (all float64
+    except the int32 edge endpoints)."""
+    name: str
+    n_vertices: int
+    edge_i: np.ndarray          # (E,) int32
+    edge_j: np.ndarray          # (E,) int32
+    meas: np.ndarray            # (E, 8) float64, Z_ij ~ S_j S_i^-1
+    weight: np.ndarray          # (E,) float64
+    poses_init: np.ndarray      # (N, 8) drifted estimate (the initial guess)
+    poses_gt: np.ndarray        # (N, 8) ground truth
+    fixed_vertex: int = 0
+    n_loop_edges: int = 0
+    seed: int = 0
+
+    @property
+    def n_edges(self) -> int:
+        return int(self.edge_i.shape[0])
+
+
+def _window_edges(n, window):
+    """All forward pairs (i, i+k), 1 <= k <= window (k = 1 is the tree edge)."""
+    ii, jj = [], []
+    for k in range(1, window + 1):
+        i = np.arange(0, n - k)
+        ii.append(i)
+        jj.append(i + k)
+    return np.concatenate(ii), np.concatenate(jj)
+
+
+def _sampled_edges(n, rng, max_partners=10, lo=2, hi=15):
+    """Tree edges plus, per keyframe, up to ``max_partners`` partners drawn
+    without replacement from lo <= |i - j| <= hi; undirected duplicates are
+    removed.  Pairs are stored with i < j."""
+    pairs = set((k, k + 1) for k in range(n - 1))
+    for k in range(n):
+        cand = [j for j in range(k - hi, k + hi + 1) if 0 <= j < n and lo <= abs(j - k)]
+        m = min(max_partners, len(cand))
+        pick = rng.choice(len(cand), size=m, replace=False)
+        for p in pick:
+            j = cand[int(p)]
+            pairs.add((min(k, j), max(k, j)))
+    pairs = sorted(pairs)
+    a = np.array(pairs, dtype=np.int64)
+    return a[:, 0], a[:, 1]
+
+
+def _loop_pairs(centres, n_loops, min_gap=200, max_dist=1.5):
+    """``n_loops`` revisit pairs (i, j), j - i > min_gap, spatially close,
+    spread evenly over the later keyframes.  Returned as (later, earlier)."""
+    n = len(centres)
+    out = []
+    if n_loops <= 0:
+        return out
+    starts = np.linspace(min_gap + 1, n - 1, n_loops + 2)[1:-1].astype(int) if n_loops > 1 \
+        else np.array([n - 1])
+    used = set()
+    for s in starts:
+        found = None
+        for i in list(range(s, n)) + list(range(s - 1, min_gap, -1)):
+            if i in used:
+                continue
+            prev = centres[: i - min_gap]
+            if len(prev) == 0:
+                continue
+            d = np.linalg.norm(prev - centres[i], axis=1)
+            j = int(np.argmin(d))
+            if d[j] <= max_dist:
+                found = (i, j)
+                break
+        if found is not None:
+            used.add(found[0])
+            out.append(found)
+    return out
+
+
+def make_graph(kind, n, *, seed, window=15, n_loops=1, noise=(0.01, 0.02, 0.01),
+               meas_noise=False, name=None, weight=1.0):
+    """Build one synthetic essential graph.
+
+    kind      'circle' | 'figure8' | 'corridor'
+    n         number of keyframes
+    window    covisibility window (forward pairs within ``window`` frames);
+              for 'circle' the sampled scheme of the 200-keyframe case is used
+    n_loops   loop edges (for 'circle': the single last -> first edge)
+    noise     (sig_rot rad, sig_trans m, sig_logscale) per drift step
+    meas_noise  add i.i.d. noise of the same form to every measurement
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    if kind == "circle":
+        c, f = _circle(n)
+    elif kind == "figure8":
+        c, f = _figure8(n)
+    elif kind == "corridor":
+        c, f = _corridor(n, rng)
+    else:
+        raise ValueError(f"unknown trajectory kind {kind!r}")
+    gt = _poses_from_path(c, f)
+
+    # drifted estimate: chain of noisy relative steps from the (exact) first pose
+    steps = compose(gt[1:], inverse(gt[:-1]))
+    steps = compose(_noise(rng, n - 1, *noise), steps)
+    steps = np.concatenate([np.zeros((1, 8)), steps], axis=0)
+    est = _prefix_compose(steps, gt[0])
+
+    if kind == "circle":
+        ei, ej = _sampled_edges(n, rng)
+        loops = [(n - 1, 0)] if n_loops > 0 else []
+    else:
+        ei, ej = _window_edges(n, window)
+        loops = _loop_pairs(c, n_loops)
+    meas = compose(est[ej], inverse(est[ei]))
+    if loops:
+        li = np.array([p[0] for p in loops], dtype=np.int64)
+        lj = np.array([p[1] for p in loops], dtype=np.int64)
+        lmeas = compose(gt[lj], inverse(gt[li]))
+        ei = np.concatenate([ei, li])
+        ej = np.concatenate([ej, lj])
+        meas = np.concatenate([meas, lmeas], axis=0)
+    if meas_noise:
+        meas = compose(_noise(rng, meas.shape[0], *noise), meas)
+    meas[:, 0:4] /= np.linalg.norm(meas[:, 0:4], axis=1, keepdims=True)
+    E = ei.shape[0]
+    return PoseGraph(
+        name=name or f"{kind}{n}", n_vertices=n,
+        edge_i=ei.astype(np.int32), edge_j=ej.astype(np.int32),
+        meas=np.ascontiguousarray(meas), weight=np.full(E, float(weight)),
+        poses_init=np.ascontiguousarray(est), poses_gt=np.ascontiguousarray(gt),
+        fixed_vertex=0, n_loop_edges=len(loops), seed=seed)
+
+
+# The five evaluation configurations (seeded; sizes as in the workload table).
+CONFIGS = {
+    "c1_circle200": dict(kind="circle", n=200, seed=0, n_loops=1,
+                         noise=(0.01, 0.02, 0.01)),
+    "c2_figure8_2k": dict(kind="figure8", n=2000, seed=1, window=15, n_loops=5,
+                          noise=(0.01, 0.02, 0.01)),
+    "c3_corridor_8k": dict(kind="corridor", n=8000, seed=2, window=19, n_loops=40,
+                           noise=(0.01, 0.02, 0.02)),
+    "c5_figure8_4k_noisy": dict(kind="figure8", n=4000, seed=3, window=17, n_loops=10,
+                                noise=(0.01, 0.02, 0.01), meas_noise=True),
+}
+
+
+def make_config(name, **overrides):
+    """One of the named single-graph configurations."""
+    kw = dict(CONFIGS[name])
+    kw.update(overrides)
+    return make_graph(name=name, **kw)
+
+
+def make_batch(n_graphs=256, seed0=1000, n_min=100, n_max=5000, window=15,
+               kf_per_loop=400, noise=(0.01, 0.02, 0.01)):
+    """The batched workload: ``n_graphs`` independent figure-8 graphs with
+    keyframe counts drawn uniformly from [n_min, n_max], covisibility window
+    ``window`` and one loop edge per ``kf_per_loop`` keyframes.  Graph k uses
+    seed ``seed0 + k`` for both its size and its noise."""
+    out = []
+    for k in range(n_graphs):
+        rng = np.random.Generator(np.random.PCG64(seed0 + k))
+        n = int(rng.integers(n_min, n_max + 1))
+        loops = max(1, n // kf_per_loop)
+        out.append(make_graph("figure8", n, seed=seed0 + k, window=window,
+                              n_loops=loops, noise=noise, name=f"batch{k}"))
+    return out
