@@ -1,0 +1,251 @@
+/*
+ * pgo.h - C ABI of the GB300 Sim(3) essential-graph optimiser.
+ *
+ * The operation is the pose graph optimisation step of loop correction
+ * (FastLoop, Sec. III-B: after loop fusion, pose graph optimisation over the
+ * essential graph propagates the loop correction to every keyframe;
+ * Sec. IV-F: Levenberg-Marquardt with automatically differentiated
+ * Jacobians; Sec. VI: a Levenberg-Marquardt pose optimisation scheme).
+ *
+ * Problem (readings where the paper is silent are stated once here):
+ *   vertices   keyframe poses S_v = (q, t, s) in Sim(3), world -> camera,
+ *              x_c = s R(q) x_w + t, stored as 8 doubles
+ *              (qx, qy, qz, qw, tx, ty, tz, s), "pose8" below;
+ *   edges      (i, j, Z_ij, w_ij, Omega_ij): measured relative transform
+ *              Z_ij ~ S_j S_i^-1 (pose8), scalar weight w (default 1) and
+ *              7x7 information Omega (default identity);
+ *   residual   r_ij = log(Z_ij S_i S_j^-1) in R^7, tangent order
+ *              [omega(3), upsilon(3), sigma(1)];
+ *   cost       F = sum_ij w_ij r_ij^T Omega_ij r_ij;
+ *   gauge      one fixed vertex (the loop keyframe) is held constant;
+ *   update     S_v <- exp(delta_v) S_v (left perturbation), quaternion
+ *              renormalised;
+ *   LM step    (H + lambda I) delta = -b with H = sum w A^T Omega A,
+ *              b = sum w A^T Omega r, A = dr/d(delta) (exact Jacobians);
+ *              gain ratio rho = (F - F') / (delta^T (lambda delta - b));
+ *              accept if rho > 0 (lambda *= max(1/3, 1 - (2 rho - 1)^3),
+ *              nu = 2), else lambda *= nu, nu *= 2;
+ *              lambda_0 = tau * max diag(H).
+ *
+ * Conventions:
+ *   - Every call is ordered on the graph's CUDA stream (given at creation).
+ *     Calls that return data to host memory, or fill a report, synchronise
+ *     that stream before returning.
+ *   - Pointers flagged by a mem_space argument are host (PGO_MEM_HOST) or
+ *     device (PGO_MEM_DEVICE) memory of the current device; the caller owns
+ *     them.  The library copies inputs into its own device buffers.
+ *   - Errors: every function returns a pgo_status; pgo_last_error() gives a
+ *     thread-local message for the last failure on the calling thread.  A
+ *     failing call leaves the graph usable unless it returned PGO_ERR_CUDA.
+ *   - Edge-indexed outputs use the caller's edge order.
+ */
+#ifndef PGO_GB300_H
+#define PGO_GB300_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  PGO_OK = 0,
+  PGO_ERR_INVALID_ARG = 1,   /* bad size, index, self-edge, non-finite or
+                                non-positive scale, NULL where required */
+  PGO_ERR_OOM = 2,           /* device or host allocation failed */
+  PGO_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  PGO_ERR_NUMERICAL = 4,     /* non-finite cost or a non-PD block */
+  PGO_ERR_NOT_CONVERGED = 5, /* an iteration cap was reached */
+  PGO_ERR_STATE = 6          /* call out of order (e.g. backward before solve) */
+} pgo_status;
+
+typedef enum { PGO_FP64 = 0, PGO_MIXED = 1 } pgo_precision;
+typedef enum { PGO_MEM_HOST = 0, PGO_MEM_DEVICE = 1 } pgo_mem_space;
+typedef enum { PGO_GRAD_TANGENT7 = 0, PGO_GRAD_POSE8 = 1 } pgo_grad_layout;
+
+/* Graph description (Sec. III-B: the essential graph's keyframes and edges).
+ * All arrays are in mem_space.  edge_i/edge_j: int32[n_edges], endpoints in
+ * [0, n_vertices), i != j.  meas: double[n_edges * 8] pose8 of Z_ij (the
+ * quaternion need not be normalised; it is normalised on copy).  weight:
+ * double[n_edges] or NULL (all 1).  info: double[n_edges * 49] row-major
+ * symmetric positive definite 7x7 matrices, or NULL (identity).  poses:
+ * double[n_vertices * 8] initial estimate, or NULL (set later with
+ * pgo_graph_set_poses).  stream: a cudaStream_t (NULL = legacy default
+ * stream) on which every later call on this graph is ordered. */
+typedef struct {
+  int32_t n_vertices;
+  int32_t n_edges;
+  int32_t fixed_vertex;
+  int32_t mem_space;
+  const int32_t* edge_i;
+  const int32_t* edge_j;
+  const double* meas;
+  const double* weight;
+  const double* info;
+  const double* poses;
+  void* stream;
+} pgo_graph_desc;
+
+/* Solve options.  pgo_default_options() fills the documented defaults. */
+typedef struct {
+  int32_t max_iters;      /* LM iterations, rejected ones included (20) */
+  int32_t precision;      /* pgo_precision (PGO_FP64) */
+  double tau;             /* lambda_0 = tau * max diag(H) (1e-5) */
+  double lambda_init;     /* > 0: use as lambda_0 instead (0) */
+  double ftol;            /* stop when |F - F'| <= ftol * F after a step,
+                             accepted or rejected (1e-14) */
+  double gtol;            /* stop when |b|_inf <= gtol (1e-13) */
+  double pcg_tol;         /* PCG: |r| <= pcg_tol * |b| (1e-10) */
+  int32_t pcg_max_iters;  /* PCG iteration cap per linear solve (5000) */
+  int32_t refine_steps;   /* PGO_MIXED: FP64 iterative-refinement passes (3) */
+  double refine_tol;      /* PGO_MIXED: inner FP32 PCG relative tolerance (1e-5) */
+  int32_t polish_iters;   /* undamped Newton steps after LM, each kept only
+                             while it lowers |b|_inf (0; use >0 before
+                             pgo_backward) */
+  int32_t schedule;       /* kernel schedule id; -1 = library default */
+} pgo_solve_options;
+
+/* Solve report. */
+typedef struct {
+  double initial_cost;
+  double final_cost;
+  double final_lambda;
+  double grad_inf_norm;   /* |b|_inf at the last linearisation */
+  int32_t iterations;     /* LM iterations executed (rejected included) */
+  int32_t accepted;
+  int32_t pcg_iterations; /* total inner PCG iterations */
+  int32_t stop_reason;    /* 0 max_iters, 1 |dF| <= ftol F, 2 gtol, 3 lambda overflow,
+                             4 numerical failure */
+  int32_t status;         /* pgo_status of the solve */
+  float ms_total;         /* device time of the solve (CUDA events) */
+} pgo_report;
+
+typedef struct pgo_graph pgo_graph;
+typedef struct pgo_batch pgo_batch;
+
+/* Thread-local message describing the last failure on this thread. */
+const char* pgo_last_error(void);
+
+/* Library version string. */
+const char* pgo_version(void);
+
+/* Fill *opt with the defaults listed in pgo_solve_options. */
+pgo_status pgo_default_options(pgo_solve_options* opt);
+
+/* Create a resident device copy of an essential graph (Sec. III-B, IV-E:
+ * keep the data on the GPU and allocate once).  Validates the description,
+ * sorts edges by endpoint, builds the block-sparse pattern of the normal
+ * matrix and allocates every buffer a solve needs.  *out receives a handle
+ * owned by the caller (free with pgo_graph_destroy).  On error *out is NULL. */
+pgo_status pgo_graph_create(const pgo_graph_desc* desc, pgo_graph** out);
+
+/* Release every resource of a graph (NULL is ignored).  Synchronises the
+ * graph's stream first. */
+void pgo_graph_destroy(pgo_graph* g);
+
+/* Replace the current vertex estimate: poses double[n_vertices * 8] pose8 in
+ * mem_space.  Quaternions are normalised on copy.  Host poses are validated
+ * (finite, non-zero quaternion, scale > 0) and the call returns once they are
+ * copied; device poses are copied on the graph's stream with no host round
+ * trip and no host validation (a non-finite pose makes the next solve report
+ * PGO_ERR_NUMERICAL). */
+pgo_status pgo_graph_set_poses(pgo_graph* g, const double* poses, int32_t mem_space);
+
+/* Copy the current vertex estimate to poses (double[n_vertices * 8]). */
+pgo_status pgo_graph_get_poses(pgo_graph* g, double* poses, int32_t mem_space);
+
+/* Cost F at the current estimate (Sec. IV-F objective) and, optionally, the
+ * per-edge residuals r_ij (double[n_edges * 7], NULL to skip).  *cost is host
+ * memory; residuals are in mem_space. */
+pgo_status pgo_graph_cost(pgo_graph* g, double* cost, double* residuals, int32_t mem_space);
+
+/* Linearise at the current estimate (Sec. IV-F: exact Jacobians of every
+ * edge residual, then the block-sparse normal equations).  Outputs (any may
+ * be NULL) in mem_space, all FP64 whatever the precision:
+ *   jac     double[n_edges * 2 * 49]: A_i then A_j per edge, row-major 7x7;
+ *   h_diag  double[n_vertices * 49]: diagonal blocks sum w A^T Omega A;
+ *   h_off   double[n_edges * 49]: the (i, j) block w A_i^T Omega A_j;
+ *   b       double[n_vertices * 7]: sum w A^T Omega r.
+ * No rows are dropped: the fixed vertex's blocks are reported as computed. */
+pgo_status pgo_graph_linearize(pgo_graph* g, int32_t precision, double* jac, double* h_diag,
+                               double* h_off, double* b, int32_t mem_space);
+
+/* One damped linear solve at the current estimate (Sec. IV-F linear solver):
+ * (H + lambda I) delta = -b with the block-Jacobi preconditioned conjugate
+ * gradient method, the fixed vertex's rows and columns removed.
+ * delta: double[n_vertices * 7] in mem_space (fixed row = 0).  *pcg_iters
+ * (host, nullable) receives the iteration count.  Returns
+ * PGO_ERR_NOT_CONVERGED when opt->pcg_max_iters is reached (delta is still
+ * written). */
+pgo_status pgo_graph_damped_step(pgo_graph* g, const pgo_solve_options* opt, double lambda,
+                                 double* delta, int32_t* pcg_iters, int32_t mem_space);
+
+/* Re-solve the damped system at the last linearisation (the one made by
+ * pgo_graph_linearize, pgo_graph_damped_step or the last LM iteration of
+ * pgo_solve) for a new lambda, without relinearising: this is the LM step
+ * after a rejected update (Sec. IV-F linear solver).  delta (nullable,
+ * double[n_vertices * 7] in mem_space) and *pcg_iters (nullable, host)
+ * are written after synchronising; with both NULL the call only enqueues the
+ * work on the graph's stream and returns. */
+pgo_status pgo_graph_resolve(pgo_graph* g, const pgo_solve_options* opt, double lambda, double* delta,
+                             int32_t* pcg_iters, int32_t mem_space);
+
+/* Fill *report from the device state of the last pgo_solve (synchronises the
+ * graph's stream); use after a pgo_solve called with report == NULL. */
+pgo_status pgo_graph_report(pgo_graph* g, pgo_report* report);
+
+/* Run Levenberg-Marquardt from the current estimate (Sec. IV-F, Sec. VI) and
+ * keep the result as the new current estimate.  opt NULL = defaults.
+ * report (host, nullable) is filled after synchronising.  poses_out
+ * (double[n_vertices * 8], nullable) receives the optimised poses in
+ * out_mem_space.  The whole solve runs on the device as one CUDA graph;
+ * the host issues no per-iteration work. */
+pgo_status pgo_solve(pgo_graph* g, const pgo_solve_options* opt, pgo_report* report,
+                     double* poses_out, int32_t out_mem_space);
+
+/* Implicit adjoint of the last solve (extends Sec. IV-F's differentiated
+ * objective): with b(x*, Z, w) = 0 at the optimum, mu = H_full^-1 dL/dx and
+ * dL/dtheta = -mu^T db/dtheta, H_full the full (second-order) Hessian of F/2.
+ *   dL_dposes   N x 7 left-tangent gradient (PGO_GRAD_TANGENT7) or N x 8
+ *               gradient w.r.t. the pose8 entries (PGO_GRAD_POSE8);
+ *               the fixed vertex's row is ignored;
+ *   dL_dmeas    E x 7 left-tangent gradient w.r.t. each Z (TANGENT7) or
+ *               E x 8 w.r.t. its pose8 entries (POSE8); nullable;
+ *   dL_dweight  E; nullable.
+ * Needs a solve converged to a stationary point (use polish_iters > 0);
+ * returns PGO_ERR_STATE if no solve has run.  The linear solve uses PCG on
+ * H_full (tolerance opt->pcg_tol, cap opt->pcg_max_iters). */
+pgo_status pgo_backward(pgo_graph* g, const pgo_solve_options* opt, const double* dL_dposes,
+                        int32_t grad_layout, double* dL_dmeas, double* dL_dweight,
+                        int32_t mem_space);
+
+/* Batched form: many independent graphs of uneven size solved together in
+ * one persistent device schedule captured in a CUDA graph.  descs: n_graphs
+ * descriptions (host structs; their arrays in each desc's mem_space).
+ * stream: the batch's stream. */
+pgo_status pgo_batch_create(int32_t n_graphs, const pgo_graph_desc* descs, void* stream,
+                            pgo_batch** out);
+void pgo_batch_destroy(pgo_batch* b);
+
+/* Solve every graph of the batch with LM (same rules as pgo_solve, per-graph
+ * lambda, acceptance and stopping).  reports: host array of n_graphs
+ * (nullable).  poses_out: host array of n_graphs pointers, each
+ * double[n_vertices_k * 8] in out_mem_space (nullable). */
+pgo_status pgo_batch_solve(pgo_batch* b, const pgo_solve_options* opt, pgo_report* reports,
+                           double* const* poses_out, int32_t out_mem_space);
+
+/* Stateless cost evaluation (the Sec. IV-F objective) over caller-owned
+ * device arrays: n_vertices poses (pose8), n_edges edges (edge_i, edge_j,
+ * meas pose8, weight nullable).  *cost_out is a device double written on
+ * `stream`.  Uses a temporary device workspace of one double per thread
+ * block, allocated and freed on the stream (stream-ordered allocator).
+ * No validation of indices beyond a device-side bounds check that skips and
+ * counts bad edges; returns PGO_ERR_INVALID_ARG for negative sizes. */
+pgo_status pgo_evaluate_cost(int32_t n_vertices, int32_t n_edges, const int32_t* edge_i,
+                             const int32_t* edge_j, const double* meas, const double* weight,
+                             const double* poses, double* cost_out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PGO_GB300_H */

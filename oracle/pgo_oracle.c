@@ -809,7 +809,7 @@ static double grad_inf(const ograph *g, const double *b) {
 }
 
 /* Levenberg-Marquardt (rules in the file header).  poses (N x 8) in/out.
- * stop_reason: 0 max iterations, 1 relative cost decrease <= ftol,
+ * stop_reason: 0 max iterations, 1 |F - F'| <= ftol F (accepted or rejected step),
  * 2 gradient inf-norm <= gtol, 3 lambda overflow.
  * Near the optimum the cost decrease of a step falls below the rounding of
  * F itself (it is quadratic in the gradient), so cost-based acceptance stalls
@@ -866,8 +866,9 @@ EXPORT int og_lm(void *h, double *poses, const og_options *opt, og_report *rep) 
         }
     }
     double rho = (pred > 0.0 && isfinite(Fn)) ? (F - Fn) / pred : -1.0;
+    /* |F - F'| <= ftol F, accepted or not: no progress is measurable */
+    const int flat = isfinite(Fn) && fabs(F - Fn) <= opt->ftol * F;
     if (rho > 0.0) {
-      double dF = F - Fn;
       sim3 *sw = S; S = Sn; Sn = sw;
       double f = 2.0 * rho - 1.0;
       f = 1.0 - f * f * f;
@@ -876,10 +877,11 @@ EXPORT int og_lm(void *h, double *poses, const og_options *opt, og_report *rep) 
       need_lin = 1;
       ++acc;
       F = Fn;
-      if (dF <= opt->ftol * (F + dF)) { stop = 1; break; }
+      if (flat) { stop = 1; break; }
     } else {
       lambda *= nu;
       nu *= 2.0;
+      if (flat) { stop = 1; break; }
       if (!(lambda < 1e32)) { stop = 3; break; }
     }
   }

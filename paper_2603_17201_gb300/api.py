@@ -1,0 +1,252 @@
+"""Python binding of the GB300 Sim(3) essential-graph optimiser.
+
+Thin marshalling over the C ABI (``include/pgo.h``): arrays go in as host
+numpy arrays or torch tensors (CUDA tensors are passed as device pointers on
+the current torch stream), and every computation runs in the CUDA library.
+The problem is the pose graph optimisation step of loop correction
+(Sec. III-B, Sec. IV-F): Levenberg-Marquardt over keyframe Sim(3) poses with
+one fixed gauge keyframe.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib as L
+
+__all__ = ["PoseGraph", "evaluate_cost", "default_options", "PGOError"]
+
+PGOError = L.PGOError
+default_options = L.default_options
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_cuda_tensor(x):
+    try:
+        torch = _torch()
+    except Exception:  # pragma: no cover - torch is a hard dependency of the package
+        return False
+    return isinstance(x, torch.Tensor) and x.is_cuda
+
+
+def _current_stream_handle():
+    torch = _torch()
+    if torch.cuda.is_available():
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+class _Marshal:
+    """Holds host or device copies of a set of arrays in one memory space."""
+
+    def __init__(self, device: bool):
+        self.device = device
+        self.keep = []
+
+    def put(self, x, dtype, shape=None):
+        if x is None:
+            return None
+        if self.device:
+            torch = _torch()
+            tdt = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+            t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x, dtype=dtype))
+            t = t.to(device="cuda", dtype=tdt).contiguous()
+            if shape is not None:
+                t = t.reshape(shape)
+            self.keep.append(t)
+            return ctypes.c_void_p(t.data_ptr())
+        if not isinstance(x, np.ndarray):
+            try:
+                x = x.detach().cpu().numpy()
+            except AttributeError:
+                x = np.asarray(x)
+        a = np.ascontiguousarray(x, dtype=dtype)
+        if shape is not None:
+            a = a.reshape(shape)
+        self.keep.append(a)
+        return ctypes.c_void_p(a.ctypes.data)
+
+    @property
+    def mem_space(self):
+        return L.PGO_MEM_DEVICE if self.device else L.PGO_MEM_HOST
+
+
+class PoseGraph:
+    """A device-resident essential graph (see ``pgo_graph_create``).
+
+    n_vertices, edge_i, edge_j (E,), meas (E, 8) pose8 of Z_ij ~ S_j S_i^-1,
+    weight (E,) or None, info (E, 7, 7) or None, poses (N, 8) or None,
+    fixed_vertex (the gauge keyframe)."""
+
+    def __init__(self, n_vertices, edge_i, edge_j, meas, weight=None, info=None, poses=None,
+                 fixed_vertex=0, stream=None):
+        self._lib = L.load()
+        self._h = ctypes.c_void_p()
+        device = any(_is_cuda_tensor(x) for x in (edge_i, edge_j, meas, weight, info, poses))
+        m = _Marshal(device)
+        E = int(len(edge_i))
+        d = L.GraphDesc()
+        d.n_vertices = int(n_vertices)
+        d.n_edges = E
+        d.fixed_vertex = int(fixed_vertex)
+        d.mem_space = m.mem_space
+        d.edge_i = m.put(edge_i, np.int32)
+        d.edge_j = m.put(edge_j, np.int32)
+        d.meas = m.put(meas, np.float64, (E, 8))
+        d.weight = m.put(weight, np.float64, (E,))
+        d.info = m.put(info, np.float64, (E, 49))
+        d.poses = m.put(poses, np.float64, (int(n_vertices), 8))
+        if device:
+            _torch().cuda.current_stream().synchronize()
+        d.stream = stream if stream is not None else _current_stream_handle()
+        L.check(self._lib.pgo_graph_create(ctypes.byref(d), ctypes.byref(self._h)))
+        self.n_vertices = int(n_vertices)
+        self.n_edges = E
+        self.fixed_vertex = int(fixed_vertex)
+
+    @classmethod
+    def from_synthetic(cls, g, poses=None, **kw):
+        """From a ``synthetic.PoseGraph``; the initial estimate is its drifted
+        chain unless ``poses`` is given."""
+        return cls(g.n_vertices, g.edge_i, g.edge_j, g.meas, g.weight, None,
+                   g.poses_init if poses is None else poses, g.fixed_vertex, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.pgo_graph_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # ---------------------------------------------------------------- state
+    def set_poses(self, poses):
+        """Replace the current estimate.  A CUDA tensor is copied on the
+        graph's stream (it must be ready on that stream); host arrays are
+        validated and copied synchronously."""
+        m = _Marshal(_is_cuda_tensor(poses))
+        p = m.put(poses, np.float64, (self.n_vertices, 8))
+        L.check(self._lib.pgo_graph_set_poses(self._h, p, m.mem_space))
+        self._keep = m.keep
+
+    def get_poses(self, device=False):
+        """Current estimate (N, 8): a CUDA tensor if ``device`` else numpy."""
+        if device:
+            torch = _torch()
+            out = torch.empty((self.n_vertices, 8), dtype=torch.float64, device="cuda")
+            L.check(self._lib.pgo_graph_get_poses(self._h, ctypes.c_void_p(out.data_ptr()), L.PGO_MEM_DEVICE))
+            return out
+        out = np.empty((self.n_vertices, 8))
+        L.check(self._lib.pgo_graph_get_poses(self._h, ctypes.c_void_p(out.ctypes.data), L.PGO_MEM_HOST))
+        return out
+
+    def cost(self, residuals=False):
+        """F at the current estimate (and the (E, 7) residuals)."""
+        c = ctypes.c_double()
+        r = np.empty((self.n_edges, 7)) if residuals else None
+        L.check(self._lib.pgo_graph_cost(self._h, ctypes.byref(c),
+                                         ctypes.c_void_p(r.ctypes.data) if residuals else None,
+                                         L.PGO_MEM_HOST))
+        return (c.value, r) if residuals else c.value
+
+    # ---------------------------------------------------------------- steps
+    def linearize(self, precision="fp64", jacobians=True):
+        """Normal equations at the current estimate (FP64 copies):
+        dict(jac (E,2,7,7), h_diag (N,7,7), h_off (E,7,7), b (N,7))."""
+        prec = L.PGO_MIXED if str(precision).lower() == "mixed" else L.PGO_FP64
+        N, E = self.n_vertices, self.n_edges
+        jac = np.empty((E, 2, 7, 7)) if jacobians else None
+        hd = np.empty((N, 7, 7))
+        ho = np.empty((E, 7, 7))
+        b = np.empty((N, 7))
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else None  # noqa: E731
+        L.check(self._lib.pgo_graph_linearize(self._h, prec, ptr(jac), ptr(hd), ptr(ho), ptr(b), L.PGO_MEM_HOST))
+        out = dict(h_diag=hd, h_off=ho, b=b)
+        if jacobians:
+            out["jac"] = jac
+        return out
+
+    def damped_step(self, lam, **opts):
+        """Solve (H + lam I) delta = -b at the current estimate with PCG.
+        Returns (delta (N, 7), PCG iterations); raises on the iteration cap
+        unless ``allow_cap=True``."""
+        allow_cap = opts.pop("allow_cap", False)
+        o = L.default_options(**opts)
+        d = np.empty((self.n_vertices, 7))
+        it = ctypes.c_int32()
+        st = self._lib.pgo_graph_damped_step(self._h, ctypes.byref(o), float(lam),
+                                             ctypes.c_void_p(d.ctypes.data), ctypes.byref(it), L.PGO_MEM_HOST)
+        if not (allow_cap and st == L.PGO_ERR_NOT_CONVERGED):
+            L.check(st)
+        return d, int(it.value)
+
+    def resolve(self, lam, **opts):
+        """Re-solve the damped system at the last linearisation for a new
+        lambda.  Returns (delta (N, 7), PCG iterations)."""
+        allow_cap = opts.pop("allow_cap", False)
+        o = L.default_options(**opts)
+        d = np.empty((self.n_vertices, 7))
+        it = ctypes.c_int32()
+        st = self._lib.pgo_graph_resolve(self._h, ctypes.byref(o), float(lam), ctypes.c_void_p(d.ctypes.data),
+                                         ctypes.byref(it), L.PGO_MEM_HOST)
+        if not (allow_cap and st == L.PGO_ERR_NOT_CONVERGED):
+            L.check(st)
+        return d, int(it.value)
+
+    def resolve_async(self, lam, **opts):
+        """Enqueue a re-solve on the graph's stream (no synchronisation)."""
+        o = L.default_options(**opts)
+        L.check(self._lib.pgo_graph_resolve(self._h, ctypes.byref(o), float(lam), None, None, L.PGO_MEM_HOST))
+
+    def solve_report(self):
+        """Report of the last solve (synchronises the graph's stream)."""
+        rep = L.Report()
+        L.check(self._lib.pgo_graph_report(self._h, ctypes.byref(rep)))
+        return rep.as_dict()
+
+    def solve(self, poses_out=None, **opts):
+        """Levenberg-Marquardt from the current estimate; returns the report
+        dict.  ``poses_out``: optional (N, 8) numpy array or CUDA tensor."""
+        o = L.default_options(**opts)
+        rep = L.Report()
+        if poses_out is None:
+            L.check(self._lib.pgo_solve(self._h, ctypes.byref(o), ctypes.byref(rep), None, L.PGO_MEM_HOST))
+        elif _is_cuda_tensor(poses_out):
+            L.check(self._lib.pgo_solve(self._h, ctypes.byref(o), ctypes.byref(rep),
+                                        ctypes.c_void_p(poses_out.data_ptr()), L.PGO_MEM_DEVICE))
+        else:
+            assert poses_out.dtype == np.float64 and poses_out.flags.c_contiguous
+            L.check(self._lib.pgo_solve(self._h, ctypes.byref(o), ctypes.byref(rep),
+                                        ctypes.c_void_p(poses_out.ctypes.data), L.PGO_MEM_HOST))
+        return rep.as_dict()
+
+    def solve_async(self, **opts):
+        """Enqueue a solve on the graph's stream without reading a report."""
+        o = L.default_options(**opts)
+        L.check(self._lib.pgo_solve(self._h, ctypes.byref(o), None, None, L.PGO_MEM_HOST))
+
+
+def evaluate_cost(n_vertices, edge_i, edge_j, meas, weight, poses):
+    """Stateless F over CUDA tensors (int32 edges, float64 pose8 arrays);
+    returns a 0-d CUDA tensor written on the current stream."""
+    torch = _torch()
+    lib = L.load()
+    out = torch.empty((), dtype=torch.float64, device="cuda")
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+    L.check(lib.pgo_evaluate_cost(int(n_vertices), int(edge_i.numel()), ptr(edge_i), ptr(edge_j), ptr(meas),
+                                  ptr(weight), ptr(poses), ptr(out), _current_stream_handle()))
+    return out

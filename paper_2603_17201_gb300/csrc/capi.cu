@@ -1,0 +1,905 @@
+// Host runtime and C ABI of the GB300 Sim(3) essential-graph optimiser.
+//
+// pgo_graph_create validates the description, orders edges by their lower
+// endpoint, builds the vertex incidence lists that define the block-sparse
+// pattern of the normal matrix and allocates every device buffer once
+// (FastLoop keeps its loop-closing data resident on the GPU and allocates
+// once, Sec. IV-E).  pgo_solve replays one CUDA graph per (precision,
+// refinement passes): a WHILE node runs the LM iterations and a nested WHILE
+// node runs the PCG iterations, with every decision taken on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <functional>
+#include <map>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace pgo;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+pgo_status fail(pgo_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+#define CUDA_TRY(expr)                                                                         \
+  do {                                                                                         \
+    cudaError_t e_ = (expr);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      if (e_ == cudaErrorMemoryAllocation)                                                     \
+        return fail(PGO_ERR_OOM, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return fail(PGO_ERR_CUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    }                                                                                          \
+  } while (0)
+
+// Test hook: fail device allocations above this many bytes (0 = off).
+size_t g_alloc_limit = 0;
+
+// One device arena per graph, sub-allocated with 256-byte alignment.
+struct Arena {
+  char* base = nullptr;
+  size_t size = 0, used = 0;
+  template <class T>
+  T* take(size_t count) {
+    size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base + used);
+    used += bytes;
+    return p;
+  }
+};
+
+template <class T>
+size_t arena_bytes(size_t count) {
+  return (count * sizeof(T) + 255) & ~size_t(255);
+}
+
+bool copy_in(void* dst, const void* src, size_t bytes, int mem_space, cudaStream_t s) {
+  if (bytes == 0) return true;
+  cudaMemcpyKind kind = mem_space == PGO_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  return cudaMemcpyAsync(dst, src, bytes, kind, s) == cudaSuccess;
+}
+
+// Helper that assembles a CUDA graph from captured segments and WHILE nodes.
+struct GraphBuilder {
+  cudaStream_t cs;
+  std::vector<cudaGraphNode_t> tail;
+  cudaError_t err = cudaSuccess;
+
+  void capture(cudaGraph_t graph, const std::function<void(cudaStream_t)>& fn) {
+    if (err != cudaSuccess) return;
+    err = cudaStreamBeginCaptureToGraph(cs, graph, tail.empty() ? nullptr : tail.data(), nullptr, tail.size(),
+                                        cudaStreamCaptureModeThreadLocal);
+    if (err != cudaSuccess) return;
+    fn(cs);
+    cudaStreamCaptureStatus status;
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    err = cudaStreamGetCaptureInfo(cs, &status, nullptr, nullptr, &deps, nullptr, &ndeps);
+    std::vector<cudaGraphNode_t> nt;
+    if (err == cudaSuccess) nt.assign(deps, deps + ndeps);
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(cs, &out);
+    if (err == cudaSuccess) err = e2;
+    if (err == cudaSuccess && !nt.empty()) tail = nt;
+  }
+
+  // Adds a WHILE node after the current tail; returns its body graph.
+  cudaGraph_t add_while(cudaGraph_t graph, cudaGraphConditionalHandle h) {
+    if (err != cudaSuccess) return nullptr;
+    cudaGraphNodeParams p = {};
+    p.type = cudaGraphNodeTypeConditional;
+    p.conditional.handle = h;
+    p.conditional.type = cudaGraphCondTypeWhile;
+    p.conditional.size = 1;
+    cudaGraphNode_t node;
+    err = cudaGraphAddNode(&node, graph, tail.empty() ? nullptr : tail.data(), nullptr, tail.size(), &p);
+    if (err != cudaSuccess) return nullptr;
+    tail.assign(1, node);
+    return p.conditional.phGraph_out[0];
+  }
+};
+
+}  // namespace
+
+struct pgo_graph {
+  int N = 0, E = 0, fixed = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  Arena arena;
+  DevGraph g{};
+  int* d_perm = nullptr;          // internal edge -> caller edge
+  double* d_scratch = nullptr;    // N * 8 doubles + E * 98 staging for exports
+  size_t scratch_doubles = 0;
+  double* d_cost = nullptr;
+  SolverState* h_state = nullptr; // pinned copy for reports
+  DevOptions* h_opt = nullptr;    // pinned staging of options
+  std::map<long long, cudaGraphExec_t> execs;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  bool solved = false;
+  bool has_info = false;
+};
+
+struct pgo_batch {
+  std::vector<pgo_graph*> graphs;
+  cudaStream_t stream = nullptr;
+};
+
+namespace {
+
+void fill_dev_options(const pgo_solve_options& o, DevOptions* d) {
+  d->max_iters = o.max_iters;
+  d->precision = o.precision;
+  d->pcg_max_iters = o.pcg_max_iters;
+  d->refine_steps = o.refine_steps;
+  d->polish_iters = o.polish_iters;
+  d->tau = o.tau;
+  d->lambda_init = o.lambda_init;
+  d->ftol = o.ftol;
+  d->gtol = o.gtol;
+  d->pcg_tol = o.pcg_tol;
+  d->refine_tol = o.refine_tol;
+  d->lambda_fixed = 0.0;
+}
+
+pgo_status check_options(const pgo_solve_options& o) {
+  if (o.max_iters < 0 || o.pcg_max_iters < 1 || o.refine_steps < 1 || o.refine_steps > 16)
+    return fail(PGO_ERR_INVALID_ARG, "options: max_iters >= 0, pcg_max_iters >= 1, 1 <= refine_steps <= 16");
+  if (o.precision != PGO_FP64 && o.precision != PGO_MIXED)
+    return fail(PGO_ERR_INVALID_ARG, "options: unknown precision %d", o.precision);
+  if (!(o.tau > 0) || !(o.pcg_tol > 0) || !(o.refine_tol > 0) || !(o.ftol >= 0) || !(o.gtol >= -1.0))
+    return fail(PGO_ERR_INVALID_ARG, "options: tau, pcg_tol, refine_tol must be > 0");
+  return PGO_OK;
+}
+
+// The linear-solve part of one LM iteration: block-Jacobi preconditioner,
+// then one persistent PCG launch (FP64), or, in mixed precision, FP32 PCG
+// launches inside FP64 iterative refinement (refine_steps passes, each
+// skipped on the device once the FP64 residual meets pcg_tol).
+void enqueue_linear_solve(const DevGraph& g, int mixed, int refine_steps, cudaStream_t s, cudaError_t* err) {
+  launch_precond(g, mixed, s);
+  if (!mixed) {
+    cudaError_t e = launch_pcg(g, 0, 0, s);
+    if (e != cudaSuccess && *err == cudaSuccess) *err = e;
+    return;
+  }
+  for (int pass = 0; pass < refine_steps; ++pass) {
+    launch_refine_residual(g, pass == 0, s);
+    cudaError_t e = launch_pcg(g, 1, 1, s);
+    if (e != cudaSuccess && *err == cudaSuccess) *err = e;
+    launch_refine_accumulate(g, s);
+  }
+}
+
+// One LM iteration (the body of the WHILE node, or one host-driven step).
+void enqueue_lm_body(const DevGraph& g, int mixed, int refine_steps, cudaStream_t s, unsigned long long lm_cond,
+                     cudaError_t* err) {
+  launch_linearize(g, mixed, s);
+  launch_assemble(g, mixed, s);
+  enqueue_linear_solve(g, mixed, refine_steps, s, err);
+  launch_update(g, mixed, s);
+  launch_cost(g, 1, s, lm_cond);
+}
+
+pgo_status build_solve_graph(pgo_graph* G, int mixed, int refine_steps, cudaGraphExec_t* out) {
+  const DevGraph& g = G->g;
+  cudaGraph_t graph;
+  CUDA_TRY(cudaGraphCreate(&graph, 0));
+  GraphBuilder b{G->cap_stream};
+  cudaGraphConditionalHandle hl;
+  b.err = cudaGraphConditionalHandleCreate(&hl, graph, 0, 0);
+  b.capture(graph, [&](cudaStream_t s) {
+    launch_lm_reset(g, s);
+    launch_cost(g, 0, s, hl);
+  });
+  cudaGraph_t body = b.add_while(graph, hl);
+  if (body) {
+    GraphBuilder lb{G->cap_stream};
+    cudaError_t le = cudaSuccess;
+    lb.capture(body, [&](cudaStream_t s) { enqueue_lm_body(g, mixed, refine_steps, s, hl, &le); });
+    if (lb.err != cudaSuccess) b.err = lb.err;
+    if (le != cudaSuccess) b.err = le;
+  }
+  if (b.err != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(PGO_ERR_CUDA, "building the solve graph: %s", cudaGetErrorString(b.err));
+  }
+  cudaError_t e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(PGO_ERR_CUDA, "instantiating the solve graph: %s", cudaGetErrorString(e));
+  return PGO_OK;
+}
+
+// A linear solve at a given lambda (pgo_graph_damped_step): linearise, then
+// the same linear-solve sequence as one LM iteration.
+pgo_status build_step_graph(pgo_graph* G, int mixed, int refine_steps, cudaGraphExec_t* out) {
+  const DevGraph& g = G->g;
+  cudaGraph_t graph;
+  CUDA_TRY(cudaGraphCreate(&graph, 0));
+  GraphBuilder b{G->cap_stream};
+  cudaError_t le = cudaSuccess;
+  b.capture(graph, [&](cudaStream_t s) {
+    launch_linearize(g, mixed, s);
+    launch_assemble(g, mixed, s);
+    enqueue_linear_solve(g, mixed, refine_steps, s, &le);
+  });
+  if (le != cudaSuccess) b.err = le;
+  if (b.err != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(PGO_ERR_CUDA, "building the step graph: %s", cudaGetErrorString(b.err));
+  }
+  cudaError_t e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(PGO_ERR_CUDA, "instantiating the step graph: %s", cudaGetErrorString(e));
+  return PGO_OK;
+}
+
+// Host-driven LM loop with plain stream launches (schedule 1): the same
+// kernels, for profilers that cannot look inside conditional graph nodes.
+pgo_status run_eager(pgo_graph* G, int mixed, int refine_steps, int max_iters) {
+  const DevGraph& g = G->g;
+  cudaStream_t s = G->stream;
+  cudaError_t le = cudaSuccess;
+  launch_lm_reset(g, s);
+  launch_cost(g, 0, s, 0);
+  for (int it = 0; it < max_iters + 1; ++it) {
+    CUDA_TRY(cudaMemcpyAsync(G->h_state, g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (G->h_state->done || G->h_state->it >= max_iters) break;
+    enqueue_lm_body(g, mixed, refine_steps, s, 0, &le);
+    CUDA_TRY(le);
+    CUDA_TRY(cudaGetLastError());
+  }
+  return PGO_OK;
+}
+
+// Re-solve at the last linearisation: state reset, then the linear solve.
+pgo_status build_resolve_graph(pgo_graph* G, int mixed, int refine_steps, cudaGraphExec_t* out) {
+  const DevGraph& g = G->g;
+  cudaGraph_t graph;
+  CUDA_TRY(cudaGraphCreate(&graph, 0));
+  GraphBuilder b{G->cap_stream};
+  cudaError_t le = cudaSuccess;
+  b.capture(graph, [&](cudaStream_t s) {
+    launch_resolve_reset(g, s);
+    enqueue_linear_solve(g, mixed, refine_steps, s, &le);
+  });
+  if (le != cudaSuccess) b.err = le;
+  if (b.err != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(PGO_ERR_CUDA, "building the re-solve graph: %s", cudaGetErrorString(b.err));
+  }
+  cudaError_t e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(PGO_ERR_CUDA, "instantiating the re-solve graph: %s", cudaGetErrorString(e));
+  return PGO_OK;
+}
+
+pgo_status get_exec(pgo_graph* G, int kind, int mixed, int refine_steps, cudaGraphExec_t* out) {
+  const long long key = ((long long)kind << 32) | ((long long)mixed << 16) | (mixed ? refine_steps : 0);
+  auto it = G->execs.find(key);
+  if (it != G->execs.end()) {
+    *out = it->second;
+    return PGO_OK;
+  }
+  cudaGraphExec_t ex = nullptr;
+  pgo_status st = kind == 0   ? build_solve_graph(G, mixed, refine_steps, &ex)
+                  : kind == 1 ? build_step_graph(G, mixed, refine_steps, &ex)
+                              : build_resolve_graph(G, mixed, refine_steps, &ex);
+  if (st != PGO_OK) return st;
+  G->execs[key] = ex;
+  *out = ex;
+  return PGO_OK;
+}
+
+bool finite_pose(const double* p) {
+  for (int k = 0; k < 8; ++k)
+    if (!std::isfinite(p[k])) return false;
+  const double n = p[0] * p[0] + p[1] * p[1] + p[2] * p[2] + p[3] * p[3];
+  return n > 1e-20 && p[7] > 0.0;
+}
+
+// Cholesky Omega = L L^T of a symmetric 7x7 (row-major); packed lower output.
+bool chol_pack(const double* O, double* Lp) {
+  double L[7][7] = {};
+  for (int j = 0; j < 7; ++j) {
+    double d = O[j * 7 + j];
+    for (int k = 0; k < j; ++k) d -= L[j][k] * L[j][k];
+    if (!(d > 0.0) || !std::isfinite(d)) return false;
+    L[j][j] = std::sqrt(d);
+    for (int i = j + 1; i < 7; ++i) {
+      double s = O[i * 7 + j];
+      for (int k = 0; k < j; ++k) s -= L[i][k] * L[j][k];
+      L[i][j] = s / L[j][j];
+    }
+  }
+  for (int a = 0; a < 7; ++a)
+    for (int c = 0; c <= a; ++c) Lp[a * (a + 1) / 2 + c] = L[a][c];
+  return true;
+}
+
+template <class T>
+bool fetch(std::vector<T>& dst, const T* src, size_t n, int mem_space) {
+  dst.resize(n);
+  if (n == 0) return true;
+  if (mem_space == PGO_MEM_DEVICE) return cudaMemcpy(dst.data(), src, n * sizeof(T), cudaMemcpyDeviceToHost) == cudaSuccess;
+  std::memcpy(dst.data(), src, n * sizeof(T));
+  return true;
+}
+
+pgo_status copy_out(void* dst, const void* src_dev, size_t bytes, int mem_space, cudaStream_t s) {
+  if (bytes == 0) return PGO_OK;
+  cudaMemcpyKind kind = mem_space == PGO_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  CUDA_TRY(cudaMemcpyAsync(dst, src_dev, bytes, kind, s));
+  if (mem_space != PGO_MEM_DEVICE) CUDA_TRY(cudaStreamSynchronize(s));
+  return PGO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* pgo_last_error(void) { return g_last_error.c_str(); }
+
+const char* pgo_version(void) { return "pgo-gb300 0.1 (sm_103a)"; }
+
+// Test hook (not in the public header): cap device allocations in bytes.
+void pgo_test_set_alloc_limit(size_t bytes) { g_alloc_limit = bytes; }
+
+pgo_status pgo_default_options(pgo_solve_options* opt) {
+  if (!opt) return fail(PGO_ERR_INVALID_ARG, "opt is NULL");
+  opt->max_iters = 20;
+  opt->precision = PGO_FP64;
+  opt->tau = 1e-5;
+  opt->lambda_init = 0.0;
+  opt->ftol = 1e-14;
+  opt->gtol = 1e-13;
+  opt->pcg_tol = 1e-10;
+  opt->pcg_max_iters = 5000;
+  opt->refine_steps = 3;
+  opt->refine_tol = 1e-5;
+  opt->polish_iters = 0;
+  opt->schedule = -1;
+  return PGO_OK;
+}
+
+pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
+  if (!out) return fail(PGO_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(PGO_ERR_INVALID_ARG, "desc is NULL");
+  const int N = d->n_vertices, E = d->n_edges;
+  if (N < 1) return fail(PGO_ERR_INVALID_ARG, "n_vertices must be >= 1 (got %d)", N);
+  if (E < 0) return fail(PGO_ERR_INVALID_ARG, "n_edges must be >= 0 (got %d)", E);
+  if (d->fixed_vertex < 0 || d->fixed_vertex >= N)
+    return fail(PGO_ERR_INVALID_ARG, "fixed_vertex %d out of range [0, %d)", d->fixed_vertex, N);
+  if (d->mem_space != PGO_MEM_HOST && d->mem_space != PGO_MEM_DEVICE)
+    return fail(PGO_ERR_INVALID_ARG, "mem_space must be PGO_MEM_HOST or PGO_MEM_DEVICE");
+  if (E > 0 && (!d->edge_i || !d->edge_j || !d->meas)) return fail(PGO_ERR_INVALID_ARG, "edge arrays are NULL");
+  if ((long long)E * 2 > 0x7fffffffLL) return fail(PGO_ERR_INVALID_ARG, "too many edges");
+  const int ms = d->mem_space;
+  std::vector<int32_t> ei, ej;
+  std::vector<double> meas, w, info, poses;
+  if (!fetch(ei, d->edge_i, E, ms) || !fetch(ej, d->edge_j, E, ms) || !fetch(meas, d->meas, (size_t)E * 8, ms))
+    return fail(PGO_ERR_CUDA, "reading the edge arrays failed");
+  if (d->weight && !fetch(w, d->weight, E, ms)) return fail(PGO_ERR_CUDA, "reading weights failed");
+  if (d->info && !fetch(info, d->info, (size_t)E * 49, ms)) return fail(PGO_ERR_CUDA, "reading info failed");
+  if (d->poses && !fetch(poses, d->poses, (size_t)N * 8, ms)) return fail(PGO_ERR_CUDA, "reading poses failed");
+  for (int e = 0; e < E; ++e) {
+    if (ei[e] < 0 || ei[e] >= N || ej[e] < 0 || ej[e] >= N)
+      return fail(PGO_ERR_INVALID_ARG, "edge %d: endpoint out of range (%d, %d), n_vertices %d", e, ei[e], ej[e], N);
+    if (ei[e] == ej[e]) return fail(PGO_ERR_INVALID_ARG, "edge %d is a self-edge (%d, %d)", e, ei[e], ej[e]);
+    if (!finite_pose(&meas[(size_t)e * 8]))
+      return fail(PGO_ERR_INVALID_ARG, "edge %d: measurement not finite, zero quaternion or scale <= 0", e);
+    if (d->weight && !(std::isfinite(w[e]) && w[e] >= 0.0))
+      return fail(PGO_ERR_INVALID_ARG, "edge %d: weight must be finite and >= 0", e);
+  }
+  if (d->poses)
+    for (int v = 0; v < N; ++v)
+      if (!finite_pose(&poses[(size_t)v * 8]))
+        return fail(PGO_ERR_INVALID_ARG, "vertex %d: pose not finite, zero quaternion or scale <= 0", v);
+  std::vector<double> Lpack;
+  if (d->info) {
+    Lpack.resize((size_t)E * 28);
+    for (int e = 0; e < E; ++e)
+      if (!chol_pack(&info[(size_t)e * 49], &Lpack[(size_t)e * 28]))
+        return fail(PGO_ERR_INVALID_ARG, "edge %d: information matrix is not symmetric positive definite", e);
+  }
+
+  // internal edge order: by (min endpoint, max endpoint, caller index)
+  std::vector<int> perm(E);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
+    const int la = std::min(ei[a], ej[a]), lb = std::min(ei[b], ej[b]);
+    if (la != lb) return la < lb;
+    return std::max(ei[a], ej[a]) < std::max(ei[b], ej[b]);
+  });
+  std::vector<int> sei(E), sej(E);
+  std::vector<D4> zq(E), zt(E);
+  std::vector<double> sw(E), sL(d->info ? (size_t)E * 28 : 0);
+  for (int k = 0; k < E; ++k) {
+    const int e = perm[k];
+    sei[k] = ei[e];
+    sej[k] = ej[e];
+    const double* m = &meas[(size_t)e * 8];
+    const double n = std::sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2] + m[3] * m[3]);
+    zq[k] = D4{m[0] / n, m[1] / n, m[2] / n, m[3] / n};
+    zt[k] = D4{m[4], m[5], m[6], m[7]};
+    sw[k] = d->weight ? w[e] : 1.0;
+    if (d->info) std::memcpy(&sL[(size_t)k * 28], &Lpack[(size_t)e * 28], sizeof(double) * 28);
+  }
+  // incidence lists: for each vertex its side-0 entries (vertex is i), then
+  // its side-1 entries (vertex is j), each group in edge order
+  std::vector<int> inc_ptr(N + 1, 0), inc_split(N), inc_code((size_t)2 * E), inc_other((size_t)2 * E);
+  std::vector<int> deg0(N, 0);
+  for (int k = 0; k < E; ++k) {
+    inc_ptr[sei[k] + 1]++;
+    inc_ptr[sej[k] + 1]++;
+    deg0[sei[k]]++;
+  }
+  for (int v = 0; v < N; ++v) inc_ptr[v + 1] += inc_ptr[v];
+  {
+    std::vector<int> fill0(N), fill1(N);
+    for (int v = 0; v < N; ++v) {
+      fill0[v] = inc_ptr[v];
+      inc_split[v] = fill1[v] = inc_ptr[v] + deg0[v];
+    }
+    for (int k = 0; k < E; ++k) {
+      const int a = fill0[sei[k]]++;
+      inc_code[a] = 2 * k;
+      inc_other[a] = sej[k];
+      const int b2 = fill1[sej[k]]++;
+      inc_code[b2] = 2 * k + 1;
+      inc_other[b2] = sei[k];
+    }
+  }
+
+  pgo_graph* G = new pgo_graph();
+  G->N = N;
+  G->E = E;
+  G->fixed = d->fixed_vertex;
+  G->stream = (cudaStream_t)d->stream;
+  G->has_info = d->info != nullptr;
+  const size_t Ep = E > 0 ? E : 1;
+  const int pcap = std::max(max_partials(N, E), pcg_partials_needed(N));
+  G->scratch_doubles = std::max((size_t)N * 8, (size_t)Ep * 98) + std::max((size_t)N * 49, (size_t)Ep * 49);
+  size_t total = 0;
+  total += 2 * arena_bytes<int>(Ep) + 2 * arena_bytes<D4>(Ep) + arena_bytes<double>(Ep);
+  total += d->info ? arena_bytes<double>(Ep * 28) : 0;
+  total += arena_bytes<int>(N + 1) + arena_bytes<int>(N) + 2 * arena_bytes<int>(2 * Ep) + arena_bytes<int>(Ep);
+  total += 4 * arena_bytes<D4>(N);
+  total += arena_bytes<double>(Ep * BLK64) + arena_bytes<float>(Ep * BLK32);
+  total += 2 * arena_bytes<double>((size_t)N * BLK64) + 2 * arena_bytes<float>((size_t)N * BLK32);
+  total += arena_bytes<double>((size_t)N * VEC) + arena_bytes<double>(Ep * 2 * CONTRIB);
+  total += 8 * arena_bytes<double>((size_t)N * VEC) + 6 * arena_bytes<float>((size_t)N * VEC);
+  total += arena_bytes<double>((size_t)pcap * 4) + arena_bytes<SolverState>(1) + arena_bytes<DevOptions>(1);
+  total += arena_bytes<double>(G->scratch_doubles) + arena_bytes<double>(8);
+  auto cleanup = [&](pgo_status st) {
+    pgo_graph_destroy(G);
+    return st;
+  };
+  if (g_alloc_limit && total > g_alloc_limit)
+    return cleanup(fail(PGO_ERR_OOM, "device allocation of %zu bytes exceeds the test limit", total));
+  cudaError_t ce = cudaMalloc(&G->arena.base, total);
+  if (ce != cudaSuccess) {
+    G->arena.base = nullptr;
+    cudaGetLastError();
+    return cleanup(fail(ce == cudaErrorMemoryAllocation ? PGO_ERR_OOM : PGO_ERR_CUDA,
+                        "cudaMalloc(%zu): %s", total, cudaGetErrorString(ce)));
+  }
+  G->arena.size = total;
+  Arena& A = G->arena;
+  DevGraph& g = G->g;
+  g.N = N;
+  g.E = E;
+  g.fixed = d->fixed_vertex;
+  int* d_ei = A.take<int>(Ep);
+  int* d_ej = A.take<int>(Ep);
+  D4* d_zq = A.take<D4>(Ep);
+  D4* d_zt = A.take<D4>(Ep);
+  double* d_w = A.take<double>(Ep);
+  double* d_L = d->info ? A.take<double>(Ep * 28) : nullptr;
+  int* d_ptr = A.take<int>(N + 1);
+  int* d_split = A.take<int>(N);
+  int* d_code = A.take<int>(2 * Ep);
+  int* d_other = A.take<int>(2 * Ep);
+  G->d_perm = A.take<int>(Ep);
+  g.ei = d_ei; g.ej = d_ej; g.zq = d_zq; g.zt = d_zt; g.w = d_w; g.L = d_L;
+  g.inc_ptr = d_ptr; g.inc_code = d_code; g.inc_other = d_other; g.inc_split = d_split;
+  for (int k = 0; k < 2; ++k) { g.pq[k] = A.take<D4>(N); g.pt[k] = A.take<D4>(N); }
+  g.off64 = A.take<double>(Ep * BLK64);
+  g.off32 = A.take<float>(Ep * BLK32);
+  g.diag64 = A.take<double>((size_t)N * BLK64);
+  g.minv64 = A.take<double>((size_t)N * BLK64);
+  g.diag32 = A.take<float>((size_t)N * BLK32);
+  g.minv32 = A.take<float>((size_t)N * BLK32);
+  g.b = A.take<double>((size_t)N * VEC);
+  g.contrib = A.take<double>(Ep * 2 * CONTRIB);
+  g.x64 = A.take<double>((size_t)N * VEC);
+  g.r64 = A.take<double>((size_t)N * VEC);
+  g.z64 = A.take<double>((size_t)N * VEC);
+  g.p64[0] = A.take<double>((size_t)N * VEC);
+  g.p64[1] = A.take<double>((size_t)N * VEC);
+  g.q64 = A.take<double>((size_t)N * VEC);
+  g.dx64 = A.take<double>((size_t)N * VEC);
+  g.res64 = A.take<double>((size_t)N * VEC);
+  g.x32 = A.take<float>((size_t)N * VEC);
+  g.r32 = A.take<float>((size_t)N * VEC);
+  g.z32 = A.take<float>((size_t)N * VEC);
+  g.p32[0] = A.take<float>((size_t)N * VEC);
+  g.p32[1] = A.take<float>((size_t)N * VEC);
+  g.q32 = A.take<float>((size_t)N * VEC);
+  g.partial = A.take<double>((size_t)pcap * 4);
+  g.partial_cap = pcap;
+  g.st = A.take<SolverState>(1);
+  g.opt = A.take<DevOptions>(1);
+  G->d_scratch = A.take<double>(G->scratch_doubles);
+  G->d_cost = A.take<double>(8);
+  if (A.used > A.size) return cleanup(fail(PGO_ERR_CUDA, "internal arena overflow"));
+
+  cudaStream_t s = G->stream;
+  if (cudaStreamCreateWithFlags(&G->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&G->ev0) != cudaSuccess || cudaEventCreate(&G->ev1) != cudaSuccess ||
+      cudaMallocHost(&G->h_state, sizeof(SolverState)) != cudaSuccess ||
+      cudaMallocHost(&G->h_opt, sizeof(DevOptions)) != cudaSuccess)
+    return cleanup(fail(PGO_ERR_CUDA, "creating streams/events/pinned buffers failed"));
+  bool ok = true;
+  ok &= cudaMemsetAsync(A.base, 0, A.used, s) == cudaSuccess;
+  ok &= copy_in(d_ei, sei.data(), sizeof(int) * E, PGO_MEM_HOST, s);
+  ok &= copy_in(d_ej, sej.data(), sizeof(int) * E, PGO_MEM_HOST, s);
+  ok &= copy_in(d_zq, zq.data(), sizeof(D4) * E, PGO_MEM_HOST, s);
+  ok &= copy_in(d_zt, zt.data(), sizeof(D4) * E, PGO_MEM_HOST, s);
+  ok &= copy_in(d_w, sw.data(), sizeof(double) * E, PGO_MEM_HOST, s);
+  if (d->info) ok &= copy_in(d_L, sL.data(), sizeof(double) * 28 * E, PGO_MEM_HOST, s);
+  ok &= copy_in(d_ptr, inc_ptr.data(), sizeof(int) * (N + 1), PGO_MEM_HOST, s);
+  ok &= copy_in(d_split, inc_split.data(), sizeof(int) * N, PGO_MEM_HOST, s);
+  ok &= copy_in(d_code, inc_code.data(), sizeof(int) * 2 * E, PGO_MEM_HOST, s);
+  ok &= copy_in(d_other, inc_other.data(), sizeof(int) * 2 * E, PGO_MEM_HOST, s);
+  ok &= copy_in(G->d_perm, perm.data(), sizeof(int) * E, PGO_MEM_HOST, s);
+  if (!ok) return cleanup(fail(PGO_ERR_CUDA, "uploading the graph failed"));
+  // identity poses by default, then the caller's initial estimate
+  {
+    std::vector<double> init((size_t)N * 8, 0.0);
+    for (int v = 0; v < N; ++v) { init[(size_t)v * 8 + 3] = 1.0; init[(size_t)v * 8 + 7] = 1.0; }
+    const double* src = d->poses ? poses.data() : init.data();
+    if (!copy_in(G->d_scratch, src, sizeof(double) * 8 * N, PGO_MEM_HOST, s))
+      return cleanup(fail(PGO_ERR_CUDA, "uploading poses failed"));
+    launch_set_poses(g, G->d_scratch, 0, s);
+  }
+  pgo_solve_options def;
+  pgo_default_options(&def);
+  fill_dev_options(def, G->h_opt);
+  if (!copy_in(g.opt, G->h_opt, sizeof(DevOptions), PGO_MEM_HOST, s))
+    return cleanup(fail(PGO_ERR_CUDA, "uploading options failed"));
+  ce = cudaStreamSynchronize(s);
+  if (ce != cudaSuccess) return cleanup(fail(PGO_ERR_CUDA, "graph upload: %s", cudaGetErrorString(ce)));
+  *out = G;
+  return PGO_OK;
+}
+
+void pgo_graph_destroy(pgo_graph* G) {
+  if (!G) return;
+  if (G->stream || G->arena.base) cudaStreamSynchronize(G->stream);
+  for (auto& kv : G->execs) cudaGraphExecDestroy(kv.second);
+  if (G->cap_stream) cudaStreamDestroy(G->cap_stream);
+  if (G->ev0) cudaEventDestroy(G->ev0);
+  if (G->ev1) cudaEventDestroy(G->ev1);
+  if (G->h_state) cudaFreeHost(G->h_state);
+  if (G->h_opt) cudaFreeHost(G->h_opt);
+  if (G->arena.base) cudaFree(G->arena.base);
+  delete G;
+}
+
+pgo_status pgo_graph_set_poses(pgo_graph* G, const double* poses, int32_t mem_space) {
+  if (!G || !poses) return fail(PGO_ERR_INVALID_ARG, "graph or poses is NULL");
+  if (mem_space != PGO_MEM_HOST && mem_space != PGO_MEM_DEVICE) return fail(PGO_ERR_INVALID_ARG, "bad mem_space");
+  cudaStream_t s = G->stream;
+  if (mem_space == PGO_MEM_DEVICE) {
+    // device poses are copied on the stream without a host round trip (and
+    // without host-side validation; a non-finite pose makes the next solve
+    // stop with PGO_ERR_NUMERICAL)
+    launch_set_poses(G->g, poses, -1, s);
+    CUDA_TRY(cudaGetLastError());
+    G->solved = false;
+    return PGO_OK;
+  }
+  for (int v = 0; v < G->N; ++v)
+    if (!finite_pose(&poses[(size_t)v * 8]))
+      return fail(PGO_ERR_INVALID_ARG, "vertex %d: pose not finite, zero quaternion or scale <= 0", v);
+  CUDA_TRY(cudaMemcpyAsync(G->d_scratch, poses, sizeof(double) * 8 * G->N, cudaMemcpyHostToDevice, s));
+  launch_set_poses(G->g, G->d_scratch, -1, s);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaStreamSynchronize(s));   // the host buffer may be reused on return
+  G->solved = false;
+  return PGO_OK;
+}
+
+static pgo_status current_buf(pgo_graph* G, int* buf) {
+  CUDA_TRY(cudaMemcpyAsync(G->h_state, G->g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, G->stream));
+  CUDA_TRY(cudaStreamSynchronize(G->stream));
+  *buf = G->h_state->cur;
+  return PGO_OK;
+}
+
+pgo_status pgo_graph_get_poses(pgo_graph* G, double* poses, int32_t mem_space) {
+  if (!G || !poses) return fail(PGO_ERR_INVALID_ARG, "graph or poses is NULL");
+  int buf = 0;
+  pgo_status st = current_buf(G, &buf);
+  if (st != PGO_OK) return st;
+  launch_get_poses(G->g, buf, G->d_scratch, G->stream);
+  CUDA_TRY(cudaGetLastError());
+  return copy_out(poses, G->d_scratch, sizeof(double) * 8 * G->N, mem_space, G->stream);
+}
+
+pgo_status pgo_graph_cost(pgo_graph* G, double* cost, double* residuals, int32_t mem_space) {
+  if (!G || !cost) return fail(PGO_ERR_INVALID_ARG, "graph or cost is NULL");
+  int buf = 0;
+  pgo_status st = current_buf(G, &buf);
+  if (st != PGO_OK) return st;
+  double* rdev = nullptr;
+  if (residuals) rdev = mem_space == PGO_MEM_DEVICE ? residuals : G->d_scratch;
+  launch_residuals(G->g, buf, G->d_perm, rdev, G->d_cost, G->stream);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(cost, G->d_cost, sizeof(double), cudaMemcpyDeviceToHost, G->stream));
+  CUDA_TRY(cudaStreamSynchronize(G->stream));
+  if (residuals && mem_space != PGO_MEM_DEVICE) return copy_out(residuals, rdev, sizeof(double) * 7 * G->E, mem_space, G->stream);
+  return PGO_OK;
+}
+
+// Load a state for a standalone linearisation / linear solve at `lambda`.
+static pgo_status prepare_standalone(pgo_graph* G, const pgo_solve_options& o, double lambda) {
+  int buf = 0;
+  pgo_status st = current_buf(G, &buf);
+  if (st != PGO_OK) return st;
+  SolverState* h = G->h_state;
+  std::memset(h, 0, sizeof(SolverState));
+  h->cur = buf;
+  h->need_lin = 1;
+  h->lambda = lambda;
+  h->nu = 2.0;
+  fill_dev_options(o, G->h_opt);
+  G->h_opt->gtol = -1.0;   // never stop on the gradient here
+  CUDA_TRY(cudaMemcpyAsync(G->g.st, h, sizeof(SolverState), cudaMemcpyHostToDevice, G->stream));
+  CUDA_TRY(cudaMemcpyAsync(G->g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, G->stream));
+  return PGO_OK;
+}
+
+pgo_status pgo_graph_linearize(pgo_graph* G, int32_t precision, double* jac, double* h_diag, double* h_off,
+                               double* b, int32_t mem_space) {
+  if (!G) return fail(PGO_ERR_INVALID_ARG, "graph is NULL");
+  if (precision != PGO_FP64 && precision != PGO_MIXED) return fail(PGO_ERR_INVALID_ARG, "bad precision");
+  pgo_solve_options o;
+  pgo_default_options(&o);
+  pgo_status st = prepare_standalone(G, o, 1.0);
+  if (st != PGO_OK) return st;
+  cudaStream_t s = G->stream;
+  const DevGraph& g = G->g;
+  launch_linearize(g, precision == PGO_MIXED, s);
+  launch_assemble(g, precision == PGO_MIXED, s);
+  CUDA_TRY(cudaGetLastError());
+  const int E = G->E, N = G->N;
+  double* tmp = G->d_scratch;
+  if (jac) {
+    double* dst = mem_space == PGO_MEM_DEVICE ? jac : tmp;
+    launch_jacobians_out(g, G->h_state->cur, G->d_perm, dst, s);
+    CUDA_TRY(cudaGetLastError());
+    if (mem_space != PGO_MEM_DEVICE) { st = copy_out(jac, tmp, sizeof(double) * 98 * E, mem_space, s); if (st) return st; }
+  }
+  if (h_off) {
+    double* dst = mem_space == PGO_MEM_DEVICE ? h_off : tmp;
+    launch_scatter(E, 49, G->d_perm, g.off64, BLK64, dst, 49, s);
+    CUDA_TRY(cudaGetLastError());
+    if (mem_space != PGO_MEM_DEVICE) { st = copy_out(h_off, tmp, sizeof(double) * 49 * E, mem_space, s); if (st) return st; }
+  }
+  if (h_diag) {
+    double* dst = mem_space == PGO_MEM_DEVICE ? h_diag : tmp;
+    launch_scatter(N, 49, nullptr, g.diag64, BLK64, dst, 49, s);
+    CUDA_TRY(cudaGetLastError());
+    if (mem_space != PGO_MEM_DEVICE) { st = copy_out(h_diag, tmp, sizeof(double) * 49 * N, mem_space, s); if (st) return st; }
+  }
+  if (b) {
+    double* dst = mem_space == PGO_MEM_DEVICE ? b : tmp;
+    launch_scatter(N, 7, nullptr, g.b, VEC, dst, 7, s);
+    CUDA_TRY(cudaGetLastError());
+    if (mem_space != PGO_MEM_DEVICE) { st = copy_out(b, tmp, sizeof(double) * 7 * N, mem_space, s); if (st) return st; }
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  return PGO_OK;
+}
+
+pgo_status pgo_graph_damped_step(pgo_graph* G, const pgo_solve_options* opt, double lambda, double* delta,
+                                 int32_t* pcg_iters, int32_t mem_space) {
+  if (!G || !delta) return fail(PGO_ERR_INVALID_ARG, "graph or delta is NULL");
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(PGO_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+  pgo_solve_options o;
+  if (opt) o = *opt; else pgo_default_options(&o);
+  pgo_status st = check_options(o);
+  if (st != PGO_OK) return st;
+  const int mixed = o.precision == PGO_MIXED;
+  cudaGraphExec_t ex;
+  st = get_exec(G, 1, mixed, o.refine_steps, &ex);
+  if (st != PGO_OK) return st;
+  st = prepare_standalone(G, o, lambda);
+  if (st != PGO_OK) return st;
+  cudaStream_t s = G->stream;
+  CUDA_TRY(cudaGraphLaunch(ex, s));
+  launch_scatter(G->N, 7, nullptr, mixed ? G->g.dx64 : G->g.x64, VEC, G->d_scratch, 7, s);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(G->h_state, G->g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  st = copy_out(delta, G->d_scratch, sizeof(double) * 7 * G->N, mem_space, s);
+  if (st != PGO_OK) return st;
+  if (pcg_iters) *pcg_iters = G->h_state->pcg_total;
+  if (G->h_state->pcg_hit_cap) return fail(PGO_ERR_NOT_CONVERGED, "PCG reached pcg_max_iters (%d)", o.pcg_max_iters);
+  return PGO_OK;
+}
+
+pgo_status pgo_graph_resolve(pgo_graph* G, const pgo_solve_options* opt, double lambda, double* delta,
+                             int32_t* pcg_iters, int32_t mem_space) {
+  if (!G) return fail(PGO_ERR_INVALID_ARG, "graph is NULL");
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(PGO_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+  pgo_solve_options o;
+  if (opt) o = *opt; else pgo_default_options(&o);
+  pgo_status st = check_options(o);
+  if (st != PGO_OK) return st;
+  const int mixed = o.precision == PGO_MIXED;
+  cudaGraphExec_t ex;
+  st = get_exec(G, 2, mixed, o.refine_steps, &ex);
+  if (st != PGO_OK) return st;
+  cudaStream_t s = G->stream;
+  fill_dev_options(o, G->h_opt);
+  G->h_opt->lambda_fixed = lambda;
+  CUDA_TRY(cudaMemcpyAsync(G->g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaGraphLaunch(ex, s));
+  if (!delta && !pcg_iters) return PGO_OK;
+  if (delta) {
+    launch_scatter(G->N, 7, nullptr, mixed ? G->g.dx64 : G->g.x64, VEC, G->d_scratch, 7, s);
+    CUDA_TRY(cudaGetLastError());
+  }
+  CUDA_TRY(cudaMemcpyAsync(G->h_state, G->g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (delta) {
+    st = copy_out(delta, G->d_scratch, sizeof(double) * 7 * G->N, mem_space, s);
+    if (st != PGO_OK) return st;
+  }
+  if (pcg_iters) *pcg_iters = G->h_state->pcg_total;
+  if (G->h_state->status) return fail((pgo_status)G->h_state->status, "re-solve failed on the device");
+  if (G->h_state->pcg_hit_cap) return fail(PGO_ERR_NOT_CONVERGED, "PCG reached pcg_max_iters (%d)", o.pcg_max_iters);
+  return PGO_OK;
+}
+
+static void fill_report(pgo_graph* G, pgo_report* report) {
+  const SolverState* h = G->h_state;
+  std::memset(report, 0, sizeof(*report));
+  report->initial_cost = h->F0;
+  report->final_cost = h->F;
+  report->final_lambda = h->lambda;
+  report->grad_inf_norm = h->gmax;
+  report->iterations = h->it;
+  report->accepted = h->accepted;
+  report->pcg_iterations = h->pcg_total;
+  report->stop_reason = h->stop_reason;
+  report->status = h->status;
+  float ms = 0.f;
+  if (cudaEventElapsedTime(&ms, G->ev0, G->ev1) != cudaSuccess) {
+    cudaGetLastError();
+    ms = 0.f;
+  }
+  report->ms_total = ms;
+}
+
+pgo_status pgo_graph_report(pgo_graph* G, pgo_report* report) {
+  if (!G || !report) return fail(PGO_ERR_INVALID_ARG, "graph or report is NULL");
+  if (!G->solved) return fail(PGO_ERR_STATE, "no solve has run on this graph");
+  CUDA_TRY(cudaMemcpyAsync(G->h_state, G->g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, G->stream));
+  CUDA_TRY(cudaStreamSynchronize(G->stream));
+  fill_report(G, report);
+  if (report->status) return fail((pgo_status)report->status, "the solve failed on the device (status %d)", report->status);
+  return PGO_OK;
+}
+
+pgo_status pgo_solve(pgo_graph* G, const pgo_solve_options* opt, pgo_report* report, double* poses_out,
+                     int32_t out_mem_space) {
+  if (!G) return fail(PGO_ERR_INVALID_ARG, "graph is NULL");
+  pgo_solve_options o;
+  if (opt) o = *opt; else pgo_default_options(&o);
+  pgo_status st = check_options(o);
+  if (st != PGO_OK) return st;
+  if (poses_out && out_mem_space != PGO_MEM_HOST && out_mem_space != PGO_MEM_DEVICE)
+    return fail(PGO_ERR_INVALID_ARG, "bad out_mem_space");
+  const int mixed = o.precision == PGO_MIXED;
+  const bool eager = o.schedule == 1;
+  cudaGraphExec_t ex = nullptr;
+  if (!eager) {
+    st = get_exec(G, 0, mixed, o.refine_steps, &ex);
+    if (st != PGO_OK) return st;
+  }
+  cudaStream_t s = G->stream;
+  fill_dev_options(o, G->h_opt);
+  CUDA_TRY(cudaMemcpyAsync(G->g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaEventRecord(G->ev0, s));
+  if (eager) {
+    st = run_eager(G, mixed, o.refine_steps, o.max_iters);
+    if (st != PGO_OK) return st;
+  } else {
+    CUDA_TRY(cudaGraphLaunch(ex, s));
+  }
+  CUDA_TRY(cudaEventRecord(G->ev1, s));
+  G->solved = true;
+  if (poses_out) {
+    // the current buffer is only known on the device: gather both and let
+    // the device pick (k_get_poses reads st->cur through launch_get_poses)
+    CUDA_TRY(cudaMemcpyAsync(G->h_state, G->g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    launch_get_poses(G->g, G->h_state->cur, G->d_scratch, s);
+    CUDA_TRY(cudaGetLastError());
+    st = copy_out(poses_out, G->d_scratch, sizeof(double) * 8 * G->N, out_mem_space, s);
+    if (st != PGO_OK) return st;
+  }
+  if (report) {
+    CUDA_TRY(cudaMemcpyAsync(G->h_state, G->g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    fill_report(G, report);
+    if (report->status)
+      return fail((pgo_status)report->status, "solve failed on the device (status %d, stop reason %d)",
+                  report->status, report->stop_reason);
+  }
+  return PGO_OK;
+}
+
+pgo_status pgo_backward(pgo_graph* G, const pgo_solve_options*, const double*, int32_t, double*, double*, int32_t) {
+  if (!G) return fail(PGO_ERR_INVALID_ARG, "graph is NULL");
+  if (!G->solved) return fail(PGO_ERR_STATE, "pgo_backward needs a completed pgo_solve");
+  return fail(PGO_ERR_STATE, "pgo_backward is not available in this build");
+}
+
+pgo_status pgo_batch_create(int32_t, const pgo_graph_desc*, void*, pgo_batch** out) {
+  if (out) *out = nullptr;
+  return fail(PGO_ERR_STATE, "batched solve is not available in this build");
+}
+void pgo_batch_destroy(pgo_batch* b) { delete b; }
+pgo_status pgo_batch_solve(pgo_batch*, const pgo_solve_options*, pgo_report*, double* const*, int32_t) {
+  return fail(PGO_ERR_STATE, "batched solve is not available in this build");
+}
+
+pgo_status pgo_evaluate_cost(int32_t n_vertices, int32_t n_edges, const int32_t* edge_i, const int32_t* edge_j,
+                             const double* meas, const double* weight, const double* poses, double* cost_out,
+                             void* stream) {
+  if (n_vertices < 0 || n_edges < 0) return fail(PGO_ERR_INVALID_ARG, "negative size");
+  if (!cost_out) return fail(PGO_ERR_INVALID_ARG, "cost_out is NULL");
+  if (n_edges > 0 && (!edge_i || !edge_j || !meas || !poses)) return fail(PGO_ERR_INVALID_ARG, "NULL input array");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int blocks = eval_cost_blocks(n_edges);
+  // workspace: partials (blocks doubles) + ticket + bad counter
+  const size_t bytes = sizeof(double) * blocks + 64;
+  void* ws = nullptr;
+  CUDA_TRY(cudaMallocAsync(&ws, bytes, s));
+  double* partial = reinterpret_cast<double*>(ws);
+  unsigned* ticket = reinterpret_cast<unsigned*>(reinterpret_cast<char*>(ws) + sizeof(double) * blocks);
+  int* bad = reinterpret_cast<int*>(ticket + 4);
+  cudaError_t e = cudaMemsetAsync(ticket, 0, 64, s);
+  if (e == cudaSuccess) {
+    launch_eval_cost_raw(n_vertices, n_edges, edge_i, edge_j, meas, weight, poses, partial, ticket, bad, cost_out, s);
+    e = cudaGetLastError();
+  }
+  cudaError_t e2 = cudaFreeAsync(ws, s);
+  if (e != cudaSuccess) return fail(PGO_ERR_CUDA, "pgo_evaluate_cost: %s", cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return fail(PGO_ERR_CUDA, "pgo_evaluate_cost free: %s", cudaGetErrorString(e2));
+  return PGO_OK;
+}
+
+}  // extern "C"

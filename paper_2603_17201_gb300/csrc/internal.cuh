@@ -1,0 +1,118 @@
+// Internal device data structures and kernel launchers of the GB300 Sim(3)
+// essential-graph optimiser.  Not part of the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/pgo.h"
+
+namespace pgo {
+
+// 32-byte aligned 4-vector of doubles (one 256-bit access).
+struct alignas(32) D4 {
+  double x, y, z, w;
+};
+
+// Padded block strides (elements): 7x7 row-major blocks padded so every block
+// starts on a 16-byte boundary for vector loads.
+constexpr int BLK64 = 50;   // doubles per FP64 block (400 B)
+constexpr int BLK32 = 52;   // floats per FP32 block (208 B)
+constexpr int VEC = 8;      // per-vertex vector stride (7 used, 1 zero pad)
+constexpr int CONTRIB = 36; // per edge-side: 28 upper-triangular H entries + 7 b + pad
+
+// Reduction tickets (one per reducing kernel family).
+enum Ticket {
+  T_ASSEMBLE = 0, T_PCG_INIT, T_PCG_SPMV, T_PCG_UPDATE, T_UPDATE, T_COST, T_REFINE,
+  T_COST_STATELESS, T_POLISH, T_MISC, T_COUNT
+};
+
+// Device-resident solver state (LM + PCG scalars); one per graph.
+struct SolverState {
+  double F0;        // cost at the start of the solve
+  double F;         // cost at the current estimate
+  double F_new;     // cost at the candidate
+  double lambda, nu;
+  double pred;      // predicted decrease delta^T (lambda delta - b)
+  double gmax;      // |b|_inf (free vertices)
+  double maxdiag;   // max diag(H) (free vertices)
+  double bnorm2;    // |b|^2 of the LM right-hand side
+  double rz, pq, alpha, beta, rr, bb;   // PCG scalars (current linear solve)
+  double ref_rr;    // mixed: FP64 residual norm^2 of the refined solution
+  int it, accepted, done, need_lin, stop_reason, status, cur, pcg_total;
+  int pcg_iter, pcg_done, pcg_hit_cap, ref_done;
+  int polish_it, polish_done;
+  unsigned ticket[T_COUNT];
+};
+
+// Options as read by the kernels (copied from pgo_solve_options per solve).
+struct DevOptions {
+  int max_iters, precision, pcg_max_iters, refine_steps, polish_iters;
+  double tau, lambda_init, ftol, gtol, pcg_tol, refine_tol;
+  double lambda_fixed;   // lambda of a standalone re-solve
+};
+
+// Device view of one graph.
+struct DevGraph {
+  int N, E, fixed;
+  const int* ei;          // internal (sorted) edge order
+  const int* ej;
+  const D4* zq;           // measurement quaternion (x, y, z, w), normalised
+  const D4* zt;           // measurement (tx, ty, tz, s)
+  const double* w;        // weight per edge
+  const double* L;        // E x 28 lower-triangular factor of Omega, or nullptr
+  const int* inc_ptr;     // N + 1: incidence CSR over vertices
+  const int* inc_code;    // 2E: edge * 2 + side (0: vertex is i, 1: vertex is j)
+  const int* inc_other;   // 2E: the other endpoint
+  const int* inc_split;   // N: first entry of the vertex's side-1 (v is j) entries;
+                          //    each vertex lists its side-0 entries first
+  D4* pq[2];              // pose buffers (current = pq[cur])
+  D4* pt[2];
+  // normal equations
+  double* off64;          // E x BLK64  (i, j) block w A_i^T Omega A_j
+  float* off32;           // E x BLK32  (mixed)
+  double* diag64;         // N x BLK64  H_vv (undamped)
+  float* diag32;          // N x BLK32
+  double* b;              // N x VEC
+  double* contrib;        // E x 2 x CONTRIB per-edge-side contributions
+  // preconditioner (explicit inverse of the damped diagonal block)
+  double* minv64;         // N x BLK64
+  float* minv32;          // N x BLK32
+  // PCG vectors (FP64 and FP32 sets)
+  double *x64, *r64, *z64, *p64[2], *q64;
+  float *x32, *r32, *z32, *p32[2], *q32;
+  double* dx64;           // mixed: accumulated FP64 solution
+  double* res64;          // mixed: FP64 refinement residual
+  double* partial;        // reduction partials (max blocks)
+  int partial_cap;
+  SolverState* st;
+  DevOptions* opt;
+};
+
+// ---- launchers (each enqueues on `s`; inside stream capture they become
+// graph nodes).  `cond` is a graph conditional handle set by the last block
+// of the kernel, or 0 when the kernel is not inside a conditional body. ----
+void launch_cost(const DevGraph& g, int mode, cudaStream_t s, unsigned long long lm_cond);
+void launch_linearize(const DevGraph& g, int mixed, cudaStream_t s);
+void launch_assemble(const DevGraph& g, int mixed, cudaStream_t s);
+void launch_precond(const DevGraph& g, int mixed, cudaStream_t s);
+cudaError_t launch_pcg(const DevGraph& g, int mixed, int from_residual, cudaStream_t s);
+int pcg_partials_needed(int N);
+void launch_refine_residual(const DevGraph& g, int first, cudaStream_t s);
+void launch_refine_accumulate(const DevGraph& g, cudaStream_t s);
+void launch_update(const DevGraph& g, int mixed, cudaStream_t s);
+void launch_lm_reset(const DevGraph& g, cudaStream_t s);
+void launch_resolve_reset(const DevGraph& g, cudaStream_t s);
+int max_partials(int N, int E);
+void launch_set_poses(const DevGraph& g, const double* src, int buf, cudaStream_t s);
+void launch_get_poses(const DevGraph& g, int buf, double* dst, cudaStream_t s);
+void launch_residuals(const DevGraph& g, int buf, const int* perm, double* r_out, double* cost_out,
+                      cudaStream_t s);
+void launch_scatter(int n, int width, const int* perm, const double* src, int sstride, double* dst,
+                    int dstride, cudaStream_t s);
+void launch_jacobians_out(const DevGraph& g, int buf, const int* perm, double* out, cudaStream_t s);
+int eval_cost_blocks(int E);
+void launch_eval_cost_raw(int N, int E, const int* ei, const int* ej, const double* meas, const double* w,
+                          const double* poses, double* partial, unsigned* ticket, int* bad,
+                          double* cost_out, cudaStream_t s);
+
+}  // namespace pgo

@@ -1,0 +1,351 @@
+// Edge and vertex kernels of the Levenberg-Marquardt loop (Sec. IV-F):
+//   K1 k_linearize  edge residual r = log(Z S_i S_j^-1) and its exact
+//                   Jacobians (forward-mode duals through the log map),
+//                   the off-diagonal block and per-edge-side contributions;
+//   K2 k_assemble   deterministic per-vertex gather of the contributions into
+//                   the diagonal blocks H_vv and the gradient b_v;
+//   k_cost          F = sum w r^T Omega r (FP64) and the LM accept/reject rule;
+//   k_update        candidate poses exp(delta) S and the predicted decrease.
+#include <cfloat>
+
+#include "edge.cuh"
+
+namespace pgo {
+
+// packed upper-triangular index (a <= c) of a symmetric 7x7 block
+__device__ __forceinline__ int upk(int a, int c) { return a * 7 - (a * (a - 1)) / 2 + (c - a); }
+
+__constant__ unsigned char c_up_a[28] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 6};
+__constant__ unsigned char c_up_c[28] = {0, 1, 2, 3, 4, 5, 6, 1, 2, 3, 4, 5, 6, 2, 3, 4, 5, 6, 3, 4, 5, 6, 4, 5, 6, 5, 6, 6};
+
+// K1: one thread per edge.
+__global__ void __launch_bounds__(128) k_linearize(DevGraph g, int mixed) {
+  const SolverState* st = g.st;
+  if (st->done || !st->need_lin) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= g.E) return;
+  double r[7], Ai[7][7], Aj[7][7];
+  edge_jacobians(g, st->cur, e, r, Ai, Aj);
+  const double w = g.w[e];
+  // off-diagonal (i, j) block: w A_i^T A_j
+  double* off = g.off64 + (size_t)e * BLK64;
+  float* off32 = mixed ? g.off32 + (size_t)e * BLK32 : nullptr;
+#pragma unroll
+  for (int a = 0; a < 7; ++a) {
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) s += Ai[k][a] * Aj[k][c];
+      s *= w;
+      off[a * 7 + c] = s;
+      if (mixed) off32[a * 7 + c] = (float)s;
+    }
+  }
+  // per-side contributions: upper(w A^T A) and w A^T r
+  double* ci = g.contrib + (size_t)e * 2 * CONTRIB;
+  double* cj = ci + CONTRIB;
+#pragma unroll
+  for (int a = 0; a < 7; ++a) {
+#pragma unroll
+    for (int c = a; c < 7; ++c) {
+      double si = 0.0, sj = 0.0;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        si += Ai[k][a] * Ai[k][c];
+        sj += Aj[k][a] * Aj[k][c];
+      }
+      ci[upk(a, c)] = w * si;
+      cj[upk(a, c)] = w * sj;
+    }
+    double gi = 0.0, gj = 0.0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      gi += Ai[k][a] * r[k];
+      gj += Aj[k][a] * r[k];
+    }
+    ci[28 + a] = w * gi;
+    cj[28 + a] = w * gj;
+  }
+}
+
+// K2: 8 lanes per vertex gather the incident edge-side contributions in edge
+// order (deterministic), then write H_vv (full symmetric) and b_v.  The last
+// block derives max diag(H), |b|_inf and |b|^2 over the free vertices, sets
+// lambda_0 on the first linearisation and applies the gradient stop test.
+__global__ void __launch_bounds__(256) k_assemble(DevGraph g, int mixed) {
+  SolverState* st = g.st;
+  if (st->done || !st->need_lin) return;
+  __shared__ double sh[32 * 3];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = tid >> 3, lane = tid & 7;
+  double mdiag = 0.0, mgrad = 0.0, b2 = 0.0;
+  if (v < g.N) {
+    double acc[5] = {0, 0, 0, 0, 0};
+    const int k0 = g.inc_ptr[v], k1 = g.inc_ptr[v + 1];
+    for (int k = k0; k < k1; ++k) {
+      const int code = g.inc_code[k];
+      const double* src = g.contrib + (size_t)(code >> 1) * 2 * CONTRIB + (code & 1) * CONTRIB;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) {
+        const int u = lane + 8 * m;
+        if (u < CONTRIB) acc[m] += src[u];
+      }
+    }
+    const bool free_v = (v != g.fixed);
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const int u = lane + 8 * m;
+      if (u < 28) {
+        const int a = c_up_a[u], c = c_up_c[u];
+        g.diag64[(size_t)v * BLK64 + a * 7 + c] = acc[m];
+        g.diag64[(size_t)v * BLK64 + c * 7 + a] = acc[m];
+        if (mixed) {
+          g.diag32[(size_t)v * BLK32 + a * 7 + c] = (float)acc[m];
+          g.diag32[(size_t)v * BLK32 + c * 7 + a] = (float)acc[m];
+        }
+        if (a == c && free_v) mdiag = fmax(mdiag, acc[m]);
+      } else if (u < 35) {
+        g.b[(size_t)v * VEC + (u - 28)] = acc[m];
+        if (free_v) {
+          mgrad = fmax(mgrad, fabs(acc[m]));
+          b2 += acc[m] * acc[m];
+        }
+      } else if (u == 35) {
+        g.b[(size_t)v * VEC + 7] = 0.0;
+      }
+    }
+  }
+  double mx[2] = {mdiag, mgrad};
+  double sm[1] = {b2};
+  block_max<2>(mx, sh);
+  block_sum<1>(sm, sh + 64);
+  double part[3] = {mx[0], mx[1], sm[0]};
+  if (publish_partials<3>(part, g.partial, &st->ticket[T_ASSEMBLE])) {
+    double tot[3] = {0, 0, 0};
+    for (int b = threadIdx.x; b < gridDim.x; b += blockDim.x) {
+      tot[0] = fmax(tot[0], __ldcg(g.partial + b * 3 + 0));
+      tot[1] = fmax(tot[1], __ldcg(g.partial + b * 3 + 1));
+      tot[2] += __ldcg(g.partial + b * 3 + 2);
+    }
+    double m2[2] = {tot[0], tot[1]};
+    double s1[1] = {tot[2]};
+    block_max<2>(m2, sh);
+    block_sum<1>(s1, sh + 64);
+    if (threadIdx.x == 0) {
+      const DevOptions* o = g.opt;
+      st->maxdiag = m2[0];
+      st->gmax = m2[1];
+      st->bnorm2 = s1[0];
+      if (st->lambda < 0.0) st->lambda = (o->lambda_init > 0.0) ? o->lambda_init : o->tau * m2[0];
+      st->need_lin = 0;
+      if (!(m2[1] > o->gtol)) {
+        st->done = 1;
+        st->stop_reason = isfinite(m2[1]) ? 2 : 4;
+        if (!isfinite(m2[1])) st->status = PGO_ERR_NUMERICAL;
+      }
+    }
+  }
+}
+
+// Cost of one edge at the poses in buffer `buf` (FP64).
+__device__ __forceinline__ double edge_cost(const DevGraph& g, int buf, int e) {
+  const int i = g.ei[e], j = g.ej[e];
+  Sim3T<double> Si = load_pose(g, buf, i), Sj = load_pose(g, buf, j), Z = load_meas(g, e);
+  Sim3T<double> T = compose(Z, compose(Si, inverse(Sj)));
+  qnormalize(T.q);
+  double r[7];
+  sim3_log(T, r);
+  double c = 0.0;
+  if (g.L) {
+    const double* L = g.L + (size_t)e * 28;
+#pragma unroll
+    for (int cc = 0; cc < 7; ++cc) {
+      double s = 0.0;
+#pragma unroll
+      for (int a = cc; a < 7; ++a) s += L[a * (a + 1) / 2 + cc] * r[a];
+      c += s * s;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) c += r[k] * r[k];
+  }
+  return g.w[e] * c;
+}
+
+// mode 0: F at the current poses (start of a solve).
+// mode 1: F' at the candidate poses, then the LM accept/reject rule.
+__global__ void __launch_bounds__(256) k_cost(DevGraph g, int mode, unsigned long long lm_cond) {
+  SolverState* st = g.st;
+  if (mode == 1 && st->done) {
+    // stopped earlier in this iteration (gradient test): leave the LM loop
+    if (blockIdx.x == 0 && threadIdx.x == 0) set_cond(lm_cond, false);
+    return;
+  }
+  __shared__ double sh[32];
+  const int buf = mode == 0 ? st->cur : (st->cur ^ 1);
+  double c[1] = {0.0};
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < g.E; e += gridDim.x * blockDim.x)
+    c[0] += edge_cost(g, buf, e);
+  block_sum<1>(c, sh);
+  if (!publish_partials<1>(c, g.partial, &st->ticket[T_COST])) return;
+  double tot[1];
+  gather_partials_sum<1>(g.partial, tot, sh);
+  if (threadIdx.x != 0) return;
+  const DevOptions* o = g.opt;
+  const double Fn = tot[0];
+  if (mode == 0) {
+    st->F = Fn;
+    st->F0 = Fn;
+    if (!isfinite(Fn)) {
+      st->done = 1;
+      st->stop_reason = 4;
+      st->status = PGO_ERR_NUMERICAL;
+    }
+    if (o->max_iters <= 0) st->done = 1;
+    set_cond(lm_cond, !st->done);
+    return;
+  }
+  st->F_new = Fn;
+  const double F = st->F, pred = st->pred;
+  const double rho = (pred > 0.0 && isfinite(Fn)) ? (F - Fn) / pred : -1.0;
+  // |F - F'| <= ftol F, accepted or not: no progress is measurable
+  const bool flat = isfinite(Fn) && fabs(F - Fn) <= o->ftol * F;
+  if (rho > 0.0) {
+    st->cur ^= 1;
+    double f = 2.0 * rho - 1.0;
+    f = 1.0 - f * f * f;
+    st->lambda *= fmax(f, 1.0 / 3.0);
+    st->nu = 2.0;
+    st->need_lin = 1;
+    st->accepted += 1;
+    st->F = Fn;
+    if (flat) {
+      st->done = 1;
+      st->stop_reason = 1;
+    }
+  } else {
+    st->lambda *= st->nu;
+    st->nu *= 2.0;
+    if (flat) {
+      st->done = 1;
+      st->stop_reason = 1;
+    } else if (!(st->lambda < 1e32)) {
+      st->done = 1;
+      st->stop_reason = 3;
+    }
+  }
+  st->it += 1;
+  if (st->it >= o->max_iters && !st->done) {
+    st->done = 1;
+    st->stop_reason = 0;
+  }
+  set_cond(lm_cond, !st->done && st->it < o->max_iters);
+}
+
+// Candidate poses S' = exp(delta) S (delta from x64 or, mixed, dx64) into
+// buffer cur^1; the fixed vertex is copied.  The last block stores the
+// predicted decrease delta^T (lambda delta - b).
+__global__ void __launch_bounds__(256) k_update(DevGraph g, int mixed) {
+  SolverState* st = g.st;
+  if (st->done) return;
+  __shared__ double sh[32];
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cur = st->cur;
+  const double lam = st->lambda;
+  double pr[1] = {0.0};
+  if (v < g.N) {
+    Sim3T<double> S = load_pose(g, cur, v);
+    if (v == g.fixed) {
+      store_pose(g, cur ^ 1, v, S);
+    } else {
+      const double* dx = (mixed ? g.dx64 : g.x64) + (size_t)v * VEC;
+      double d[7];
+#pragma unroll
+      for (int k = 0; k < 7; ++k) d[k] = dx[k];
+      Sim3T<double> E = sim3_exp(d);
+      Sim3T<double> P = compose(E, S);
+      qnormalize(P.q);
+      store_pose(g, cur ^ 1, v, P);
+      const double* bv = g.b + (size_t)v * VEC;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) pr[0] += d[k] * (lam * d[k] - bv[k]);
+    }
+  }
+  block_sum<1>(pr, sh);
+  if (!publish_partials<1>(pr, g.partial, &st->ticket[T_UPDATE])) return;
+  double tot[1];
+  gather_partials_sum<1>(g.partial, tot, sh);
+  if (threadIdx.x == 0) st->pred = tot[0];
+}
+
+// Fresh LM state for a solve (keeps the current pose buffer).
+__global__ void k_lm_reset(DevGraph g) {
+  SolverState* st = g.st;
+  const int cur = st->cur;
+  st->F = 0.0;
+  st->F_new = 0.0;
+  st->lambda = -1.0;
+  st->nu = 2.0;
+  st->pred = 0.0;
+  st->gmax = 0.0;
+  st->maxdiag = 0.0;
+  st->it = 0;
+  st->accepted = 0;
+  st->done = 0;
+  st->need_lin = 1;
+  st->stop_reason = 0;
+  st->status = 0;
+  st->pcg_total = 0;
+  st->pcg_hit_cap = 0;
+  st->ref_done = 0;
+  for (int t = 0; t < T_COUNT; ++t) st->ticket[t] = 0u;
+  st->cur = cur;
+}
+
+// State for a standalone re-solve at opt->lambda_fixed (no linearisation).
+__global__ void k_resolve_reset(DevGraph g) {
+  SolverState* st = g.st;
+  st->done = 0;
+  st->need_lin = 0;
+  st->ref_done = 0;
+  st->status = 0;
+  st->pcg_total = 0;
+  st->pcg_hit_cap = 0;
+  st->lambda = g.opt->lambda_fixed;
+  for (int t = 0; t < T_COUNT; ++t) st->ticket[t] = 0u;
+}
+
+void launch_resolve_reset(const DevGraph& g, cudaStream_t s) { k_resolve_reset<<<1, 1, 0, s>>>(g); }
+
+void launch_cost(const DevGraph& g, int mode, cudaStream_t s, unsigned long long lm_cond) {
+  int blocks = (g.E + 255) / 256;
+  if (blocks > g.partial_cap) blocks = g.partial_cap;
+  if (blocks < 1) blocks = 1;
+  k_cost<<<blocks, 256, 0, s>>>(g, mode, lm_cond);
+}
+
+void launch_linearize(const DevGraph& g, int mixed, cudaStream_t s) {
+  if (g.E == 0) return;
+  k_linearize<<<(g.E + 127) / 128, 128, 0, s>>>(g, mixed);
+}
+
+void launch_assemble(const DevGraph& g, int mixed, cudaStream_t s) {
+  int blocks = (g.N * 8 + 255) / 256;
+  k_assemble<<<blocks, 256, 0, s>>>(g, mixed);
+}
+
+void launch_update(const DevGraph& g, int mixed, cudaStream_t s) {
+  k_update<<<(g.N + 255) / 256, 256, 0, s>>>(g, mixed);
+}
+
+void launch_lm_reset(const DevGraph& g, cudaStream_t s) { k_lm_reset<<<1, 1, 0, s>>>(g); }
+
+int max_partials(int N, int E) {
+  int a = (N * 32 + 255) / 256;   // warp-per-row kernels
+  int c = (E + 255) / 256;
+  int m = a > c ? a : c;
+  return m + 8;
+}
+
+}  // namespace pgo

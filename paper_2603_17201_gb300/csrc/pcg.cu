@@ -1,0 +1,773 @@
+// K3/K4: damped linear solve (H + lambda I) delta = rhs by block-Jacobi
+// preconditioned conjugate gradients over the block-sparse normal matrix.
+// (The paper's Sec. IV-F keeps an exact LDL^T on the CPU; here the solve
+// stays on the GPU, with no host round trip per iteration.)
+//
+// k_pcg is a persistent cooperative kernel: one launch runs every PCG
+// iteration of one linear solve.  One block per SM owns a contiguous range of
+// block rows; 8 lanes serve one block row and lane a (< 7) owns output
+// component a, so a 7x7 block times a 7-vector costs each lane 7 FMAs with no
+// cross-lane reduction (this matters on GB300, where every FP64 warp
+// instruction occupies the SM's FP64 pipe for ~16 cycles whatever the number
+// of active lanes).  Each stored off-diagonal block (i, j) serves row i as
+// H_ij and row j as H_ij^T; p = z + beta p_prev is formed on the fly.
+// Per iteration: SpMV + local p.q -> grid barrier -> alpha, x/r/z update +
+// local r.z, r.r -> grid barrier -> beta and the stopping test.  Every block
+// reduces the per-block partials itself in the same fixed order, so all
+// blocks take identical decisions and the result is deterministic.
+//
+// The grid barrier is a monotone arrival counter (release add, acquire poll)
+// with a bounded spin: on timeout the kernel records PGO_ERR_CUDA in the
+// state and every block returns.
+#include "common.cuh"
+
+namespace pgo {
+
+template <class V>
+struct Bufs;
+
+template <>
+struct Bufs<double> {
+  static __device__ __forceinline__ const double* off(const DevGraph& g) { return g.off64; }
+  static __device__ __forceinline__ const double* diag(const DevGraph& g) { return g.diag64; }
+  static __device__ __forceinline__ double* minv(const DevGraph& g) { return g.minv64; }
+  static __device__ __forceinline__ double* x(const DevGraph& g) { return g.x64; }
+  static __device__ __forceinline__ double* r(const DevGraph& g) { return g.r64; }
+  static __device__ __forceinline__ double* z(const DevGraph& g) { return g.z64; }
+  static __device__ __forceinline__ double* p(const DevGraph& g, int k) { return g.p64[k]; }
+  static __device__ __forceinline__ double* q(const DevGraph& g) { return g.q64; }
+  static constexpr int BLK = BLK64;
+};
+template <>
+struct Bufs<float> {
+  static __device__ __forceinline__ const float* off(const DevGraph& g) { return g.off32; }
+  static __device__ __forceinline__ const float* diag(const DevGraph& g) { return g.diag32; }
+  static __device__ __forceinline__ float* minv(const DevGraph& g) { return g.minv32; }
+  static __device__ __forceinline__ float* x(const DevGraph& g) { return g.x32; }
+  static __device__ __forceinline__ float* r(const DevGraph& g) { return g.r32; }
+  static __device__ __forceinline__ float* z(const DevGraph& g) { return g.z32; }
+  static __device__ __forceinline__ float* p(const DevGraph& g, int k) { return g.p32[k]; }
+  static __device__ __forceinline__ float* q(const DevGraph& g) { return g.q32; }
+  static constexpr int BLK = BLK32;
+};
+
+// ---- K3: block-Jacobi preconditioner M_v = (H_vv + lambda I)^-1 ----------
+// 7x7 Cholesky in FP64, explicit inverse stored as V; M = 0 on the fixed
+// vertex (its unknowns stay zero).
+template <class V>
+__global__ void __launch_bounds__(32) k_precond(DevGraph g) {
+  const SolverState* st = g.st;
+  if (st->done) return;
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= g.N) return;
+  V* M = Bufs<V>::minv(g) + (size_t)v * Bufs<V>::BLK;
+  if (v == g.fixed) {
+#pragma unroll
+    for (int k = 0; k < 49; ++k) M[k] = V(0);
+    return;
+  }
+  const double lam = st->lambda;
+  double A[7][7];
+  const double* D = g.diag64 + (size_t)v * BLK64;
+#pragma unroll
+  for (int a = 0; a < 7; ++a)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) A[a][c] = D[a * 7 + c] + (a == c ? lam : 0.0);
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    double d = A[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+    ok = ok && (d > 0.0);
+    d = sqrt(fmax(d, 1e-300));
+    A[j][j] = d;
+    const double inv = 1.0 / d;
+#pragma unroll
+    for (int i = j + 1; i < 7; ++i) {
+      double s = A[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
+      A[i][j] = s * inv;
+    }
+  }
+  if (!ok) {
+    // not positive definite: fall back to the inverse of the damped diagonal
+#pragma unroll
+    for (int a = 0; a < 7; ++a)
+#pragma unroll
+      for (int c = 0; c < 7; ++c) M[a * 7 + c] = (a == c) ? V(1.0 / fmax(D[a * 8] + lam, 1e-300)) : V(0);
+    return;
+  }
+  double Li[7][7];
+#pragma unroll
+  for (int c = 0; c < 7; ++c) {
+#pragma unroll
+    for (int a = 0; a < 7; ++a) {
+      if (a < c) {
+        Li[a][c] = 0.0;
+        continue;
+      }
+      double s = (a == c) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = c; k < a; ++k) s -= A[a][k] * Li[k][c];
+      Li[a][c] = s / A[a][a];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 7; ++a)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) s += Li[k][a] * Li[k][c];
+      M[a * 7 + c] = V(s);
+    }
+}
+
+// 7x7 block (first 49 entries of a 16-byte aligned padded block), read-only.
+__device__ __forceinline__ void load_block(const double* src, double (&B)[49]) {
+  const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+  for (int k = 0; k < 24; ++k) {
+    const double2 v = __ldg(s2 + k);
+    B[2 * k] = v.x;
+    B[2 * k + 1] = v.y;
+  }
+  B[48] = __ldg(src + 48);
+}
+__device__ __forceinline__ void load_block(const float* src, float (&B)[49]) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const float4 v = __ldg(s4 + k);
+    B[4 * k] = v.x;
+    B[4 * k + 1] = v.y;
+    B[4 * k + 2] = v.z;
+    B[4 * k + 3] = v.w;
+  }
+  B[48] = __ldg(src + 48);
+}
+
+// p_u = z_u + beta p_prev_u (vectors written by other blocks: L2 loads).
+__device__ __forceinline__ void load_p(const double* z, const double* pp, size_t base, double beta, double (&p)[8]) {
+  const double2* z2 = reinterpret_cast<const double2*>(z + base);
+  const double2* p2 = reinterpret_cast<const double2*>(pp + base);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 a = __ldcg(z2 + k), b = __ldcg(p2 + k);
+    p[2 * k] = a.x + beta * b.x;
+    p[2 * k + 1] = a.y + beta * b.y;
+  }
+}
+__device__ __forceinline__ void load_p(const float* z, const float* pp, size_t base, float beta, float (&p)[8]) {
+  const float4* z4 = reinterpret_cast<const float4*>(z + base);
+  const float4* p4 = reinterpret_cast<const float4*>(pp + base);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float4 a = __ldcg(z4 + k), b = __ldcg(p4 + k);
+    p[4 * k] = a.x + beta * b.x;
+    p[4 * k + 1] = a.y + beta * b.y;
+    p[4 * k + 2] = a.z + beta * b.z;
+    p[4 * k + 3] = a.w + beta * b.w;
+  }
+}
+
+// ---- grid barrier ---------------------------------------------------------
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s: only reached on a fault
+
+// All blocks of the (co-resident) grid arrive; returns false if the wait
+// exceeded the time limit or another block reported a timeout.
+__device__ __forceinline__ bool grid_sync(unsigned* counter, int* abort_flag, unsigned& target) {
+  __shared__ int ok;
+  __syncthreads();
+  target += gridDim.x;
+  if (threadIdx.x == 0) {
+    ok = 1;
+    red_release_add(counter, 1u);
+    const unsigned long long t0 = globaltimer_ns();
+    unsigned spins = 0;
+    while (ld_acquire_u32(counter) < target) {
+      if ((++spins & 255u) == 0u &&
+          (globaltimer_ns() - t0 > kBarrierTimeoutNs || *(volatile int*)abort_flag)) {
+        atomicExch(abort_flag, 1);
+        ok = 0;
+        break;
+      }
+    }
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+template <class S>
+struct PcgShared {
+  S red[32 * 2];
+  S tot[2];
+};
+
+// Sum of per-block partials (K values each) in fixed order, by every block
+// (warp 0 reduces, the block reads the result from shared memory).
+template <class S, int K>
+__device__ __forceinline__ void reduce_partials(const S* partial, S (&out)[K], S* sh) {
+  if (threadIdx.x < 32) {
+    S acc[K];
+#pragma unroll
+    for (int k = 0; k < K; ++k) acc[k] = S(0);
+    for (int b = threadIdx.x; b < gridDim.x; b += 32) {
+#pragma unroll
+      for (int k = 0; k < K; ++k) acc[k] += __ldcg(partial + b * K + k);
+    }
+#pragma unroll
+    for (int k = 0; k < K; ++k)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[k] += __shfl_xor_sync(0xffffffffu, acc[k], o);
+    if (threadIdx.x == 0)
+#pragma unroll
+      for (int k = 0; k < K; ++k) sh[k] = acc[k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k) out[k] = sh[k];
+  __syncthreads();
+}
+
+// Block sum of per-thread values (K each); thread 0 writes the block partial.
+template <class S, int K>
+__device__ __forceinline__ void write_partial(S (&v)[K], S* partial, S* sh) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[k] += __shfl_xor_sync(0xffffffffu, v[k], o);
+  if (lane == 0)
+#pragma unroll
+    for (int k = 0; k < K; ++k) sh[warp * K + k] = v[k];
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      S s = S(0);
+      for (int w = 0; w < nw; ++w) s += sh[w * K + k];
+      partial[blockIdx.x * K + k] = s;
+    }
+  }
+  __syncthreads();
+}
+
+struct PcgArgs {
+  int from_residual;   // 0: rhs = -b; 1: rhs = res64 (refinement)
+  int inner;           // tolerance: 0 -> pcg_tol, 1 -> refine_tol
+  int rows_per_block;  // contiguous block-row range per block
+  int cap_entries;     // off-diagonal blocks staged in shared memory per block
+};
+
+// Plain (generic-address) 7x7 block loads: the block may sit in shared or
+// global memory; it is read-only for the whole kernel.
+__device__ __forceinline__ void load_block_any(const double* src, double (&B)[49]) {
+  const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+  for (int k = 0; k < 24; ++k) {
+    const double2 v = s2[k];
+    B[2 * k] = v.x;
+    B[2 * k + 1] = v.y;
+  }
+  B[48] = src[48];
+}
+__device__ __forceinline__ void load_block_any(const float* src, float (&B)[49]) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const float4 v = s4[k];
+    B[4 * k] = v.x;
+    B[4 * k + 1] = v.y;
+    B[4 * k + 2] = v.z;
+    B[4 * k + 3] = v.w;
+  }
+  B[48] = src[48];
+}
+
+// y += B p (TR = false) or y += B^T p (TR = true), row-major 7x7 block.
+template <bool TR>
+__device__ __forceinline__ void bmv(const double* Bp, const double (&p)[8], double (&y)[7]) {
+  // FP64: one block row at a time keeps register pressure low
+#pragma unroll
+  for (int r = 0; r < 7; ++r) {
+    double row[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) row[c] = Bp[r * 7 + c];
+    if (!TR) {
+      double acc = 0.0;
+#pragma unroll
+      for (int c = 0; c < 7; ++c) acc += row[c] * p[c];
+      y[r] += acc;
+    } else {
+#pragma unroll
+      for (int c = 0; c < 7; ++c) y[c] += row[c] * p[r];
+    }
+  }
+}
+template <bool TR>
+__device__ __forceinline__ void bmv(const float* Bp, const float (&p)[8], float (&y)[7]) {
+  float B[49];
+  load_block_any(Bp, B);
+#pragma unroll
+  for (int a = 0; a < 7; ++a) {
+    float acc = 0.f;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) acc += (TR ? B[c * 7 + a] : B[a * 7 + c]) * p[c];
+    y[a] += acc;
+  }
+}
+
+// Copy n 16-byte chunks of padded blocks into shared memory.
+template <class V>
+__device__ __forceinline__ void stage_blocks(V* dst, const V* src_base, const int* codes, int nblk,
+                                             bool by_code) {
+  constexpr int CH = Bufs<V>::BLK * (int)sizeof(V) / 16;   // 16-byte chunks per block
+  for (int t = threadIdx.x; t < nblk * CH; t += blockDim.x) {
+    const int l = t / CH, c = t - l * CH;
+    const size_t srcb = by_code ? (size_t)(codes[l] >> 1) : (size_t)l;
+    const float4 v = __ldg(reinterpret_cast<const float4*>(src_base + srcb * Bufs<V>::BLK) + c);
+    reinterpret_cast<float4*>(dst + (size_t)l * Bufs<V>::BLK)[c] = v;
+  }
+}
+
+// One PCG solve.  V: storage and arithmetic type of blocks and vectors;
+// S: type of the dot products and scalars (double for the FP64 solve, float
+// for the inner solve of the mixed mode); G: lanes per block row in the SpMV
+// (each lane takes whole 7x7 blocks of the row, then the G lanes reduce).
+//
+// Shared memory (dynamic): the block's diagonal blocks and preconditioner
+// blocks, then its first cap_entries off-diagonal blocks (in incidence
+// order) with their neighbour indices, staged once at launch so that each
+// iteration reads the operator from shared memory; entries beyond the
+// capacity are read from global memory.
+template <class V, class S, int G>
+__global__ void __launch_bounds__(512) k_pcg(DevGraph g, PcgArgs a) {
+  SolverState* st = g.st;
+  if (st->done || (a.from_residual && st->ref_done)) return;
+  __shared__ PcgShared<S> sh;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  constexpr int BLK = Bufs<V>::BLK;
+  const DevOptions* o = g.opt;
+  unsigned* counter = &st->ticket[T_PCG_SPMV];
+  int* abort_flag = reinterpret_cast<int*>(&st->ticket[T_PCG_UPDATE]);
+  S* partial = reinterpret_cast<S*>(g.partial);
+  unsigned target = 0;
+
+  const int sl = threadIdx.x & (G - 1);        // SpMV: lane within the row's group of G
+  const int sslot = threadIdx.x / G;
+  const int nsslots = blockDim.x / G;
+  const int lane8 = threadIdx.x & 7;           // update: component owned by this lane (7 = idle)
+  const int slot = threadIdx.x >> 3;           // row slot within the block
+  const int nslots = blockDim.x >> 3;
+  const int row0 = blockIdx.x * a.rows_per_block;
+  const int row1 = min(row0 + a.rows_per_block, g.N);
+  const int nrows = row1 - row0;
+  const bool act = lane8 < 7;
+  const int c7 = act ? lane8 : 0;
+  const unsigned gm8 = 0xffu << (threadIdx.x & 24);   // the 8 lanes of a row (update)
+  const unsigned gmG = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << (threadIdx.x & (32 - G)));
+
+  const V* off = Bufs<V>::off(g);
+  V* x = Bufs<V>::x(g);
+  V* r = Bufs<V>::r(g);
+  V* z = Bufs<V>::z(g);
+  V* q = Bufs<V>::q(g);
+  const V lam = V(st->lambda);
+  const double tol = a.inner ? o->refine_tol : o->pcg_tol;
+  const int maxit = o->pcg_max_iters;
+
+  // ---- stage the block's operator in shared memory ----
+  V* s_diag = reinterpret_cast<V*>(smem_raw);
+  V* s_minv = s_diag + (size_t)a.rows_per_block * BLK;
+  V* s_off = s_minv + (size_t)a.rows_per_block * BLK;
+  int* s_code = reinterpret_cast<int*>(s_off + (size_t)a.cap_entries * BLK);
+  int* s_other = s_code + a.cap_entries;
+  const int e0 = __ldg(g.inc_ptr + row0);
+  const int nst = min(__ldg(g.inc_ptr + row1) - e0, a.cap_entries);
+  for (int l = threadIdx.x; l < nst; l += blockDim.x) {
+    s_code[l] = __ldg(g.inc_code + e0 + l);
+    s_other[l] = __ldg(g.inc_other + e0 + l);
+  }
+  stage_blocks<V>(s_diag, Bufs<V>::diag(g) + (size_t)row0 * BLK, nullptr, nrows, false);
+  stage_blocks<V>(s_minv, Bufs<V>::minv(g) + (size_t)row0 * BLK, nullptr, nrows, false);
+  __syncthreads();
+  stage_blocks<V>(s_off, off, s_code, nst, true);
+  __syncthreads();
+
+  // ---- start: x = 0, r = rhs, z = M r, p_prev = 0 ----
+  S loc[2] = {S(0), S(0)};
+  // (loops over rows advance in whole-block steps so every lane of a warp
+  // runs the same trip count)
+  for (int v0 = row0; v0 < row1; v0 += nslots) {
+    const int v = v0 + slot;
+    const bool has = v < row1;
+    const size_t base = (size_t)(has ? v : row0) * VEC;
+    V rv = V(0);
+    if (has && act && v != g.fixed) {
+      const double src = a.from_residual ? g.res64[base + c7] : -g.b[base + c7];
+      rv = V(src);
+    }
+    V zv = V(0);
+    const V* M = s_minv + (size_t)((has ? v : row0) - row0) * BLK;
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      const V rc = __shfl_sync(gm8, rv, (threadIdx.x & ~7) + c);
+      zv += M[c7 * 7 + c] * rc;
+    }
+    if (!act || !has) zv = V(0);
+    if (has) {
+      x[base + lane8] = V(0);
+      r[base + lane8] = rv;
+      z[base + lane8] = zv;
+      Bufs<V>::p(g, 1)[base + lane8] = V(0);
+      Bufs<V>::p(g, 0)[base + lane8] = V(0);
+    }
+    loc[0] += S(rv) * S(zv);
+    loc[1] += S(rv) * S(rv);
+  }
+  write_partial<S, 2>(loc, partial, sh.red);
+  if (!grid_sync(counter, abort_flag, target)) goto timeout;
+  S rz, bb;
+  {
+    S t[2];
+    reduce_partials<S, 2>(partial, t, sh.red);
+    rz = t[0];
+    bb = t[1];
+  }
+  {
+    S beta = S(0);
+    int it = 0;
+    bool done = !(bb > S(0)) || !(rz > S(0));
+    const S tol2 = S(tol * tol);
+    while (!done) {
+      // ---- SpMV: q = (H + lambda I) p, p = z + beta p_prev ----
+      const V* pprev = Bufs<V>::p(g, (it + 1) & 1);
+      V* pcur = Bufs<V>::p(g, it & 1);
+      const V vb = V(beta);
+      S pq = S(0);
+      for (int v0 = row0; v0 < row1; v0 += nsslots) {
+        const int v = v0 + sslot;
+        const bool has = v < row1;
+        const size_t base = (size_t)(has ? v : row0) * VEC;
+        const int k0 = has ? __ldg(g.inc_ptr + v) : 0, k1 = has ? __ldg(g.inc_ptr + v + 1) : -1;
+        const int ks = has ? __ldg(g.inc_split + v) : 0;
+        V y[7];
+#pragma unroll
+        for (int a2 = 0; a2 < 7; ++a2) y[a2] = V(0);
+        // side-0 entries (H_vu stored as the (v, u) block) and the diagonal
+        // block (entry k0 - 1), then side-1 entries (H_uv^T): two loops so
+        // that the lanes of a warp never diverge between the two products
+        for (int k = k0 - 1 + sl; k < ks; k += G) {
+          const bool dg = k < k0;
+          const int l = k - e0;
+          int code = 0, u = v;
+          const V* Bp;
+          if (dg) {
+            Bp = s_diag + (size_t)(v - row0) * BLK;
+          } else if (l < nst) {
+            code = s_code[l];
+            u = s_other[l];
+            Bp = s_off + (size_t)l * BLK;
+          } else {
+            code = __ldg(g.inc_code + k);
+            u = __ldg(g.inc_other + k);
+            Bp = off + (size_t)(code >> 1) * BLK;
+          }
+          V pu[8];
+          load_p(z, pprev, (size_t)u * VEC, vb, pu);
+          if (dg) {
+#pragma unroll
+            for (int a2 = 0; a2 < 7; ++a2) y[a2] += lam * pu[a2];
+          }
+          bmv<false>(Bp, pu, y);
+        }
+        for (int k = ks + sl; k < k1; k += G) {
+          const int l = k - e0;
+          int code, u;
+          const V* Bp;
+          if (l < nst) {
+            code = s_code[l];
+            u = s_other[l];
+            Bp = s_off + (size_t)l * BLK;
+          } else {
+            code = __ldg(g.inc_code + k);
+            u = __ldg(g.inc_other + k);
+            Bp = off + (size_t)(code >> 1) * BLK;
+          }
+          V pu[8];
+          load_p(z, pprev, (size_t)u * VEC, vb, pu);
+          bmv<true>(Bp, pu, y);
+        }
+        // reduce the row's partial products over its G lanes
+#pragma unroll
+        for (int a2 = 0; a2 < 7; ++a2)
+#pragma unroll
+          for (int o2 = G / 2; o2 > 0; o2 >>= 1) y[a2] += __shfl_xor_sync(gmG, y[a2], o2);
+        if (has && sl < 7) {
+          V yc = y[0];
+#pragma unroll
+          for (int a2 = 1; a2 < 7; ++a2) yc = (sl == a2) ? y[a2] : yc;
+          const V pv = __ldcg(z + base + sl) + vb * __ldcg(pprev + base + sl);
+          const bool live = v != g.fixed;
+          q[base + sl] = live ? yc : V(0);
+          pcur[base + sl] = pv;
+          if (live) pq += S(pv) * S(yc);
+        } else if (has && sl == 7) {
+          q[base + 7] = V(0);
+          pcur[base + 7] = V(0);
+        }
+      }
+      {
+        S l1[1] = {pq};
+        write_partial<S, 1>(l1, partial + 2 * gridDim.x, sh.red);
+      }
+      if (!grid_sync(counter, abort_flag, target)) goto timeout;
+      S alpha;
+      {
+        S t[1];
+        reduce_partials<S, 1>(partial + 2 * gridDim.x, t, sh.red);
+        if (!(t[0] > S(0))) break;   // breakdown: keep the current x
+        alpha = rz / t[0];
+      }
+      // ---- update: x += alpha p, r -= alpha q, z = M r ----
+      const V va = V(alpha);
+      S l2[2] = {S(0), S(0)};
+      for (int v0 = row0; v0 < row1; v0 += nslots) {
+        const int v = v0 + slot;
+        const bool has = v < row1;
+        const size_t base = (size_t)(has ? v : row0) * VEC;
+        V rv = V(0);
+        if (has && act && v != g.fixed) {
+          x[base + c7] += va * pcur[base + c7];
+          rv = r[base + c7] - va * q[base + c7];
+          r[base + c7] = rv;
+        }
+        V zv = V(0);
+        const V* M = s_minv + (size_t)((has ? v : row0) - row0) * BLK;
+#pragma unroll
+        for (int c = 0; c < 7; ++c) {
+          const V rc = __shfl_sync(gm8, rv, (threadIdx.x & ~7) + c);
+          zv += M[c7 * 7 + c] * rc;
+        }
+        if (has && act) {
+          z[base + c7] = zv;
+          l2[0] += S(rv) * S(zv);
+          l2[1] += S(rv) * S(rv);
+        }
+      }
+      write_partial<S, 2>(l2, partial + 3 * gridDim.x, sh.red);
+      if (!grid_sync(counter, abort_flag, target)) goto timeout;
+      S t2[2];
+      reduce_partials<S, 2>(partial + 3 * gridDim.x, t2, sh.red);
+      beta = (rz > S(0)) ? t2[0] / rz : S(0);
+      rz = t2[0];
+      ++it;
+      done = !(t2[1] > tol2 * bb) || !(rz > S(0)) || !isfinite((double)t2[1]);
+      if (!done && it >= maxit) {
+        done = true;
+        if (blockIdx.x == 0 && threadIdx.x == 0) st->pcg_hit_cap = 1;
+      }
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->pcg_total += it;
+      st->pcg_iter = it;
+    }
+  }
+  // leave the counter at zero for the next launch: the last block to get here
+  // resets it (all blocks have passed their last barrier).
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(&st->ticket[T_PCG_INIT], 1u);
+    if (t == gridDim.x - 1) {
+      st->ticket[T_PCG_INIT] = 0u;
+      st->ticket[T_PCG_SPMV] = 0u;
+      __threadfence();
+    }
+  }
+  return;
+timeout:
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->status = PGO_ERR_CUDA;
+  return;
+}
+
+// ---- mixed precision: FP64 refinement ------------------------------------
+// res = -b - (H + lambda I) dx in FP64 with the FP64 blocks (8 lanes per row,
+// lane a owns component a); the first pass starts from dx = 0.  The last
+// block stores |res|^2 and the outer stopping test |res| <= pcg_tol |b|.
+__global__ void __launch_bounds__(256) k_refine_residual(DevGraph g, int first) {
+  SolverState* st = g.st;
+  if (st->done || (!first && st->ref_done)) return;
+  __shared__ double sh[32];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = tid >> 3, lane8 = tid & 7;
+  const bool act = lane8 < 7;
+  const int c7 = act ? lane8 : 0;
+  const unsigned gm8 = 0xffu << (threadIdx.x & 24);   // the 8 lanes of this row
+  const double lam = st->lambda;
+  double part[1] = {0.0};
+  if (v < g.N) {
+    const size_t base = (size_t)v * VEC;
+    double y = 0.0;
+    if (!first) {
+      const double xv = g.dx64[base + c7];
+      y = lam * xv;
+      const double* D = g.diag64 + (size_t)v * BLK64;
+#pragma unroll
+      for (int c = 0; c < 7; ++c) y += D[c7 * 7 + c] * __shfl_sync(gm8, xv, (threadIdx.x & ~7) + c);
+      const int k0 = g.inc_ptr[v], ks = g.inc_split[v], k1 = g.inc_ptr[v + 1];
+      for (int k = k0; k < ks; ++k) {   // side 0: H_vu
+        const int code = __ldg(g.inc_code + k);
+        const double xu = g.dx64[(size_t)__ldg(g.inc_other + k) * VEC + c7];
+        const double* B = g.off64 + (size_t)(code >> 1) * BLK64;
+#pragma unroll
+        for (int c = 0; c < 7; ++c) y += B[c7 * 7 + c] * __shfl_sync(gm8, xu, (threadIdx.x & ~7) + c);
+      }
+      for (int k = ks; k < k1; ++k) {   // side 1: H_uv^T
+        const int code = __ldg(g.inc_code + k);
+        const double xu = g.dx64[(size_t)__ldg(g.inc_other + k) * VEC + c7];
+        const double* B = g.off64 + (size_t)(code >> 1) * BLK64;
+#pragma unroll
+        for (int c = 0; c < 7; ++c) y += B[c * 7 + c7] * __shfl_sync(gm8, xu, (threadIdx.x & ~7) + c);
+      }
+    } else if (act) {
+      g.dx64[base + c7] = 0.0;
+    }
+    if (!act) {
+      g.res64[base + 7] = 0.0;
+      if (first) g.dx64[base + 7] = 0.0;
+    } else {
+      const double rv = (v == g.fixed) ? 0.0 : -g.b[base + c7] - y;
+      g.res64[base + c7] = rv;
+      part[0] = rv * rv;
+    }
+  }
+  block_sum<1>(part, sh);
+  if (!publish_partials<1>(part, g.partial, &st->ticket[T_REFINE])) return;
+  double tot[1];
+  gather_partials_sum<1>(g.partial, tot, sh);
+  if (threadIdx.x == 0) {
+    st->ref_rr = tot[0];
+    const double tol = g.opt->pcg_tol;
+    st->ref_done = !(tot[0] > tol * tol * st->bnorm2);
+  }
+}
+
+// dx64 += x32 (after an inner FP32 solve).
+__global__ void __launch_bounds__(256) k_refine_accumulate(DevGraph g) {
+  const SolverState* st = g.st;
+  if (st->done || st->ref_done) return;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= g.N * VEC) return;
+  g.dx64[t] += (double)g.x32[t];
+}
+
+// ---- launch configuration ---------------------------------------------------
+#ifndef PCG_G32
+#define PCG_G32 16
+#endif
+static int g_num_sms = 0;
+
+static int num_sms() {
+  if (g_num_sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&g_num_sms, cudaDevAttrMultiProcessorCount, dev);
+    if (g_num_sms <= 0) g_num_sms = 1;
+  }
+  return g_num_sms;
+}
+
+static size_t g_smem_optin = 0;
+
+template <class V, class S, int G>
+static cudaError_t launch_pcg_kernel(const DevGraph& g, PcgArgs a, cudaStream_t s) {
+  const int sms = num_sms();
+  if (g_smem_optin == 0) {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    g_smem_optin = v > 0 ? (size_t)v : 48 * 1024;
+  }
+  // one block per SM, rows split evenly; max(8, G) lanes per row, <= 512 threads
+  const int lanes = G > 8 ? G : 8;
+  int blocks = sms;
+  int rows_per_block = (g.N + blocks - 1) / blocks;
+  if (rows_per_block < 1) rows_per_block = 1;
+  blocks = (g.N + rows_per_block - 1) / rows_per_block;
+  int threads = rows_per_block * lanes;
+  threads = ((threads + 31) / 32) * 32;
+  if (threads > 512) threads = 512;
+  if (threads < 32) threads = 32;
+  a.rows_per_block = rows_per_block;
+  // shared memory: diag + preconditioner blocks of the rows, then as many
+  // off-diagonal blocks (and their indices) as fit
+  const size_t blk_bytes = (size_t)Bufs<V>::BLK * sizeof(V);
+  const size_t budget = g_smem_optin - 2048;   // static shared memory and slack
+  const size_t fixed_bytes = 2 * (size_t)rows_per_block * blk_bytes;
+  size_t cap = 0;
+  if (budget > fixed_bytes) cap = (budget - fixed_bytes) / (blk_bytes + 2 * sizeof(int));
+  const size_t max_entries = (size_t)2 * (size_t)(g.E > 0 ? g.E : 1);
+  if (cap > max_entries) cap = max_entries;
+  a.cap_entries = (int)cap;
+  const size_t smem = fixed_bytes + cap * (blk_bytes + 2 * sizeof(int));
+  cudaError_t e = cudaFuncSetAttribute(k_pcg<V, S, G>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_pcg<V, S, G>, g, a);
+}
+
+// Partial slots (of 4 doubles) the persistent solve needs: 5 values per block.
+int pcg_partials_needed(int) { return 2 * num_sms() + 8; }
+
+void launch_precond(const DevGraph& g, int mixed, cudaStream_t s) {
+  const int nb = (g.N + 31) / 32;
+  if (mixed) k_precond<float><<<nb, 32, 0, s>>>(g);
+  else k_precond<double><<<nb, 32, 0, s>>>(g);
+}
+
+cudaError_t launch_pcg(const DevGraph& g, int mixed, int from_residual, cudaStream_t s) {
+  PcgArgs a;
+  a.from_residual = from_residual;
+  a.inner = mixed;
+  a.rows_per_block = 1;
+  a.cap_entries = 0;
+  if (mixed) return launch_pcg_kernel<float, float, PCG_G32>(g, a, s);
+  return launch_pcg_kernel<double, double, 8>(g, a, s);
+}
+
+void launch_refine_residual(const DevGraph& g, int first, cudaStream_t s) {
+  k_refine_residual<<<(g.N * 8 + 255) / 256, 256, 0, s>>>(g, first);
+}
+
+void launch_refine_accumulate(const DevGraph& g, cudaStream_t s) {
+  k_refine_accumulate<<<(g.N * VEC + 255) / 256, 256, 0, s>>>(g);
+}
+
+}  // namespace pgo

@@ -292,7 +292,7 @@ def _loop_pairs(centres, n_loops, min_gap=200, max_dist=1.5):
 
 
 def make_graph(kind, n, *, seed, window=15, n_loops=1, noise=(0.01, 0.02, 0.01),
-               meas_noise=False, name=None, weight=1.0):
+               meas_noise=False, name=None, weight=1.0, loop_min_gap=200, loop_max_dist=1.5):
     """Build one synthetic essential graph.
 
     kind      'circle' | 'figure8' | 'corridor'
@@ -300,6 +300,8 @@ def make_graph(kind, n, *, seed, window=15, n_loops=1, noise=(0.01, 0.02, 0.01),
     window    covisibility window (forward pairs within ``window`` frames);
               for 'circle' the sampled scheme of the 200-keyframe case is used
     n_loops   loop edges (for 'circle': the single last -> first edge)
+    loop_min_gap, loop_max_dist  a loop joins keyframes more than
+              ``loop_min_gap`` frames apart within ``loop_max_dist`` metres
     noise     (sig_rot rad, sig_trans m, sig_logscale) per drift step
     meas_noise  add i.i.d. noise of the same form to every measurement
     """
@@ -325,7 +327,7 @@ def make_graph(kind, n, *, seed, window=15, n_loops=1, noise=(0.01, 0.02, 0.01),
         loops = [(n - 1, 0)] if n_loops > 0 else []
     else:
         ei, ej = _window_edges(n, window)
-        loops = _loop_pairs(c, n_loops)
+        loops = _loop_pairs(c, n_loops, min_gap=loop_min_gap, max_dist=loop_max_dist)
     meas = compose(est[ej], inverse(est[ei]))
     if loops:
         li = np.array([p[0] for p in loops], dtype=np.int64)

@@ -184,6 +184,9 @@ def test_scale_ring_closed_form(oracle_mod):
     p, rep = og.lm(poses, max_iters=30)
     c = sz.sum()
     assert abs(rep["final_cost"] - c * c / n) < 1e-14
+    # cost-based stopping resolves the optimum to sqrt(eps); polishing
+    # (undamped Newton steps kept while |b| drops) pins the stationary point
+    p, rep = og.lm(poses, max_iters=30, polish_iters=5)
     _, r = og.cost(p, residuals=True)
     assert np.abs(r[:, 6] - c / n).max() < 1e-12
     assert np.abs(r[:, :6]).max() < 1e-13
