@@ -245,6 +245,26 @@ pgo_status pgo_evaluate_cost(int32_t n_vertices, int32_t n_edges, const int32_t*
                              const int32_t* edge_j, const double* meas, const double* weight,
                              const double* poses, double* cost_out, void* stream);
 
+/* pgo_evaluate_cost without any device allocation (no counterpart in the
+ * paper: an addition for callers that cannot allocate device memory at call
+ * time, such as a real-time loop-closing thread that must not stall on the
+ * allocator, or an application that reserves the whole device memory budget
+ * at start-up).  Same arguments and result as pgo_evaluate_cost, computed by
+ * the same kernel, but its workspace is a fixed 33,024-byte array inside the
+ * library's device image, held by every GPU that loads the library until the
+ * process exits.  Limits and rules:
+ *   - n_edges <= 1,048,576, else PGO_ERR_INVALID_ARG (use pgo_evaluate_cost);
+ *   - the first call on each device, with that device current, looks up the
+ *     workspace address (cudaGetSymbolAddress) and caches it: make that first
+ *     call before any stream capture;
+ *   - every call shares the one workspace and it keeps the last call's
+ *     contents (each call clears its counters first); calls that overlap on
+ *     the GPU, from several streams or threads, race and must be avoided;
+ *   - it calls no cudaMalloc, cudaFree or allocating library routine. */
+pgo_status pgo_evaluate_cost_noalloc(int32_t n_vertices, int32_t n_edges, const int32_t* edge_i,
+                                     const int32_t* edge_j, const double* meas, const double* weight,
+                                     const double* poses, double* cost_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -185,4 +185,10 @@ void launch_eval_cost_raw(int N, int E, const int* ei, const int* ej, const doub
                                                       cost_out);
 }
 
+void launch_eval_cost_raw_blocks(int N, int E, const int* ei, const int* ej, const double* meas, const double* w,
+                                 const double* poses, double* partial, unsigned* ticket, int* bad,
+                                 double* cost_out, int blocks, cudaStream_t s) {
+  k_eval_cost_raw<<<blocks, 256, 0, s>>>(N, E, ei, ej, meas, w, poses, partial, ticket, bad, cost_out);
+}
+
 }  // namespace pgo

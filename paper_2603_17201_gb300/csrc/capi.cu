@@ -117,6 +117,10 @@ struct GraphBuilder {
 
 }  // namespace
 
+namespace pgo {
+void set_last_error(const char* msg) { g_last_error = msg; }
+}  // namespace pgo
+
 struct pgo_graph {
   int N = 0, E = 0, fixed = 0;
   cudaStream_t stream = nullptr;

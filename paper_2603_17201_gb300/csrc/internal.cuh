@@ -114,5 +114,9 @@ int eval_cost_blocks(int E);
 void launch_eval_cost_raw(int N, int E, const int* ei, const int* ej, const double* meas, const double* w,
                           const double* poses, double* partial, unsigned* ticket, int* bad,
                           double* cost_out, cudaStream_t s);
+void launch_eval_cost_raw_blocks(int N, int E, const int* ei, const int* ej, const double* meas, const double* w,
+                                 const double* poses, double* partial, unsigned* ticket, int* bad,
+                                 double* cost_out, int blocks, cudaStream_t s);
+void set_last_error(const char* msg);   // message returned by pgo_last_error()
 
 }  // namespace pgo
