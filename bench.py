@@ -34,6 +34,10 @@ SCHED = {"graph": -1, "eager": 1}
 MAX_ITERS = 20
 METRIC = "Sim(3) PGO ms/solve & edges/s at rel cost <=1e-6: mixed vs plain FP64, one GB300"
 UNIT = "edges/s"
+# DRAM bytes (read + write) of one roofline launch from an ncu capture of
+# `bench.py --roofline-only` (profiles/k_pcg_float_c2_figure8_2k.md); None
+# whenever the kernel has changed since the counters were taken.
+TRAFFIC_PER_LAUNCH = 7.76e6
 
 
 def parse():
@@ -44,6 +48,9 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--roofline-only", action="store_true",
+                    help="only the roofline leg: linearise once, then one 400-iteration FP32 PCG launch "
+                         "(the launch an ncu capture of the dominant kernel should see first)")
     ap.add_argument("--schedule", default="graph", choices=["graph", "eager"],
                     help="graph: one CUDA graph per solve (default); eager: host-driven launches "
                          "(for profilers that cannot see inside conditional graph nodes)")
@@ -138,6 +145,48 @@ def oracle_reference(g, max_iters):
     t = time.perf_counter()
     p, rep = og.lm(g.poses_init, max_iters=max_iters)
     return time.perf_counter() - t, rep
+
+
+def roofline_leg(pg, N, E, stream, flush, torch, reps=5):
+    """Average duration of the dominant kernel (the FP32 PCG of the mixed
+    solve): re-solve the damped system at the current linearisation with a
+    fixed iteration count (one k_pcg launch of `cap` iterations plus the tiny
+    preconditioner and residual kernels), timed with CUDA events on the
+    graph's stream; algorithmic bytes per launch = cap x per-iteration bytes."""
+    peaks, peak_kind = measured_peaks()
+    cap, lam = 400, 1e-3
+    kw = dict(precision="mixed", pcg_tol=1e-30, refine_tol=1e-30, refine_steps=1, pcg_max_iters=cap)
+    durs = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pg.resolve_async(lam, **kw)
+        e1.record(stream)
+        e1.synchronize()
+        durs.append(e0.elapsed_time(e1))
+    launch_ms = statistics.median(durs)
+    bytes_launch = cap * pcg_bytes_per_iter(N, E, 4)
+    achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+            "traffic": TRAFFIC_PER_LAUNCH, "kernel": "k_pcg<float,float,16> (mixed inner PCG)",
+            "peak_kind": peak_kind, "us_per_pcg_iteration": 1e3 * launch_ms / cap,
+            "algorithmic_bytes_per_launch": bytes_launch, "iterations_per_launch": cap}
+
+
+def run_roofline_only(args):
+    import torch
+    from paper_2603_17201_gb300 import PoseGraph
+    from paper_2603_17201_gb300 import synthetic as syn
+    torch.cuda.set_device(0)
+    g = syn.make_config(args.workload)
+    pg = PoseGraph.from_synthetic(g)
+    pg.linearize("mixed", jacobians=False)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    r = roofline_leg(pg, g.n_vertices, g.n_edges, torch.cuda.current_stream(), flush, torch, reps=1)
+    print(json.dumps({"roofline": r}), flush=True)
 
 
 # --------------------------------------------------------------------- reference arm
@@ -244,32 +293,7 @@ def run_ours(args):
         if precision == "mixed":
             launches = args.steps * (per_iter + 1)
 
-    # ---- roofline of the dominant kernel (the FP32 PCG kernel of the mixed
-    # solve): re-solve the damped system at the converged linearisation with a
-    # fixed iteration count, timed with CUDA events on the graph's stream ----
-    peaks, peak_kind = measured_peaks()
-    cap = 400
-    lam = 1e-3
-    pg.damped_step(lam, precision="mixed", pcg_tol=1e-30, refine_tol=1e-30, refine_steps=1,
-                   pcg_max_iters=cap, allow_cap=True)
-    durs = []
-    for _ in range(5):
-        flush.fill_(1.0)
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        its_r = pg.resolve_async(lam, precision="mixed", pcg_tol=1e-30, refine_tol=1e-30, refine_steps=1,
-                                 pcg_max_iters=cap)
-        e1.record(stream)
-        e1.synchronize()
-        durs.append(e0.elapsed_time(e1))
-    launch_ms = statistics.median(durs)
-    bytes_launch = cap * pcg_bytes_per_iter(N, E, 4)
-    achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
-    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks.get("hbm_gbs", 6800.0), "unit": "GB/s",
-                "frac": achieved / peaks.get("hbm_gbs", 6800.0), "traffic": None,
-                "kernel": "k_pcg<float> (mixed inner PCG)", "peak_kind": peak_kind,
-                "us_per_pcg_iteration": 1e3 * launch_ms / cap}
+    roofline = roofline_leg(pg, N, E, stream, flush, torch)
 
     # ---- correctness gate: final cost vs the FP64 oracle ----
     cpu = None
@@ -328,7 +352,9 @@ def run_ours(args):
 
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.roofline_only:
+        run_roofline_only(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -98,7 +98,7 @@ typedef struct {
   double pcg_tol;         /* PCG: |r| <= pcg_tol * |b| (1e-10) */
   int32_t pcg_max_iters;  /* PCG iteration cap per linear solve (5000) */
   int32_t refine_steps;   /* PGO_MIXED: FP64 iterative-refinement passes (3) */
-  double refine_tol;      /* PGO_MIXED: inner FP32 PCG relative tolerance (1e-5) */
+  double refine_tol;      /* PGO_MIXED: inner FP32 PCG relative tolerance (1e-6) */
   int32_t polish_iters;   /* undamped Newton steps after LM, each kept only
                              while it lowers |b|_inf (0; use >0 before
                              pgo_backward) */
