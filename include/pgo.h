@@ -151,6 +151,14 @@ void pgo_graph_destroy(pgo_graph* g);
  * PGO_ERR_NUMERICAL). */
 pgo_status pgo_graph_set_poses(pgo_graph* g, const double* poses, int32_t mem_space);
 
+/* Replace the edge measurements (double[n_edges * 8] pose8, caller's edge
+ * order) and, if weight is non-NULL, the weights (double[n_edges]); the graph
+ * structure is unchanged (Sec. III-B: loop fusion updates the essential
+ * graph's constraints).  Host inputs are validated like pgo_graph_create's;
+ * device inputs are copied on the graph's stream without host validation. */
+pgo_status pgo_graph_set_measurements(pgo_graph* g, const double* meas, const double* weight,
+                                      int32_t mem_space);
+
 /* Copy the current vertex estimate to poses (double[n_vertices * 8]). */
 pgo_status pgo_graph_get_poses(pgo_graph* g, double* poses, int32_t mem_space);
 

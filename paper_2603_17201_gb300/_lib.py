@@ -36,7 +36,7 @@ PGO_GRAD_POSE8 = 1
 # Every exported symbol the header declares (checked by the CPU test-suite).
 EXPORTED = [
     "pgo_last_error", "pgo_version", "pgo_default_options", "pgo_graph_create", "pgo_graph_destroy",
-    "pgo_graph_set_poses", "pgo_graph_get_poses", "pgo_graph_cost", "pgo_graph_linearize",
+    "pgo_graph_set_poses", "pgo_graph_set_measurements", "pgo_graph_get_poses", "pgo_graph_cost", "pgo_graph_linearize",
     "pgo_graph_damped_step", "pgo_graph_resolve", "pgo_graph_report", "pgo_solve", "pgo_backward", "pgo_batch_create", "pgo_batch_destroy",
     "pgo_batch_solve", "pgo_evaluate_cost", "pgo_evaluate_cost_noalloc",
 ]
@@ -97,6 +97,7 @@ def load(build_if_missing: bool = True):
         lib.pgo_graph_destroy.restype = None
         lib.pgo_graph_set_poses.argtypes = [vp, vp, c_int32]
         lib.pgo_graph_get_poses.argtypes = [vp, vp, c_int32]
+        lib.pgo_graph_set_measurements.argtypes = [vp, vp, vp, c_int32]
         lib.pgo_graph_cost.argtypes = [vp, _dp, vp, c_int32]
         lib.pgo_graph_linearize.argtypes = [vp, c_int32, vp, vp, vp, vp, c_int32]
         lib.pgo_graph_damped_step.argtypes = [vp, ctypes.POINTER(SolveOptions), c_double, vp,

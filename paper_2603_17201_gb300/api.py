@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["PoseGraph", "evaluate_cost", "default_options", "PGOError"]
+__all__ = ["PoseGraph", "evaluate_cost", "default_options", "PGOError", "solve_pose_graph"]
 
 PGOError = L.PGOError
 default_options = L.default_options
@@ -143,6 +143,40 @@ class PoseGraph:
         L.check(self._lib.pgo_graph_set_poses(self._h, p, m.mem_space))
         self._keep = m.keep
 
+    def set_measurements(self, meas, weight=None):
+        """Replace the edge measurements (E, 8) and optionally the weights (E,)
+        (caller's edge order).  CUDA tensors are copied on the graph's stream."""
+        dev = _is_cuda_tensor(meas) or _is_cuda_tensor(weight)
+        m = _Marshal(dev)
+        pm = m.put(meas, np.float64, (self.n_edges, 8))
+        pw = m.put(weight, np.float64, (self.n_edges,))
+        L.check(self._lib.pgo_graph_set_measurements(self._h, pm, pw, m.mem_space))
+        self._keep_meas = m.keep
+
+    def backward(self, dL_dposes, layout="pose8", meas_grad=True, weight_grad=True, **opts):
+        """Implicit-adjoint gradients of the last solve (see pgo_backward).
+        dL_dposes: (N, 8) for layout 'pose8' or (N, 7) for 'tangent'.
+        Returns (dL/dmeas (E, 8 or 7), dL/dweight (E,)) as CUDA tensors when
+        dL_dposes is a CUDA tensor, else numpy arrays."""
+        lay = L.PGO_GRAD_POSE8 if layout == "pose8" else L.PGO_GRAD_TANGENT7
+        w = 8 if lay == L.PGO_GRAD_POSE8 else 7
+        o = L.default_options(**opts)
+        if _is_cuda_tensor(dL_dposes):
+            torch = _torch()
+            g = dL_dposes.to(torch.float64).contiguous()
+            dm = torch.empty((self.n_edges, w), dtype=torch.float64, device=g.device) if meas_grad else None
+            dw = torch.empty((self.n_edges,), dtype=torch.float64, device=g.device) if weight_grad else None
+            ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+            L.check(self._lib.pgo_backward(self._h, ctypes.byref(o), ptr(g), lay, ptr(dm), ptr(dw),
+                                           L.PGO_MEM_DEVICE))
+            return dm, dw
+        g = np.ascontiguousarray(dL_dposes, dtype=np.float64)
+        dm = np.empty((self.n_edges, w)) if meas_grad else None
+        dw = np.empty(self.n_edges) if weight_grad else None
+        ptr = lambda a: ctypes.c_void_p(a.ctypes.data) if a is not None else None  # noqa: E731
+        L.check(self._lib.pgo_backward(self._h, ctypes.byref(o), ptr(g), lay, ptr(dm), ptr(dw), L.PGO_MEM_HOST))
+        return dm, dw
+
     def get_poses(self, device=False):
         """Current estimate (N, 8): a CUDA tensor if ``device`` else numpy."""
         if device:
@@ -238,6 +272,52 @@ class PoseGraph:
         """Enqueue a solve on the graph's stream without reading a report."""
         o = L.default_options(**opts)
         L.check(self._lib.pgo_solve(self._h, ctypes.byref(o), None, None, L.PGO_MEM_HOST))
+
+
+class _SolveFunction:
+    """Holder for the torch.autograd.Function (built lazily so that the
+    module imports without torch)."""
+    fn = None
+
+    @classmethod
+    def get(cls):
+        if cls.fn is not None:
+            return cls.fn
+        torch = _torch()
+
+        class PoseGraphSolve(torch.autograd.Function):
+            """poses* = argmin_S F(S; Z, w): forward runs the LM solve (with
+            Newton polishing), backward the implicit adjoint (pgo_backward)."""
+
+            @staticmethod
+            def forward(ctx, meas, weight, graph, poses0, opts):
+                graph.set_measurements(meas.detach(), weight.detach())
+                graph.set_poses(poses0.detach())
+                out = torch.empty((graph.n_vertices, 8), dtype=torch.float64, device=meas.device)
+                ctx.report = graph.solve(poses_out=out, **opts)
+                ctx.graph = graph
+                ctx.opts = {k: v for k, v in opts.items() if k in ("pcg_tol", "pcg_max_iters")}
+                return out
+
+            @staticmethod
+            def backward(ctx, grad_poses):
+                dm, dw = ctx.graph.backward(grad_poses.contiguous(), layout="pose8", **ctx.opts)
+                return dm, dw, None, None, None
+
+        cls.fn = PoseGraphSolve
+        return cls.fn
+
+
+def solve_pose_graph(graph, meas, weight, poses0, **opts):
+    """Differentiable solve: poses (N, 8) = argmin F over the graph's
+    structure with measurements ``meas`` (E, 8) and weights ``weight`` (E,),
+    starting from ``poses0``.  Gradients flow back to meas and weight through
+    the implicit adjoint.  ``opts`` are solve options (polish_iters defaults
+    to 8 so that the optimum is a stationary point to full precision)."""
+    opts = dict(opts)
+    opts.setdefault("polish_iters", 8)
+    opts.setdefault("max_iters", 50)
+    return _SolveFunction.get().apply(meas, weight, graph, poses0, opts)
 
 
 def evaluate_cost(n_vertices, edge_i, edge_j, meas, weight, poses):

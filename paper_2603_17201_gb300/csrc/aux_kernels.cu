@@ -37,6 +37,7 @@ __global__ void k_get_poses(DevGraph g, int buf, double* dst) {
 __global__ void __launch_bounds__(256) k_residuals(DevGraph g, int buf, const int* perm, double* r_out,
                                                    double* cost_out) {
   __shared__ double sh[32];
+  if (buf < 0) buf = g.st->cur;
   double c[1] = {0.0};
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < g.E; e += gridDim.x * blockDim.x) {
     const int i = g.ei[e], j = g.ej[e];
@@ -148,6 +149,24 @@ __global__ void __launch_bounds__(128) k_jacobians_out(DevGraph g, int buf, cons
       o[a * 7 + c] = Ai[a][c];
       o[49 + a * 7 + c] = Aj[a][c];
     }
+}
+
+// Caller-order measurements (pose8) and weights -> internal edge order.
+__global__ void k_set_meas(DevGraph g, const int* perm, const double* meas8, const double* weight) {
+  const int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= g.E) return;
+  const int e = perm[k];
+  const double* m = meas8 + (size_t)e * 8;
+  const double n = sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2] + m[3] * m[3]);
+  const_cast<D4*>(g.zq)[k] = D4{m[0] / n, m[1] / n, m[2] / n, m[3] / n};
+  const_cast<D4*>(g.zt)[k] = D4{m[4], m[5], m[6], m[7]};
+  const_cast<double*>(g.zqn)[k] = n;
+  if (weight) const_cast<double*>(g.w)[k] = weight[e];
+}
+
+void launch_set_meas(const DevGraph& g, const int* perm, const double* meas8, const double* weight, cudaStream_t s) {
+  if (g.E == 0) return;
+  k_set_meas<<<(g.E + 127) / 128, 128, 0, s>>>(g, perm, meas8, weight);
 }
 
 void launch_set_poses(const DevGraph& g, const double* src, int buf, cudaStream_t s) {

@@ -137,6 +137,7 @@ struct pgo_graph {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   bool solved = false;
   bool has_info = false;
+  bool lin_valid = false;
 };
 
 struct pgo_batch {
@@ -434,7 +435,7 @@ pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
   });
   std::vector<int> sei(E), sej(E);
   std::vector<D4> zq(E), zt(E);
-  std::vector<double> sw(E), sL(d->info ? (size_t)E * 28 : 0);
+  std::vector<double> sw(E), szqn(E), sL(d->info ? (size_t)E * 28 : 0);
   for (int k = 0; k < E; ++k) {
     const int e = perm[k];
     sei[k] = ei[e];
@@ -442,6 +443,7 @@ pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
     const double* m = &meas[(size_t)e * 8];
     const double n = std::sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2] + m[3] * m[3]);
     zq[k] = D4{m[0] / n, m[1] / n, m[2] / n, m[3] / n};
+    szqn[k] = n;
     zt[k] = D4{m[4], m[5], m[6], m[7]};
     sw[k] = d->weight ? w[e] : 1.0;
     if (d->info) std::memcpy(&sL[(size_t)k * 28], &Lpack[(size_t)e * 28], sizeof(double) * 28);
@@ -482,7 +484,7 @@ pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
   const int pcap = std::max(max_partials(N, E), pcg_partials_needed(N));
   G->scratch_doubles = std::max((size_t)N * 8, (size_t)Ep * 98) + std::max((size_t)N * 49, (size_t)Ep * 49);
   size_t total = 0;
-  total += 2 * arena_bytes<int>(Ep) + 2 * arena_bytes<D4>(Ep) + arena_bytes<double>(Ep);
+  total += 2 * arena_bytes<int>(Ep) + 2 * arena_bytes<D4>(Ep) + 2 * arena_bytes<double>(Ep);
   total += d->info ? arena_bytes<double>(Ep * 28) : 0;
   total += arena_bytes<int>(N + 1) + arena_bytes<int>(N) + 2 * arena_bytes<int>(2 * Ep) + arena_bytes<int>(Ep);
   total += 4 * arena_bytes<D4>(N);
@@ -516,13 +518,14 @@ pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
   D4* d_zq = A.take<D4>(Ep);
   D4* d_zt = A.take<D4>(Ep);
   double* d_w = A.take<double>(Ep);
+  double* d_zqn = A.take<double>(Ep);
   double* d_L = d->info ? A.take<double>(Ep * 28) : nullptr;
   int* d_ptr = A.take<int>(N + 1);
   int* d_split = A.take<int>(N);
   int* d_code = A.take<int>(2 * Ep);
   int* d_other = A.take<int>(2 * Ep);
   G->d_perm = A.take<int>(Ep);
-  g.ei = d_ei; g.ej = d_ej; g.zq = d_zq; g.zt = d_zt; g.w = d_w; g.L = d_L;
+  g.ei = d_ei; g.ej = d_ej; g.zq = d_zq; g.zt = d_zt; g.w = d_w; g.L = d_L; g.zqn = d_zqn;
   g.inc_ptr = d_ptr; g.inc_code = d_code; g.inc_other = d_other; g.inc_split = d_split;
   for (int k = 0; k < 2; ++k) { g.pq[k] = A.take<D4>(N); g.pt[k] = A.take<D4>(N); }
   g.off64 = A.take<double>(Ep * BLK64);
@@ -568,6 +571,7 @@ pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
   ok &= copy_in(d_zq, zq.data(), sizeof(D4) * E, PGO_MEM_HOST, s);
   ok &= copy_in(d_zt, zt.data(), sizeof(D4) * E, PGO_MEM_HOST, s);
   ok &= copy_in(d_w, sw.data(), sizeof(double) * E, PGO_MEM_HOST, s);
+  ok &= copy_in(d_zqn, szqn.data(), sizeof(double) * E, PGO_MEM_HOST, s);
   if (d->info) ok &= copy_in(d_L, sL.data(), sizeof(double) * 28 * E, PGO_MEM_HOST, s);
   ok &= copy_in(d_ptr, inc_ptr.data(), sizeof(int) * (N + 1), PGO_MEM_HOST, s);
   ok &= copy_in(d_split, inc_split.data(), sizeof(int) * N, PGO_MEM_HOST, s);
@@ -752,6 +756,59 @@ pgo_status pgo_graph_damped_step(pgo_graph* G, const pgo_solve_options* opt, dou
   return PGO_OK;
 }
 
+// Undamped Gauss-Newton steps after LM, each kept only while it lowers the
+// gradient norm |b|_2 (LM's cost-based acceptance cannot resolve the last
+// digits of the optimum; the implicit adjoint needs b(x*) ~ 0).  A step that
+// does not lower it is halved up to three times before polishing stops.
+// FP64, host-driven: a few steps with a synchronisation each.
+static pgo_status run_polish(pgo_graph* G, const pgo_solve_options& o) {
+  const DevGraph& g = G->g;
+  cudaStream_t s = G->stream;
+  fill_dev_options(o, G->h_opt);
+  G->h_opt->lambda_fixed = 0.0;
+  CUDA_TRY(cudaMemcpyAsync(g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
+  auto linearize_here = [&](double* b2, double* gmax) -> pgo_status {
+    launch_state_ctl(g, 0, s);
+    launch_linearize(g, 0, s);
+    launch_assemble_mode(g, 2, s);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaMemcpyAsync(G->h_state, g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    *b2 = G->h_state->bnorm2;
+    *gmax = G->h_state->gmax;
+    return PGO_OK;
+  };
+  double b0 = 0.0, g0 = 0.0;
+  pgo_status st = linearize_here(&b0, &g0);
+  if (st != PGO_OK) return st;
+  for (int k = 0; k < o.polish_iters && g0 > o.gtol; ++k) {
+    launch_precond(g, 0, s);
+    CUDA_TRY(launch_pcg(g, 0, 0, s));       // delta = -H^-1 b (x64)
+    bool improved = false;
+    double b1 = 0.0, g1 = 0.0;
+    for (int half = 0; half < 4 && !improved; ++half) {
+      if (half > 0) launch_scale_x(g, 0.5, s);
+      launch_update(g, 0, s);               // candidate into the other buffer
+      launch_state_ctl(g, 1, s);            // make it current
+      st = linearize_here(&b1, &g1);
+      if (st != PGO_OK) return st;
+      improved = b1 < b0;
+      if (!improved) launch_state_ctl(g, 1, s);   // back to the previous poses
+    }
+    if (!improved) {
+      st = linearize_here(&b1, &g1);        // restore b and H at the kept poses
+      if (st != PGO_OK) return st;
+      break;
+    }
+    b0 = b1;
+    g0 = g1;
+  }
+  // the final cost and gradient go into the report
+  launch_residuals(g, -1, G->d_perm, nullptr, &g.st->F, s);
+  CUDA_TRY(cudaGetLastError());
+  return PGO_OK;
+}
+
 pgo_status pgo_graph_resolve(pgo_graph* G, const pgo_solve_options* opt, double lambda, double* delta,
                              int32_t* pcg_iters, int32_t mem_space) {
   if (!G) return fail(PGO_ERR_INVALID_ARG, "graph is NULL");
@@ -842,8 +899,13 @@ pgo_status pgo_solve(pgo_graph* G, const pgo_solve_options* opt, pgo_report* rep
   } else {
     CUDA_TRY(cudaGraphLaunch(ex, s));
   }
+  if (o.polish_iters > 0) {
+    st = run_polish(G, o);
+    if (st != PGO_OK) return st;
+  }
   CUDA_TRY(cudaEventRecord(G->ev1, s));
   G->solved = true;
+  G->lin_valid = true;
   if (poses_out) {
     // the current buffer is only known on the device: gather both and let
     // the device pick (k_get_poses reads st->cur through launch_get_poses)
@@ -865,10 +927,84 @@ pgo_status pgo_solve(pgo_graph* G, const pgo_solve_options* opt, pgo_report* rep
   return PGO_OK;
 }
 
-pgo_status pgo_backward(pgo_graph* G, const pgo_solve_options*, const double*, int32_t, double*, double*, int32_t) {
-  if (!G) return fail(PGO_ERR_INVALID_ARG, "graph is NULL");
+pgo_status pgo_backward(pgo_graph* G, const pgo_solve_options* opt, const double* dL_dposes, int32_t layout,
+                        double* dL_dmeas, double* dL_dweight, int32_t mem_space) {
+  if (!G || !dL_dposes) return fail(PGO_ERR_INVALID_ARG, "graph or dL_dposes is NULL");
+  if (layout != PGO_GRAD_TANGENT7 && layout != PGO_GRAD_POSE8) return fail(PGO_ERR_INVALID_ARG, "bad grad_layout");
+  if (mem_space != PGO_MEM_HOST && mem_space != PGO_MEM_DEVICE) return fail(PGO_ERR_INVALID_ARG, "bad mem_space");
   if (!G->solved) return fail(PGO_ERR_STATE, "pgo_backward needs a completed pgo_solve");
-  return fail(PGO_ERR_STATE, "pgo_backward is not available in this build");
+  pgo_solve_options o;
+  if (opt) o = *opt; else pgo_default_options(&o);
+  pgo_status st = check_options(o);
+  if (st != PGO_OK) return st;
+  cudaStream_t s = G->stream;
+  const DevGraph& g = G->g;
+  const int N = G->N, E = G->E;
+  const int pw = layout == PGO_GRAD_POSE8 ? 8 : 7;
+  // scratch: outputs first (E * pw + E doubles), the input gradient after them
+  double* d_out_meas = G->d_scratch;
+  double* d_out_w = G->d_scratch + (size_t)E * pw;
+  double* d_in = G->d_scratch + std::max((size_t)N * 8, (size_t)(E > 0 ? E : 1) * 98);
+  const double* dl = dL_dposes;
+  if (mem_space == PGO_MEM_HOST) {
+    CUDA_TRY(cudaMemcpyAsync(d_in, dL_dposes, sizeof(double) * pw * N, cudaMemcpyHostToDevice, s));
+    dl = d_in;
+  }
+  fill_dev_options(o, G->h_opt);
+  G->h_opt->lambda_fixed = 0.0;
+  CUDA_TRY(cudaMemcpyAsync(g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
+  launch_state_ctl(g, 0, s);          // done = 0, lambda = 0, tickets cleared
+  launch_adj_hessian(g, s);           // full-Hessian blocks of every edge
+  launch_assemble_mode(g, 1, s);      // diagonal blocks
+  launch_adj_rhs(g, dl, layout, s);   // b = -dL/dx
+  cudaError_t le = cudaSuccess;
+  launch_precond(g, 0, s);
+  le = launch_pcg(g, 0, 0, s);        // mu = H^-1 dL/dx  (x64)
+  CUDA_TRY(le);
+  double* om = dL_dmeas ? (mem_space == PGO_MEM_DEVICE ? dL_dmeas : d_out_meas) : nullptr;
+  double* ow = dL_dweight ? (mem_space == PGO_MEM_DEVICE ? dL_dweight : d_out_w) : nullptr;
+  launch_adj_edges(g, G->d_perm, om, ow, layout, s);
+  CUDA_TRY(cudaGetLastError());
+  CUDA_TRY(cudaMemcpyAsync(G->h_state, g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  G->lin_valid = false;
+  if (mem_space == PGO_MEM_HOST) {
+    if (dL_dmeas) { st = copy_out(dL_dmeas, d_out_meas, sizeof(double) * pw * E, mem_space, s); if (st) return st; }
+    if (dL_dweight) { st = copy_out(dL_dweight, d_out_w, sizeof(double) * E, mem_space, s); if (st) return st; }
+  }
+  if (G->h_state->status) return fail((pgo_status)G->h_state->status, "adjoint solve failed on the device");
+  if (G->h_state->pcg_hit_cap) return fail(PGO_ERR_NOT_CONVERGED, "adjoint PCG reached pcg_max_iters (%d)", o.pcg_max_iters);
+  return PGO_OK;
+}
+
+pgo_status pgo_graph_set_measurements(pgo_graph* G, const double* meas, const double* weight, int32_t mem_space) {
+  if (!G || !meas) return fail(PGO_ERR_INVALID_ARG, "graph or meas is NULL");
+  if (mem_space != PGO_MEM_HOST && mem_space != PGO_MEM_DEVICE) return fail(PGO_ERR_INVALID_ARG, "bad mem_space");
+  cudaStream_t s = G->stream;
+  const int E = G->E;
+  if (E == 0) return PGO_OK;
+  const double* dm = meas;
+  const double* dw = weight;
+  if (mem_space == PGO_MEM_HOST) {
+    for (int e = 0; e < E; ++e) {
+      if (!finite_pose(&meas[(size_t)e * 8]))
+        return fail(PGO_ERR_INVALID_ARG, "edge %d: measurement not finite, zero quaternion or scale <= 0", e);
+      if (weight && !(std::isfinite(weight[e]) && weight[e] >= 0.0))
+        return fail(PGO_ERR_INVALID_ARG, "edge %d: weight must be finite and >= 0", e);
+    }
+    double* tm = G->d_scratch;
+    double* tw = G->d_scratch + (size_t)E * 8;
+    CUDA_TRY(cudaMemcpyAsync(tm, meas, sizeof(double) * 8 * E, cudaMemcpyHostToDevice, s));
+    if (weight) CUDA_TRY(cudaMemcpyAsync(tw, weight, sizeof(double) * E, cudaMemcpyHostToDevice, s));
+    dm = tm;
+    dw = weight ? tw : nullptr;
+  }
+  launch_set_meas(G->g, G->d_perm, dm, dw, s);
+  CUDA_TRY(cudaGetLastError());
+  if (mem_space == PGO_MEM_HOST) CUDA_TRY(cudaStreamSynchronize(s));
+  G->solved = false;
+  G->lin_valid = false;
+  return PGO_OK;
 }
 
 pgo_status pgo_batch_create(int32_t, const pgo_graph_desc*, void*, pgo_batch** out) {

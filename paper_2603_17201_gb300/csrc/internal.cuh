@@ -59,6 +59,7 @@ struct DevGraph {
   const D4* zq;           // measurement quaternion (x, y, z, w), normalised
   const D4* zt;           // measurement (tx, ty, tz, s)
   const double* w;        // weight per edge
+  const double* zqn;      // norm of the caller's measurement quaternion (pose8 gradients)
   const double* L;        // E x 28 lower-triangular factor of Omega, or nullptr
   const int* inc_ptr;     // N + 1: incidence CSR over vertices
   const int* inc_code;    // 2E: edge * 2 + side (0: vertex is i, 1: vertex is j)
@@ -94,6 +95,19 @@ struct DevGraph {
 void launch_cost(const DevGraph& g, int mode, cudaStream_t s, unsigned long long lm_cond);
 void launch_linearize(const DevGraph& g, int mixed, cudaStream_t s);
 void launch_assemble(const DevGraph& g, int mixed, cudaStream_t s);
+// mode 1: full-Hessian assembly for the adjoint; mode 2: polish step
+// (both skip the LM lambda_0 and gradient-stop logic)
+void launch_assemble_mode(const DevGraph& g, int mode, cudaStream_t s);
+void launch_adj_hessian(const DevGraph& g, cudaStream_t s);
+void launch_adj_rhs(const DevGraph& g, const double* dL, int layout, cudaStream_t s);
+void launch_adj_edges(const DevGraph& g, const int* perm, double* dL_dmeas, double* dL_dw, int layout,
+                      cudaStream_t s);
+void launch_set_meas(const DevGraph& g, const int* perm, const double* meas8, const double* weight,
+                     cudaStream_t s);
+// state control: 0 prepare a standalone step at lambda = opt->lambda_fixed
+// (done = 0, need_lin = 1), 1 swap the current pose buffer
+void launch_state_ctl(const DevGraph& g, int op, cudaStream_t s);
+void launch_scale_x(const DevGraph& g, double f, cudaStream_t s);
 void launch_precond(const DevGraph& g, int mixed, cudaStream_t s);
 cudaError_t launch_pcg(const DevGraph& g, int mixed, int from_residual, cudaStream_t s);
 int pcg_partials_needed(int N);

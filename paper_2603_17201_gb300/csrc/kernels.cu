@@ -73,9 +73,9 @@ __global__ void __launch_bounds__(128) k_linearize(DevGraph g, int mixed) {
 // order (deterministic), then write H_vv (full symmetric) and b_v.  The last
 // block derives max diag(H), |b|_inf and |b|^2 over the free vertices, sets
 // lambda_0 on the first linearisation and applies the gradient stop test.
-__global__ void __launch_bounds__(256) k_assemble(DevGraph g, int mixed) {
+__global__ void __launch_bounds__(256) k_assemble(DevGraph g, int mixed, int mode) {
   SolverState* st = g.st;
-  if (st->done || !st->need_lin) return;
+  if (mode == 0 && (st->done || !st->need_lin)) return;
   __shared__ double sh[32 * 3];
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = tid >> 3, lane = tid & 7;
@@ -137,6 +137,10 @@ __global__ void __launch_bounds__(256) k_assemble(DevGraph g, int mixed) {
       st->maxdiag = m2[0];
       st->gmax = m2[1];
       st->bnorm2 = s1[0];
+      if (mode != 0) {
+        st->need_lin = 0;
+        return;
+      }
       if (st->lambda < 0.0) st->lambda = (o->lambda_init > 0.0) ? o->lambda_init : o->tau * m2[0];
       st->need_lin = 0;
       if (!(m2[1] > o->gtol)) {
@@ -332,7 +336,40 @@ void launch_linearize(const DevGraph& g, int mixed, cudaStream_t s) {
 
 void launch_assemble(const DevGraph& g, int mixed, cudaStream_t s) {
   int blocks = (g.N * 8 + 255) / 256;
-  k_assemble<<<blocks, 256, 0, s>>>(g, mixed);
+  k_assemble<<<blocks, 256, 0, s>>>(g, mixed, 0);
+}
+
+void launch_assemble_mode(const DevGraph& g, int mode, cudaStream_t s) {
+  int blocks = (g.N * 8 + 255) / 256;
+  k_assemble<<<blocks, 256, 0, s>>>(g, 0, mode);
+}
+
+// 0: standalone step at opt->lambda_fixed; 1: swap the current pose buffer.
+__global__ void k_state_ctl(DevGraph g, int op) {
+  SolverState* st = g.st;
+  if (op == 0) {
+    st->done = 0;
+    st->need_lin = 1;
+    st->ref_done = 0;
+    st->status = 0;
+    st->pcg_hit_cap = 0;
+    st->lambda = g.opt->lambda_fixed;
+    for (int t = 0; t < T_COUNT; ++t) st->ticket[t] = 0u;
+  } else {
+    st->cur ^= 1;
+  }
+}
+
+void launch_state_ctl(const DevGraph& g, int op, cudaStream_t s) { k_state_ctl<<<1, 1, 0, s>>>(g, op); }
+
+// x64 *= f (step halving of the Newton polish).
+__global__ void k_scale_x(DevGraph g, double f) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < g.N * VEC) g.x64[t] *= f;
+}
+
+void launch_scale_x(const DevGraph& g, double f, cudaStream_t s) {
+  k_scale_x<<<(g.N * VEC + 255) / 256, 256, 0, s>>>(g, f);
 }
 
 void launch_update(const DevGraph& g, int mixed, cudaStream_t s) {
