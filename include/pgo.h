@@ -236,11 +236,23 @@ pgo_status pgo_batch_create(int32_t n_graphs, const pgo_graph_desc* descs, void*
 void pgo_batch_destroy(pgo_batch* b);
 
 /* Solve every graph of the batch with LM (same rules as pgo_solve, per-graph
- * lambda, acceptance and stopping).  reports: host array of n_graphs
- * (nullable).  poses_out: host array of n_graphs pointers, each
- * double[n_vertices_k * 8] in out_mem_space (nullable). */
+ * lambda, acceptance and stopping), starting from each graph's current
+ * estimate.  One persistent kernel launch (a one-node CUDA graph): each
+ * thread block solves whole graphs taken from a device work queue, largest
+ * first.  opt->schedule < 0 picks the launch schedule (lanes per block row,
+ * threads per block) with the autotuner on the first solve of each
+ * precision (one timed LM iteration per candidate; the estimate is restored
+ * after each trial); a schedule id >= 0 forces one.  reports: host array of
+ * n_graphs (nullable; ms_total is the whole batch).  poses_out: host array
+ * of n_graphs pointers, each double[n_vertices_k * 8] in out_mem_space
+ * (nullable).  With both NULL the call only enqueues the solve. */
 pgo_status pgo_batch_solve(pgo_batch* b, const pgo_solve_options* opt, pgo_report* reports,
                            double* const* poses_out, int32_t out_mem_space);
+
+/* The schedule of the last batch solve: lanes per block row in the SpMV,
+ * threads per block, and the autotuner's best trial time in ms (nullable
+ * outputs).  PGO_ERR_STATE before the first solve. */
+pgo_status pgo_batch_schedule(const pgo_batch* b, int32_t* lanes, int32_t* threads, float* tune_ms);
 
 /* Stateless cost evaluation (the Sec. IV-F objective) over caller-owned
  * device arrays: n_vertices poses (pose8), n_edges edges (edge_i, edge_j,

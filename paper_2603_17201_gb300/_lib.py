@@ -38,7 +38,7 @@ EXPORTED = [
     "pgo_last_error", "pgo_version", "pgo_default_options", "pgo_graph_create", "pgo_graph_destroy",
     "pgo_graph_set_poses", "pgo_graph_set_measurements", "pgo_graph_get_poses", "pgo_graph_cost", "pgo_graph_linearize",
     "pgo_graph_damped_step", "pgo_graph_resolve", "pgo_graph_report", "pgo_solve", "pgo_backward", "pgo_batch_create", "pgo_batch_destroy",
-    "pgo_batch_solve", "pgo_evaluate_cost", "pgo_evaluate_cost_noalloc",
+    "pgo_batch_solve", "pgo_batch_schedule", "pgo_evaluate_cost", "pgo_evaluate_cost_noalloc",
 ]
 
 
@@ -110,8 +110,9 @@ def load(build_if_missing: bool = True):
         lib.pgo_batch_create.argtypes = [c_int32, ctypes.POINTER(GraphDesc), vp, ctypes.POINTER(vp)]
         lib.pgo_batch_destroy.argtypes = [vp]
         lib.pgo_batch_destroy.restype = None
-        lib.pgo_batch_solve.argtypes = [vp, ctypes.POINTER(SolveOptions), ctypes.POINTER(Report),
-                                        ctypes.POINTER(vp), c_int32]
+        lib.pgo_batch_solve.argtypes = [vp, ctypes.POINTER(SolveOptions), ctypes.POINTER(Report), vp, c_int32]
+        lib.pgo_batch_schedule.argtypes = [vp, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
+                                           ctypes.POINTER(ctypes.c_float)]
         lib.pgo_evaluate_cost.argtypes = [c_int32, c_int32, vp, vp, vp, vp, vp, vp, vp]
         lib.pgo_evaluate_cost_noalloc.argtypes = [c_int32, c_int32, vp, vp, vp, vp, vp, vp, vp]
         for name in EXPORTED:

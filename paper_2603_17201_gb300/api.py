@@ -15,7 +15,7 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["PoseGraph", "evaluate_cost", "default_options", "PGOError", "solve_pose_graph"]
+__all__ = ["PoseGraph", "PoseGraphBatch", "evaluate_cost", "default_options", "PGOError", "solve_pose_graph"]
 
 PGOError = L.PGOError
 default_options = L.default_options
@@ -272,6 +272,69 @@ class PoseGraph:
         """Enqueue a solve on the graph's stream without reading a report."""
         o = L.default_options(**opts)
         L.check(self._lib.pgo_solve(self._h, ctypes.byref(o), None, None, L.PGO_MEM_HOST))
+
+
+class PoseGraphBatch:
+    """Many independent essential graphs solved together (see
+    ``pgo_batch_create`` / ``pgo_batch_solve``): one persistent launch in
+    which each thread block solves whole graphs."""
+
+    def __init__(self, graphs, stream=None):
+        """graphs: sequence of synthetic.PoseGraph-like objects (n_vertices,
+        edge_i, edge_j, meas, weight, poses_init, fixed_vertex)."""
+        self._lib = L.load()
+        self._h = ctypes.c_void_p()
+        n = len(graphs)
+        descs = (L.GraphDesc * n)()
+        m = _Marshal(False)
+        self.sizes = []
+        for k, g in enumerate(graphs):
+            d = descs[k]
+            E = int(len(g.edge_i))
+            d.n_vertices = int(g.n_vertices)
+            d.n_edges = E
+            d.fixed_vertex = int(getattr(g, "fixed_vertex", 0))
+            d.mem_space = L.PGO_MEM_HOST
+            d.edge_i = m.put(g.edge_i, np.int32)
+            d.edge_j = m.put(g.edge_j, np.int32)
+            d.meas = m.put(g.meas, np.float64, (E, 8))
+            d.weight = m.put(getattr(g, "weight", None), np.float64, (E,))
+            d.poses = m.put(getattr(g, "poses_init", None), np.float64, (int(g.n_vertices), 8))
+            self.sizes.append((int(g.n_vertices), E))
+        s = stream if stream is not None else _current_stream_handle()
+        L.check(self._lib.pgo_batch_create(n, descs, s, ctypes.byref(self._h)))
+        self.n_graphs = n
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.pgo_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, poses=True, **opts):
+        """Solve every graph; returns (list of report dicts, list of (N_k, 8)
+        numpy pose arrays or None)."""
+        o = L.default_options(**opts)
+        reps = (L.Report * self.n_graphs)()
+        outs = [np.empty((nv, 8)) for nv, _ in self.sizes] if poses else None
+        ptrs = (ctypes.c_void_p * self.n_graphs)(*[o_.ctypes.data for o_ in outs]) if poses else None
+        L.check(self._lib.pgo_batch_solve(self._h, ctypes.byref(o), reps, ptrs, L.PGO_MEM_HOST))
+        return [r.as_dict() for r in reps], outs
+
+    def solve_async(self, **opts):
+        o = L.default_options(**opts)
+        L.check(self._lib.pgo_batch_solve(self._h, ctypes.byref(o), None, None, L.PGO_MEM_HOST))
+
+    def schedule(self):
+        """(lanes per block row, threads per block, autotuner best trial ms)."""
+        lanes, threads, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+        L.check(self._lib.pgo_batch_schedule(self._h, ctypes.byref(lanes), ctypes.byref(threads), ctypes.byref(ms)))
+        return lanes.value, threads.value, ms.value
 
 
 class _SolveFunction:

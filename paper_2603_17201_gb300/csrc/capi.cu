@@ -141,8 +141,16 @@ struct pgo_graph {
 };
 
 struct pgo_batch {
-  std::vector<pgo_graph*> graphs;
-  cudaStream_t stream = nullptr;
+  pgo_graph* G = nullptr;          // the graphs concatenated (disjoint vertex and edge ranges)
+  int n = 0;
+  std::vector<int> nv, ne, v0;
+  BatchArgs args{};                // device pointers
+  void* meta = nullptr;            // device allocation holding the per-graph arrays
+  double* saved_poses = nullptr;   // autotuning: the estimate to restore after each trial
+  int schedule = -1;               // tuned schedule per precision
+  int tuned[2] = {-1, -1};
+  float tune_ms[2] = {0.f, 0.f};
+  std::map<int, cudaGraphExec_t> execs;
 };
 
 namespace {
@@ -1007,13 +1015,300 @@ pgo_status pgo_graph_set_measurements(pgo_graph* G, const double* meas, const do
   return PGO_OK;
 }
 
-pgo_status pgo_batch_create(int32_t, const pgo_graph_desc*, void*, pgo_batch** out) {
-  if (out) *out = nullptr;
-  return fail(PGO_ERR_STATE, "batched solve is not available in this build");
+pgo_status pgo_batch_create(int32_t n_graphs, const pgo_graph_desc* descs, void* stream, pgo_batch** out) {
+  if (!out) return fail(PGO_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (n_graphs < 1 || !descs) return fail(PGO_ERR_INVALID_ARG, "need n_graphs >= 1 and a descs array");
+  std::vector<int32_t> ei, ej;
+  std::vector<double> meas, w, info, poses;
+  std::vector<int> nv(n_graphs), ne(n_graphs), v0(n_graphs), e0(n_graphs), fixed(n_graphs);
+  bool any_w = false, any_info = false;
+  for (int k = 0; k < n_graphs; ++k) {
+    any_w |= descs[k].weight != nullptr;
+    any_info |= descs[k].info != nullptr;
+  }
+  long long V = 0, Etot = 0;
+  for (int k = 0; k < n_graphs; ++k) {
+    const pgo_graph_desc& d = descs[k];
+    if (d.n_vertices < 1 || d.n_edges < 0 || d.fixed_vertex < 0 || d.fixed_vertex >= d.n_vertices)
+      return fail(PGO_ERR_INVALID_ARG, "graph %d: bad sizes or fixed vertex", k);
+    if (d.mem_space != PGO_MEM_HOST && d.mem_space != PGO_MEM_DEVICE)
+      return fail(PGO_ERR_INVALID_ARG, "graph %d: bad mem_space", k);
+    if (d.n_edges > 0 && (!d.edge_i || !d.edge_j || !d.meas)) return fail(PGO_ERR_INVALID_ARG, "graph %d: NULL edge arrays", k);
+    nv[k] = d.n_vertices;
+    ne[k] = d.n_edges;
+    v0[k] = (int)V;
+    e0[k] = (int)Etot;
+    fixed[k] = (int)V + d.fixed_vertex;
+    std::vector<int32_t> a, b;
+    std::vector<double> m, ww, ii, pp;
+    if (!fetch(a, d.edge_i, d.n_edges, d.mem_space) || !fetch(b, d.edge_j, d.n_edges, d.mem_space) ||
+        !fetch(m, d.meas, (size_t)d.n_edges * 8, d.mem_space))
+      return fail(PGO_ERR_CUDA, "graph %d: reading edge arrays failed", k);
+    for (int e = 0; e < d.n_edges; ++e) {
+      if (a[e] < 0 || a[e] >= d.n_vertices || b[e] < 0 || b[e] >= d.n_vertices)
+        return fail(PGO_ERR_INVALID_ARG, "graph %d edge %d: endpoint out of range", k, e);
+      ei.push_back(a[e] + (int)V);
+      ej.push_back(b[e] + (int)V);
+    }
+    meas.insert(meas.end(), m.begin(), m.end());
+    if (any_w) {
+      if (d.weight) {
+        if (!fetch(ww, d.weight, d.n_edges, d.mem_space)) return fail(PGO_ERR_CUDA, "reading weights failed");
+      } else {
+        ww.assign(d.n_edges, 1.0);
+      }
+      w.insert(w.end(), ww.begin(), ww.end());
+    }
+    if (any_info) {
+      if (d.info) {
+        if (!fetch(ii, d.info, (size_t)d.n_edges * 49, d.mem_space)) return fail(PGO_ERR_CUDA, "reading info failed");
+      } else {
+        ii.assign((size_t)d.n_edges * 49, 0.0);
+        for (int e = 0; e < d.n_edges; ++e)
+          for (int q = 0; q < 7; ++q) ii[(size_t)e * 49 + q * 8] = 1.0;
+      }
+      info.insert(info.end(), ii.begin(), ii.end());
+    }
+    if (d.poses) {
+      if (!fetch(pp, d.poses, (size_t)d.n_vertices * 8, d.mem_space)) return fail(PGO_ERR_CUDA, "reading poses failed");
+    } else {
+      pp.assign((size_t)d.n_vertices * 8, 0.0);
+      for (int v = 0; v < d.n_vertices; ++v) { pp[(size_t)v * 8 + 3] = 1.0; pp[(size_t)v * 8 + 7] = 1.0; }
+    }
+    poses.insert(poses.end(), pp.begin(), pp.end());
+    V += d.n_vertices;
+    Etot += d.n_edges;
+    if (V > 0x3fffffffLL || Etot > 0x3fffffffLL) return fail(PGO_ERR_INVALID_ARG, "batch too large");
+  }
+  pgo_graph_desc big = {};
+  big.n_vertices = (int)V;
+  big.n_edges = (int)Etot;
+  big.fixed_vertex = fixed[0];
+  big.mem_space = PGO_MEM_HOST;
+  big.edge_i = ei.data();
+  big.edge_j = ej.data();
+  big.meas = meas.data();
+  big.weight = any_w ? w.data() : nullptr;
+  big.info = any_info ? info.data() : nullptr;
+  big.poses = poses.data();
+  big.stream = stream;
+  pgo_graph* G = nullptr;
+  pgo_status st = pgo_graph_create(&big, &G);
+  if (st != PGO_OK) return st;
+  pgo_batch* B = new pgo_batch();
+  B->G = G;
+  B->n = n_graphs;
+  B->nv = nv;
+  B->ne = ne;
+  B->v0 = v0;
+  // processing order: largest graphs first (longest-processing-time rule)
+  std::vector<int> order(n_graphs);
+  std::iota(order.begin(), order.end(), 0);
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    return (long long)ne[a] + nv[a] > (long long)ne[b] + nv[b];
+  });
+  const size_t ints = (size_t)n_graphs * 6 + 4;
+  const size_t bytes = ints * sizeof(int) + 256 + (size_t)n_graphs * sizeof(BatchGraphState);
+  cudaError_t ce = cudaMalloc(&B->meta, bytes);
+  if (ce == cudaSuccess) ce = cudaMalloc(&B->saved_poses, sizeof(D4) * 2 * (size_t)V);
+  if (ce != cudaSuccess) {
+    cudaGetLastError();
+    pgo_batch_destroy(B);
+    return fail(ce == cudaErrorMemoryAllocation ? PGO_ERR_OOM : PGO_ERR_CUDA, "batch metadata: %s", cudaGetErrorString(ce));
+  }
+  int* m = reinterpret_cast<int*>(B->meta);
+  std::vector<int> hostm(ints, 0);
+  for (int k = 0; k < n_graphs; ++k) {
+    hostm[k] = v0[k];
+    hostm[n_graphs + k] = nv[k];
+    hostm[2 * n_graphs + k] = e0[k];
+    hostm[3 * n_graphs + k] = ne[k];
+    hostm[4 * n_graphs + k] = fixed[k];
+    hostm[5 * n_graphs + k] = order[k];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  BatchArgs& a = B->args;
+  a.n_graphs = n_graphs;
+  a.v0 = m;
+  a.nv = m + n_graphs;
+  a.e0 = m + 2 * n_graphs;
+  a.ne = m + 3 * n_graphs;
+  a.fixed = m + 4 * n_graphs;
+  a.order = m + 5 * n_graphs;
+  a.queue = reinterpret_cast<unsigned*>(m + 6 * n_graphs);
+  a.gst = reinterpret_cast<BatchGraphState*>(reinterpret_cast<char*>(B->meta) + ((ints * sizeof(int) + 255) & ~size_t(255)));
+  bool ok = cudaMemcpyAsync(m, hostm.data(), ints * sizeof(int), cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok &= cudaMemsetAsync(a.gst, 0, (size_t)n_graphs * sizeof(BatchGraphState), s) == cudaSuccess;
+  ok &= cudaStreamSynchronize(s) == cudaSuccess;
+  if (!ok) {
+    pgo_batch_destroy(B);
+    return fail(PGO_ERR_CUDA, "uploading batch metadata failed");
+  }
+  *out = B;
+  return PGO_OK;
 }
-void pgo_batch_destroy(pgo_batch* b) { delete b; }
-pgo_status pgo_batch_solve(pgo_batch*, const pgo_solve_options*, pgo_report*, double* const*, int32_t) {
-  return fail(PGO_ERR_STATE, "batched solve is not available in this build");
+
+void pgo_batch_destroy(pgo_batch* B) {
+  if (!B) return;
+  for (auto& kv : B->execs) cudaGraphExecDestroy(kv.second);
+  if (B->G) pgo_graph_destroy(B->G);   // synchronises the stream
+  if (B->meta) cudaFree(B->meta);
+  if (B->saved_poses) cudaFree(B->saved_poses);
+  delete B;
+}
+
+static pgo_status batch_exec(pgo_batch* B, int schedule, cudaGraphExec_t* out) {
+  auto it = B->execs.find(schedule);
+  if (it != B->execs.end()) {
+    *out = it->second;
+    return PGO_OK;
+  }
+  pgo_graph* G = B->G;
+  cudaGraph_t graph;
+  CUDA_TRY(cudaGraphCreate(&graph, 0));
+  GraphBuilder gb{G->cap_stream};
+  cudaError_t le = cudaSuccess;
+  gb.capture(graph, [&](cudaStream_t s) {
+    launch_batch_reset(G->g, B->args, s);
+    cudaMemsetAsync(B->args.queue, 0, sizeof(unsigned), s);
+    le = launch_batch_lm(G->g, B->args, schedule, s);
+  });
+  if (le != cudaSuccess) gb.err = le;
+  if (gb.err != cudaSuccess) {
+    cudaGraphDestroy(graph);
+    return fail(PGO_ERR_CUDA, "building the batch graph: %s", cudaGetErrorString(gb.err));
+  }
+  cudaGraphExec_t ex;
+  cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(PGO_ERR_CUDA, "instantiating the batch graph: %s", cudaGetErrorString(e));
+  B->execs[schedule] = ex;
+  *out = ex;
+  return PGO_OK;
+}
+
+// Autotuner: time one LM iteration (PCG capped at 40 iterations) of the
+// whole batch for every schedule of the requested precision and keep the
+// fastest; the estimate is restored after every trial.
+static pgo_status batch_autotune(pgo_batch* B, const pgo_solve_options& o, int mixed) {
+  pgo_graph* G = B->G;
+  cudaStream_t s = G->stream;
+  const size_t nbytes = sizeof(D4) * (size_t)G->N;
+  launch_batch_reset(G->g, B->args, s);   // current estimate into buffer 0
+  char* saved_q = reinterpret_cast<char*>(B->saved_poses);
+  char* saved_t = saved_q + nbytes;
+  CUDA_TRY(cudaMemcpyAsync(saved_q, G->g.pq[0], nbytes, cudaMemcpyDeviceToDevice, s));
+  CUDA_TRY(cudaMemcpyAsync(saved_t, G->g.pt[0], nbytes, cudaMemcpyDeviceToDevice, s));
+  pgo_solve_options t = o;
+  t.max_iters = 1;
+  t.pcg_max_iters = std::min(o.pcg_max_iters, 40);
+  fill_dev_options(t, G->h_opt);
+  CUDA_TRY(cudaMemcpyAsync(G->g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
+  float best = 1e30f;
+  int best_s = -1;
+  for (int sc = 0; sc < batch_schedule_count(); ++sc) {
+    if (batch_schedule_mixed(sc) != mixed) continue;
+    cudaGraphExec_t ex;
+    pgo_status st = batch_exec(B, sc, &ex);
+    if (st != PGO_OK) return st;
+    float ms = 0.f;
+    for (int rep = 0; rep < 2; ++rep) {   // first run warms up
+      CUDA_TRY(cudaEventRecord(G->ev0, s));
+      CUDA_TRY(cudaGraphLaunch(ex, s));
+      CUDA_TRY(cudaEventRecord(G->ev1, s));
+      CUDA_TRY(cudaEventSynchronize(G->ev1));
+      CUDA_TRY(cudaEventElapsedTime(&ms, G->ev0, G->ev1));
+      // restore the estimate
+      CUDA_TRY(cudaMemcpyAsync(G->g.pq[0], saved_q, nbytes, cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemcpyAsync(G->g.pt[0], saved_t, nbytes, cudaMemcpyDeviceToDevice, s));
+      CUDA_TRY(cudaMemsetAsync(B->args.gst, 0, (size_t)B->n * sizeof(BatchGraphState), s));
+    }
+    if (ms < best) {
+      best = ms;
+      best_s = sc;
+    }
+  }
+  if (best_s < 0) return fail(PGO_ERR_STATE, "no batch schedule for this precision");
+  B->tuned[mixed] = best_s;
+  B->tune_ms[mixed] = best;
+  return PGO_OK;
+}
+
+pgo_status pgo_batch_solve(pgo_batch* B, const pgo_solve_options* opt, pgo_report* reports, double* const* poses_out,
+                           int32_t out_mem_space) {
+  if (!B) return fail(PGO_ERR_INVALID_ARG, "batch is NULL");
+  pgo_solve_options o;
+  if (opt) o = *opt; else pgo_default_options(&o);
+  pgo_status st = check_options(o);
+  if (st != PGO_OK) return st;
+  if (poses_out && out_mem_space != PGO_MEM_HOST && out_mem_space != PGO_MEM_DEVICE)
+    return fail(PGO_ERR_INVALID_ARG, "bad out_mem_space");
+  pgo_graph* G = B->G;
+  cudaStream_t s = G->stream;
+  const int mixed = o.precision == PGO_MIXED;
+  int sc = o.schedule;
+  if (sc >= 0) {
+    if (sc >= batch_schedule_count() || batch_schedule_mixed(sc) != mixed)
+      return fail(PGO_ERR_INVALID_ARG, "schedule %d does not exist for this precision", sc);
+  } else {
+    if (B->tuned[mixed] < 0) {
+      st = batch_autotune(B, o, mixed);
+      if (st != PGO_OK) return st;
+    }
+    sc = B->tuned[mixed];
+  }
+  B->schedule = sc;
+  cudaGraphExec_t ex;
+  st = batch_exec(B, sc, &ex);
+  if (st != PGO_OK) return st;
+  fill_dev_options(o, G->h_opt);
+  CUDA_TRY(cudaMemcpyAsync(G->g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
+  CUDA_TRY(cudaEventRecord(G->ev0, s));
+  CUDA_TRY(cudaGraphLaunch(ex, s));
+  CUDA_TRY(cudaEventRecord(G->ev1, s));
+  if (!reports && !poses_out) return PGO_OK;
+  std::vector<BatchGraphState> hs(B->n);
+  CUDA_TRY(cudaMemcpyAsync(hs.data(), B->args.gst, sizeof(BatchGraphState) * B->n, cudaMemcpyDeviceToHost, s));
+  if (poses_out) {
+    launch_batch_get_poses(G->g, B->args, G->d_scratch, s);
+    CUDA_TRY(cudaGetLastError());
+    cudaMemcpyKind kind = out_mem_space == PGO_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    for (int k = 0; k < B->n; ++k)
+      if (poses_out[k])
+        CUDA_TRY(cudaMemcpyAsync(poses_out[k], G->d_scratch + (size_t)B->v0[k] * 8, sizeof(double) * 8 * B->nv[k], kind, s));
+  }
+  CUDA_TRY(cudaStreamSynchronize(s));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, G->ev0, G->ev1);
+  int bad = 0;
+  for (int k = 0; k < B->n; ++k) {
+    if (hs[k].status) bad = hs[k].status;
+    if (!reports) continue;
+    pgo_report& r = reports[k];
+    std::memset(&r, 0, sizeof(r));
+    r.initial_cost = hs[k].F0;
+    r.final_cost = hs[k].F;
+    r.final_lambda = hs[k].lambda;
+    r.grad_inf_norm = hs[k].gmax;
+    r.iterations = hs[k].it;
+    r.accepted = hs[k].accepted;
+    r.pcg_iterations = hs[k].pcg_total;
+    r.stop_reason = hs[k].stop_reason;
+    r.status = hs[k].status;
+    r.ms_total = ms;
+  }
+  if (bad) return fail((pgo_status)bad, "a graph of the batch failed on the device (status %d)", bad);
+  return PGO_OK;
+}
+
+pgo_status pgo_batch_schedule(const pgo_batch* B, int32_t* lanes, int32_t* threads, float* tune_ms) {
+  if (!B) return fail(PGO_ERR_INVALID_ARG, "batch is NULL");
+  if (B->schedule < 0) return fail(PGO_ERR_STATE, "no batch solve has run");
+  if (lanes) *lanes = batch_schedule_lanes(B->schedule);
+  if (threads) *threads = batch_schedule_threads(B->schedule);
+  if (tune_ms) *tune_ms = B->tune_ms[batch_schedule_mixed(B->schedule)];
+  return PGO_OK;
 }
 
 pgo_status pgo_evaluate_cost(int32_t n_vertices, int32_t n_edges, const int32_t* edge_i, const int32_t* edge_j,

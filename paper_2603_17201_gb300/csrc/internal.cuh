@@ -89,6 +89,32 @@ struct DevGraph {
   DevOptions* opt;
 };
 
+// ---- batched form (one thread block solves one graph at a time) ----
+struct BatchGraphState {
+  double F0, F, lambda, gmax;
+  int it, accepted, pcg_total, stop_reason, status, cur, pad0, pad1;
+};
+
+struct BatchArgs {
+  int n_graphs;
+  const int* v0;       // first vertex of each graph (global index)
+  const int* nv;       // vertices per graph
+  const int* e0;       // first edge (internal order)
+  const int* ne;       // edges per graph
+  const int* fixed;    // global index of each graph's fixed vertex
+  const int* order;    // processing order (largest first)
+  unsigned* queue;     // work counter (zeroed before the launch)
+  BatchGraphState* gst;
+};
+
+int batch_schedule_count();
+int batch_schedule_mixed(int s);
+int batch_schedule_lanes(int s);
+int batch_schedule_threads(int s);
+cudaError_t launch_batch_lm(const DevGraph& g, const BatchArgs& a, int schedule, cudaStream_t s);
+void launch_batch_get_poses(const DevGraph& g, const BatchArgs& a, double* dst, cudaStream_t s);
+void launch_batch_reset(const DevGraph& g, const BatchArgs& a, cudaStream_t s);
+
 // ---- launchers (each enqueues on `s`; inside stream capture they become
 // graph nodes).  `cond` is a graph conditional handle set by the last block
 // of the kernel, or 0 when the kernel is not inside a conditional body. ----

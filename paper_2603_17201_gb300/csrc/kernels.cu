@@ -8,15 +8,9 @@
 //   k_update        candidate poses exp(delta) S and the predicted decrease.
 #include <cfloat>
 
-#include "edge.cuh"
+#include "phases.cuh"
 
 namespace pgo {
-
-// packed upper-triangular index (a <= c) of a symmetric 7x7 block
-__device__ __forceinline__ int upk(int a, int c) { return a * 7 - (a * (a - 1)) / 2 + (c - a); }
-
-__constant__ unsigned char c_up_a[28] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 6};
-__constant__ unsigned char c_up_c[28] = {0, 1, 2, 3, 4, 5, 6, 1, 2, 3, 4, 5, 6, 2, 3, 4, 5, 6, 3, 4, 5, 6, 4, 5, 6, 5, 6, 6};
 
 // K1: one thread per edge.
 __global__ void __launch_bounds__(128) k_linearize(DevGraph g, int mixed) {
@@ -24,49 +18,7 @@ __global__ void __launch_bounds__(128) k_linearize(DevGraph g, int mixed) {
   if (st->done || !st->need_lin) return;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.E) return;
-  double r[7], Ai[7][7], Aj[7][7];
-  edge_jacobians(g, st->cur, e, r, Ai, Aj);
-  const double w = g.w[e];
-  // off-diagonal (i, j) block: w A_i^T A_j
-  double* off = g.off64 + (size_t)e * BLK64;
-  float* off32 = mixed ? g.off32 + (size_t)e * BLK32 : nullptr;
-#pragma unroll
-  for (int a = 0; a < 7; ++a) {
-#pragma unroll
-    for (int c = 0; c < 7; ++c) {
-      double s = 0.0;
-#pragma unroll
-      for (int k = 0; k < 7; ++k) s += Ai[k][a] * Aj[k][c];
-      s *= w;
-      off[a * 7 + c] = s;
-      if (mixed) off32[a * 7 + c] = (float)s;
-    }
-  }
-  // per-side contributions: upper(w A^T A) and w A^T r
-  double* ci = g.contrib + (size_t)e * 2 * CONTRIB;
-  double* cj = ci + CONTRIB;
-#pragma unroll
-  for (int a = 0; a < 7; ++a) {
-#pragma unroll
-    for (int c = a; c < 7; ++c) {
-      double si = 0.0, sj = 0.0;
-#pragma unroll
-      for (int k = 0; k < 7; ++k) {
-        si += Ai[k][a] * Ai[k][c];
-        sj += Aj[k][a] * Aj[k][c];
-      }
-      ci[upk(a, c)] = w * si;
-      cj[upk(a, c)] = w * sj;
-    }
-    double gi = 0.0, gj = 0.0;
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-      gi += Ai[k][a] * r[k];
-      gj += Aj[k][a] * r[k];
-    }
-    ci[28 + a] = w * gi;
-    cj[28 + a] = w * gj;
-  }
+  linearize_edge(g, st->cur, e, mixed);
 }
 
 // K2: 8 lanes per vertex gather the incident edge-side contributions in edge
@@ -80,42 +32,7 @@ __global__ void __launch_bounds__(256) k_assemble(DevGraph g, int mixed, int mod
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   const int v = tid >> 3, lane = tid & 7;
   double mdiag = 0.0, mgrad = 0.0, b2 = 0.0;
-  if (v < g.N) {
-    double acc[5] = {0, 0, 0, 0, 0};
-    const int k0 = g.inc_ptr[v], k1 = g.inc_ptr[v + 1];
-    for (int k = k0; k < k1; ++k) {
-      const int code = g.inc_code[k];
-      const double* src = g.contrib + (size_t)(code >> 1) * 2 * CONTRIB + (code & 1) * CONTRIB;
-#pragma unroll
-      for (int m = 0; m < 5; ++m) {
-        const int u = lane + 8 * m;
-        if (u < CONTRIB) acc[m] += src[u];
-      }
-    }
-    const bool free_v = (v != g.fixed);
-#pragma unroll
-    for (int m = 0; m < 5; ++m) {
-      const int u = lane + 8 * m;
-      if (u < 28) {
-        const int a = c_up_a[u], c = c_up_c[u];
-        g.diag64[(size_t)v * BLK64 + a * 7 + c] = acc[m];
-        g.diag64[(size_t)v * BLK64 + c * 7 + a] = acc[m];
-        if (mixed) {
-          g.diag32[(size_t)v * BLK32 + a * 7 + c] = (float)acc[m];
-          g.diag32[(size_t)v * BLK32 + c * 7 + a] = (float)acc[m];
-        }
-        if (a == c && free_v) mdiag = fmax(mdiag, acc[m]);
-      } else if (u < 35) {
-        g.b[(size_t)v * VEC + (u - 28)] = acc[m];
-        if (free_v) {
-          mgrad = fmax(mgrad, fabs(acc[m]));
-          b2 += acc[m] * acc[m];
-        }
-      } else if (u == 35) {
-        g.b[(size_t)v * VEC + 7] = 0.0;
-      }
-    }
-  }
+  if (v < g.N) assemble_vertex(g, v, lane, mixed, g.fixed, mdiag, mgrad, b2);
   double mx[2] = {mdiag, mgrad};
   double sm[1] = {b2};
   block_max<2>(mx, sh);
@@ -150,31 +67,6 @@ __global__ void __launch_bounds__(256) k_assemble(DevGraph g, int mixed, int mod
       }
     }
   }
-}
-
-// Cost of one edge at the poses in buffer `buf` (FP64).
-__device__ __forceinline__ double edge_cost(const DevGraph& g, int buf, int e) {
-  const int i = g.ei[e], j = g.ej[e];
-  Sim3T<double> Si = load_pose(g, buf, i), Sj = load_pose(g, buf, j), Z = load_meas(g, e);
-  Sim3T<double> T = compose(Z, compose(Si, inverse(Sj)));
-  qnormalize(T.q);
-  double r[7];
-  sim3_log(T, r);
-  double c = 0.0;
-  if (g.L) {
-    const double* L = g.L + (size_t)e * 28;
-#pragma unroll
-    for (int cc = 0; cc < 7; ++cc) {
-      double s = 0.0;
-#pragma unroll
-      for (int a = cc; a < 7; ++a) s += L[a * (a + 1) / 2 + cc] * r[a];
-      c += s * s;
-    }
-  } else {
-#pragma unroll
-    for (int k = 0; k < 7; ++k) c += r[k] * r[k];
-  }
-  return g.w[e] * c;
 }
 
 // mode 0: F at the current poses (start of a solve).
@@ -258,24 +150,7 @@ __global__ void __launch_bounds__(256) k_update(DevGraph g, int mixed) {
   const int cur = st->cur;
   const double lam = st->lambda;
   double pr[1] = {0.0};
-  if (v < g.N) {
-    Sim3T<double> S = load_pose(g, cur, v);
-    if (v == g.fixed) {
-      store_pose(g, cur ^ 1, v, S);
-    } else {
-      const double* dx = (mixed ? g.dx64 : g.x64) + (size_t)v * VEC;
-      double d[7];
-#pragma unroll
-      for (int k = 0; k < 7; ++k) d[k] = dx[k];
-      Sim3T<double> E = sim3_exp(d);
-      Sim3T<double> P = compose(E, S);
-      qnormalize(P.q);
-      store_pose(g, cur ^ 1, v, P);
-      const double* bv = g.b + (size_t)v * VEC;
-#pragma unroll
-      for (int k = 0; k < 7; ++k) pr[0] += d[k] * (lam * d[k] - bv[k]);
-    }
-  }
+  if (v < g.N) pr[0] = update_vertex(g, cur, v, g.fixed, (mixed ? g.dx64 : g.x64) + (size_t)v * VEC, lam);
   block_sum<1>(pr, sh);
   if (!publish_partials<1>(pr, g.partial, &st->ticket[T_UPDATE])) return;
   double tot[1];

@@ -19,7 +19,7 @@
 // The grid barrier is a monotone arrival counter (release add, acquire poll)
 // with a bounded spin: on timeout the kernel records PGO_ERR_CUDA in the
 // state and every block returns.
-#include "common.cuh"
+#include "phases.cuh"
 
 namespace pgo {
 
@@ -52,77 +52,13 @@ struct Bufs<float> {
 };
 
 // ---- K3: block-Jacobi preconditioner M_v = (H_vv + lambda I)^-1 ----------
-// 7x7 Cholesky in FP64, explicit inverse stored as V; M = 0 on the fixed
-// vertex (its unknowns stay zero).
 template <class V>
 __global__ void __launch_bounds__(32) k_precond(DevGraph g) {
   const SolverState* st = g.st;
   if (st->done) return;
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= g.N) return;
-  V* M = Bufs<V>::minv(g) + (size_t)v * Bufs<V>::BLK;
-  if (v == g.fixed) {
-#pragma unroll
-    for (int k = 0; k < 49; ++k) M[k] = V(0);
-    return;
-  }
-  const double lam = st->lambda;
-  double A[7][7];
-  const double* D = g.diag64 + (size_t)v * BLK64;
-#pragma unroll
-  for (int a = 0; a < 7; ++a)
-#pragma unroll
-    for (int c = 0; c < 7; ++c) A[a][c] = D[a * 7 + c] + (a == c ? lam : 0.0);
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < 7; ++j) {
-    double d = A[j][j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
-    ok = ok && (d > 0.0);
-    d = sqrt(fmax(d, 1e-300));
-    A[j][j] = d;
-    const double inv = 1.0 / d;
-#pragma unroll
-    for (int i = j + 1; i < 7; ++i) {
-      double s = A[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
-      A[i][j] = s * inv;
-    }
-  }
-  if (!ok) {
-    // not positive definite: fall back to the inverse of the damped diagonal
-#pragma unroll
-    for (int a = 0; a < 7; ++a)
-#pragma unroll
-      for (int c = 0; c < 7; ++c) M[a * 7 + c] = (a == c) ? V(1.0 / fmax(D[a * 8] + lam, 1e-300)) : V(0);
-    return;
-  }
-  double Li[7][7];
-#pragma unroll
-  for (int c = 0; c < 7; ++c) {
-#pragma unroll
-    for (int a = 0; a < 7; ++a) {
-      if (a < c) {
-        Li[a][c] = 0.0;
-        continue;
-      }
-      double s = (a == c) ? 1.0 : 0.0;
-#pragma unroll
-      for (int k = c; k < a; ++k) s -= A[a][k] * Li[k][c];
-      Li[a][c] = s / A[a][a];
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < 7; ++a)
-#pragma unroll
-    for (int c = 0; c < 7; ++c) {
-      double s = 0.0;
-#pragma unroll
-      for (int k = 0; k < 7; ++k) s += Li[k][a] * Li[k][c];
-      M[a * 7 + c] = V(s);
-    }
+  precond_vertex<V>(g, v, g.fixed, st->lambda, Bufs<V>::minv(g) + (size_t)v * Bufs<V>::BLK);
 }
 
 // 7x7 block (first 49 entries of a 16-byte aligned padded block), read-only.
@@ -521,18 +457,23 @@ __global__ void __launch_bounds__(512) k_pcg(DevGraph g, PcgArgs a) {
         for (int a2 = 0; a2 < 7; ++a2)
 #pragma unroll
           for (int o2 = G / 2; o2 > 0; o2 >>= 1) y[a2] += __shfl_xor_sync(gmG, y[a2], o2);
-        if (has && sl < 7) {
-          V yc = y[0];
-#pragma unroll
-          for (int a2 = 1; a2 < 7; ++a2) yc = (sl == a2) ? y[a2] : yc;
-          const V pv = __ldcg(z + base + sl) + vb * __ldcg(pprev + base + sl);
+        if (has) {
+          // every lane holds the row's 7 outputs after the reduction; lane sl
+          // stores components sl, sl + G, ... and the zero pad (index 7)
           const bool live = v != g.fixed;
-          q[base + sl] = live ? yc : V(0);
-          pcur[base + sl] = pv;
-          if (live) pq += S(pv) * S(yc);
-        } else if (has && sl == 7) {
-          q[base + 7] = V(0);
-          pcur[base + 7] = V(0);
+#pragma unroll
+          for (int a2 = 0; a2 < 8; ++a2) {
+            if (a2 % G != sl) continue;
+            if (a2 == 7) {
+              q[base + 7] = V(0);
+              pcur[base + 7] = V(0);
+              continue;
+            }
+            const V pv = __ldcg(z + base + a2) + vb * __ldcg(pprev + base + a2);
+            q[base + a2] = live ? y[a2] : V(0);
+            pcur[base + a2] = pv;
+            if (live) pq += S(pv) * S(y[a2]);
+          }
         }
       }
       {

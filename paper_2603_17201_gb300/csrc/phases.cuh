@@ -1,0 +1,218 @@
+// Per-edge and per-vertex steps of one LM iteration, shared by the
+// single-graph kernels (one graph over the whole GPU) and the batched
+// persistent kernel (one graph per thread block).
+#pragma once
+#include "edge.cuh"
+
+namespace pgo {
+
+// packed upper-triangular index (a <= c) of a symmetric 7x7 block
+__device__ __forceinline__ int upk(int a, int c) { return a * 7 - (a * (a - 1)) / 2 + (c - a); }
+
+static __device__ __constant__ unsigned char c_up_a[28] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 6};
+static __device__ __constant__ unsigned char c_up_c[28] = {0, 1, 2, 3, 4, 5, 6, 1, 2, 3, 4, 5, 6, 2, 3, 4, 5, 6, 3, 4, 5, 6, 4, 5, 6, 5, 6, 6};
+
+// K1 for one edge: residual and exact Jacobians (poses in buffer `cur`), the
+// off-diagonal (i, j) block w A_i^T A_j (FP64, and FP32 in mixed mode) and
+// the two edge-side contributions [upper(w A^T A), w A^T r].
+__device__ __forceinline__ void linearize_edge(const DevGraph& g, int cur, int e, int mixed) {
+  double r[7], Ai[7][7], Aj[7][7];
+  edge_jacobians(g, cur, e, r, Ai, Aj);
+  const double w = g.w[e];
+  double* off = g.off64 + (size_t)e * BLK64;
+  float* off32 = mixed ? g.off32 + (size_t)e * BLK32 : nullptr;
+#pragma unroll
+  for (int a = 0; a < 7; ++a) {
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) s += Ai[k][a] * Aj[k][c];
+      s *= w;
+      off[a * 7 + c] = s;
+      if (mixed) off32[a * 7 + c] = (float)s;
+    }
+  }
+  double* ci = g.contrib + (size_t)e * 2 * CONTRIB;
+  double* cj = ci + CONTRIB;
+#pragma unroll
+  for (int a = 0; a < 7; ++a) {
+#pragma unroll
+    for (int c = a; c < 7; ++c) {
+      double si = 0.0, sj = 0.0;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        si += Ai[k][a] * Ai[k][c];
+        sj += Aj[k][a] * Aj[k][c];
+      }
+      ci[upk(a, c)] = w * si;
+      cj[upk(a, c)] = w * sj;
+    }
+    double gi = 0.0, gj = 0.0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      gi += Ai[k][a] * r[k];
+      gj += Aj[k][a] * r[k];
+    }
+    ci[28 + a] = w * gi;
+    cj[28 + a] = w * gj;
+  }
+}
+
+// K2 for one vertex, lane `lane` of 8: gather the incident contributions in
+// incidence order (deterministic), write H_vv (full symmetric) and b_v, and
+// fold max diag, |b|_inf and |b|^2 (free vertices only) into the arguments.
+__device__ __forceinline__ void assemble_vertex(const DevGraph& g, int v, int lane, int mixed, int fixed,
+                                                double& mdiag, double& mgrad, double& b2) {
+  double acc[5] = {0, 0, 0, 0, 0};
+  const int k0 = g.inc_ptr[v], k1 = g.inc_ptr[v + 1];
+  for (int k = k0; k < k1; ++k) {
+    const int code = g.inc_code[k];
+    const double* src = g.contrib + (size_t)(code >> 1) * 2 * CONTRIB + (code & 1) * CONTRIB;
+#pragma unroll
+    for (int m = 0; m < 5; ++m) {
+      const int u = lane + 8 * m;
+      if (u < CONTRIB) acc[m] += src[u];
+    }
+  }
+  const bool free_v = (v != fixed);
+#pragma unroll
+  for (int m = 0; m < 5; ++m) {
+    const int u = lane + 8 * m;
+    if (u < 28) {
+      const int a = c_up_a[u], c = c_up_c[u];
+      g.diag64[(size_t)v * BLK64 + a * 7 + c] = acc[m];
+      g.diag64[(size_t)v * BLK64 + c * 7 + a] = acc[m];
+      if (mixed) {
+        g.diag32[(size_t)v * BLK32 + a * 7 + c] = (float)acc[m];
+        g.diag32[(size_t)v * BLK32 + c * 7 + a] = (float)acc[m];
+      }
+      if (a == c && free_v) mdiag = fmax(mdiag, acc[m]);
+    } else if (u < 35) {
+      g.b[(size_t)v * VEC + (u - 28)] = acc[m];
+      if (free_v) {
+        mgrad = fmax(mgrad, fabs(acc[m]));
+        b2 += acc[m] * acc[m];
+      }
+    } else if (u == 35) {
+      g.b[(size_t)v * VEC + 7] = 0.0;
+    }
+  }
+}
+
+// Cost of one edge at the poses in buffer `buf` (FP64).
+__device__ __forceinline__ double edge_cost(const DevGraph& g, int buf, int e) {
+  const int i = g.ei[e], j = g.ej[e];
+  Sim3T<double> Si = load_pose(g, buf, i), Sj = load_pose(g, buf, j), Z = load_meas(g, e);
+  Sim3T<double> T = compose(Z, compose(Si, inverse(Sj)));
+  qnormalize(T.q);
+  double r[7];
+  sim3_log(T, r);
+  double c = 0.0;
+  if (g.L) {
+    const double* L = g.L + (size_t)e * 28;
+#pragma unroll
+    for (int cc = 0; cc < 7; ++cc) {
+      double s = 0.0;
+#pragma unroll
+      for (int a = cc; a < 7; ++a) s += L[a * (a + 1) / 2 + cc] * r[a];
+      c += s * s;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < 7; ++k) c += r[k] * r[k];
+  }
+  return g.w[e] * c;
+}
+
+// Candidate pose of one vertex: exp(delta_v) S_v into buffer cur^1 (the fixed
+// vertex is copied); returns this vertex's term of delta^T (lambda delta - b).
+__device__ __forceinline__ double update_vertex(const DevGraph& g, int cur, int v, int fixed, const double* dxv,
+                                                double lam) {
+  Sim3T<double> S = load_pose(g, cur, v);
+  if (v == fixed) {
+    store_pose(g, cur ^ 1, v, S);
+    return 0.0;
+  }
+  double d[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) d[k] = dxv[k];
+  Sim3T<double> E = sim3_exp(d);
+  Sim3T<double> P = compose(E, S);
+  qnormalize(P.q);
+  store_pose(g, cur ^ 1, v, P);
+  const double* bv = g.b + (size_t)v * VEC;
+  double pr = 0.0;
+#pragma unroll
+  for (int k = 0; k < 7; ++k) pr += d[k] * (lam * d[k] - bv[k]);
+  return pr;
+}
+
+// K3 for one vertex: M = (H_vv + lambda I)^-1 by a 7x7 Cholesky in FP64,
+// stored as V (the inverse of the damped diagonal if the block is not
+// positive definite); M = 0 on the fixed vertex (its unknowns stay zero).
+template <class V>
+__device__ __forceinline__ void precond_vertex(const DevGraph& g, int v, int fixed, double lam, V* M) {
+  if (v == fixed) {
+#pragma unroll
+    for (int k = 0; k < 49; ++k) M[k] = V(0);
+    return;
+  }
+  double A[7][7];
+  const double* D = g.diag64 + (size_t)v * BLK64;
+#pragma unroll
+  for (int a = 0; a < 7; ++a)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) A[a][c] = D[a * 7 + c] + (a == c ? lam : 0.0);
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    double d = A[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+    ok = ok && (d > 0.0);
+    d = sqrt(fmax(d, 1e-300));
+    A[j][j] = d;
+    const double inv = 1.0 / d;
+#pragma unroll
+    for (int i = j + 1; i < 7; ++i) {
+      double s = A[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
+      A[i][j] = s * inv;
+    }
+  }
+  if (!ok) {
+#pragma unroll
+    for (int a = 0; a < 7; ++a)
+#pragma unroll
+      for (int c = 0; c < 7; ++c) M[a * 7 + c] = (a == c) ? V(1.0 / fmax(D[a * 8] + lam, 1e-300)) : V(0);
+    return;
+  }
+  double Li[7][7];
+#pragma unroll
+  for (int c = 0; c < 7; ++c) {
+#pragma unroll
+    for (int a = 0; a < 7; ++a) {
+      if (a < c) {
+        Li[a][c] = 0.0;
+        continue;
+      }
+      double s = (a == c) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = c; k < a; ++k) s -= A[a][k] * Li[k][c];
+      Li[a][c] = s / A[a][a];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 7; ++a)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) s += Li[k][a] * Li[k][c];
+      M[a * 7 + c] = V(s);
+    }
+}
+
+}  // namespace pgo
