@@ -86,6 +86,17 @@ typedef struct {
   void* stream;
 } pgo_graph_desc;
 
+/* Preconditioner of the PCG linear solve (Sec. IV-F's damped normal
+ * equations).  BLOCK_JACOBI: the inverse 7x7 diagonal blocks of H + lambda I.
+ * MULTIGRID: one V(1,1) cycle of smoothed-aggregation multigrid whose coarse
+ * unknowns are the rigid Sim(3) motions of runs of 4 consecutive vertices
+ * (recursively), block-Jacobi smoothing, dense coarsest solve; its sparsity
+ * is analysed once per graph on the host at the first solve that uses it.
+ * Both are symmetric positive definite, so either gives the same solution
+ * to the PCG tolerance; they differ in iteration count.  The batched solve
+ * always uses block-Jacobi. */
+typedef enum { PGO_PRECOND_BLOCK_JACOBI = 0, PGO_PRECOND_MULTIGRID = 1 } pgo_preconditioner;
+
 /* Solve options.  pgo_default_options() fills the documented defaults. */
 typedef struct {
   int32_t max_iters;      /* LM iterations, rejected ones included (20) */
@@ -103,6 +114,7 @@ typedef struct {
                              while it lowers |b|_inf (0; use >0 before
                              pgo_backward) */
   int32_t schedule;       /* kernel schedule id; -1 = library default */
+  int32_t preconditioner; /* pgo_preconditioner (PGO_PRECOND_MULTIGRID) */
 } pgo_solve_options;
 
 /* Solve report. */

@@ -53,7 +53,8 @@ class SolveOptions(ctypes.Structure):
     _fields_ = [("max_iters", c_int32), ("precision", c_int32), ("tau", c_double),
                 ("lambda_init", c_double), ("ftol", c_double), ("gtol", c_double),
                 ("pcg_tol", c_double), ("pcg_max_iters", c_int32), ("refine_steps", c_int32),
-                ("refine_tol", c_double), ("polish_iters", c_int32), ("schedule", c_int32)]
+                ("refine_tol", c_double), ("polish_iters", c_int32), ("schedule", c_int32),
+                ("preconditioner", c_int32)]
 
 
 class Report(ctypes.Structure):
@@ -136,6 +137,8 @@ def default_options(**overrides) -> SolveOptions:
     for k, v in overrides.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": PGO_FP64, "mixed": PGO_MIXED}[v.lower()]
+        if k == "preconditioner" and isinstance(v, str):
+            v = {"block_jacobi": 0, "jacobi": 0, "multigrid": 1, "amg": 1}[v.lower()]
         if not hasattr(o, k):
             raise TypeError(f"unknown solve option {k!r}")
         setattr(o, k, v)

@@ -1,0 +1,1019 @@
+// Smoothed-aggregation multigrid preconditioner for the damped normal
+// equations (H + lambda I) delta = rhs of the essential graph (Sec. IV-F's
+// linear solve).  Block-Jacobi PCG needs O(N) iterations on the long chains
+// of keyframes that loop closing optimises; this hierarchy brings that to a
+// few tens, independent of the graph size.
+//
+// Hierarchy.  Level 0 is the vertex graph.  Aggregates are runs of AMG_M
+// consecutive free vertices (keyframe order follows the trajectory, so a
+// run is a contiguous piece of it); each aggregate becomes one node of the
+// next level with 7 unknowns: the rigid Sim(3) motion of the whole piece.
+// Right-multiplying every pose of an aggregate by one G = exp(eps) leaves all
+// residuals between them unchanged, and in left-tangent coordinates that
+// motion is delta_v = Adj(S_v S_ref^-1) eps' with eps' = Adj(S_ref) eps for a
+// reference vertex of the aggregate.  So the tentative prolongation block of
+// vertex v is T_v = Adj(S_v S_ref^-1) (the near-null space of the operator);
+// coarser levels use the same rule with the reference vertices of the nodes.
+// The prolongation is smoothed once, P = (I - 4/(3 rho) D^-1 A) T with rho an
+// estimate of the spectral radius of D^-1 A (power iteration), and the coarse
+// operator is the Galerkin product P^T A P.  The coarsest level (at most
+// AMG_CMAX nodes) is inverted densely.  The preconditioner is one symmetric
+// V(1,1) cycle with damped block-Jacobi smoothing, weight 1/rho.
+//
+// The sparsity of every level and the index lists of every product are built
+// once on the host (amg_build); the numeric setup (k_amg_setup) runs on the
+// device at every linearisation, because H, lambda and the poses change.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "amg.cuh"
+#include "gridsync.cuh"
+#include "phases.cuh"
+
+namespace pgo {
+
+// ---------------------------------------------------------------------------
+// Host: symbolic hierarchy
+// ---------------------------------------------------------------------------
+
+struct AmgHost {
+  AmgDev h{};                // descriptor with device pointers (host copy)
+  AmgDev* d = nullptr;       // the same descriptor in device memory
+  char* mem = nullptr;
+  size_t bytes = 0;
+};
+
+namespace {
+
+struct HostLevel {
+  int n = 0, n_next = 0;
+  std::vector<int> ref, refc, agg;
+  std::vector<int> a_ptr, a_col, a_src;     // levels >= 1
+  std::vector<int> p_ptr, p_col, p_row, pt_ptr, pt_row, pt_blk;
+  std::vector<int> ap_ptr, ap_col;
+  std::vector<int> r1_ptr, r2_ptr, r3_ptr;
+  std::vector<int2> r1, r2, r3;
+};
+
+// Neighbour terms (A reference, node) of row u, the diagonal first.
+// Level 0: A reference -(u+1) is the damped diagonal block of u, a reference
+// k >= 0 is incidence code k (stored block k >> 1, transposed if k & 1).
+// Levels >= 1: the index of the stored block.
+struct NbrView {
+  int level, fixed;
+  const int *inc_ptr, *inc_code, *inc_other;   // level 0
+  const std::vector<int>* a_ptr;               // levels >= 1
+  const std::vector<int>* a_col;
+  template <class F>
+  void each(int u, F f) const {
+    if (level == 0) {
+      if (u == fixed) return;
+      f(-(u + 1), u);
+      for (int k = inc_ptr[u]; k < inc_ptr[u + 1]; ++k) {
+        const int w = inc_other[k];
+        if (w != fixed) f(inc_code[k], w);
+      }
+    } else {
+      for (int k = (*a_ptr)[u]; k < (*a_ptr)[u + 1]; ++k) f(k, (*a_col)[k]);
+    }
+  }
+};
+
+inline int find_col(const std::vector<int>& ptr, const std::vector<int>& col, int row, int c) {
+  const auto b = col.begin() + ptr[row], e = col.begin() + ptr[row + 1];
+  const auto it = std::lower_bound(b, e, c);
+  return (it != e && *it == c) ? (int)(it - col.begin()) : -1;
+}
+
+// Builds P, AP, the recipes and the pattern of the next level for `L`.
+void build_level(HostLevel& L, const NbrView& nb, HostLevel& next) {
+  const int n = L.n, nn = L.n_next;
+  std::vector<int> mark(std::max(nn, 1), -1), buf;
+  // ---- P pattern: the aggregates of the node and of its neighbours ----
+  L.p_ptr.assign(n + 1, 0);
+  for (int u = 0; u < n; ++u) {
+    buf.clear();
+    if (L.agg[u] >= 0) {
+      buf.push_back(L.agg[u]);
+      nb.each(u, [&](int, int w) { if (L.agg[w] >= 0) buf.push_back(L.agg[w]); });
+      std::sort(buf.begin(), buf.end());
+      buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+    }
+    L.p_ptr[u + 1] = L.p_ptr[u] + (int)buf.size();
+    L.p_col.insert(L.p_col.end(), buf.begin(), buf.end());
+  }
+  const int nnz_p = L.p_ptr[n];
+  L.p_row.resize(nnz_p);
+  for (int u = 0; u < n; ++u)
+    for (int k = L.p_ptr[u]; k < L.p_ptr[u + 1]; ++k) L.p_row[k] = u;
+  // CSC of P (rows ascending within each column)
+  L.pt_ptr.assign(nn + 1, 0);
+  for (int k = 0; k < nnz_p; ++k) L.pt_ptr[L.p_col[k] + 1]++;
+  for (int c = 0; c < nn; ++c) L.pt_ptr[c + 1] += L.pt_ptr[c];
+  L.pt_row.resize(nnz_p);
+  L.pt_blk.resize(nnz_p);
+  {
+    std::vector<int> fill(L.pt_ptr.begin(), L.pt_ptr.end() - 1);
+    for (int u = 0; u < n; ++u)
+      for (int k = L.p_ptr[u]; k < L.p_ptr[u + 1]; ++k) {
+        const int a = fill[L.p_col[k]]++;
+        L.pt_row[a] = u;
+        L.pt_blk[a] = k;
+      }
+  }
+  // ---- R1: per P block (u, c), the terms A_uw T_w with agg(w) = c ----
+  L.r1_ptr.assign(nnz_p + 1, 0);
+  for (int u = 0; u < n; ++u) {
+    const int k0 = L.p_ptr[u];
+    nb.each(u, [&](int, int w) {
+      if (L.agg[w] >= 0) L.r1_ptr[find_col(L.p_ptr, L.p_col, u, L.agg[w]) + 1]++;
+    });
+    (void)k0;
+  }
+  for (int k = 0; k < nnz_p; ++k) L.r1_ptr[k + 1] += L.r1_ptr[k];
+  L.r1.resize(L.r1_ptr[nnz_p]);
+  {
+    std::vector<int> fill(L.r1_ptr.begin(), L.r1_ptr.end() - 1);
+    for (int u = 0; u < n; ++u)
+      nb.each(u, [&](int a, int w) {
+        if (L.agg[w] < 0) return;
+        const int b = find_col(L.p_ptr, L.p_col, u, L.agg[w]);
+        L.r1[fill[b]++] = make_int2(a, w);
+      });
+  }
+  // ---- AP pattern and R2: AP_ud = sum_w A_uw P_wd ----
+  L.ap_ptr.assign(n + 1, 0);
+  for (int u = 0; u < n; ++u) {
+    buf.clear();
+    if (L.agg[u] >= 0)
+      nb.each(u, [&](int, int w) {
+        for (int k = L.p_ptr[w]; k < L.p_ptr[w + 1]; ++k) buf.push_back(L.p_col[k]);
+      });
+    std::sort(buf.begin(), buf.end());
+    buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+    L.ap_ptr[u + 1] = L.ap_ptr[u] + (int)buf.size();
+    L.ap_col.insert(L.ap_col.end(), buf.begin(), buf.end());
+  }
+  const int nnz_ap = L.ap_ptr[n];
+  L.r2_ptr.assign(nnz_ap + 1, 0);
+  for (int u = 0; u < n; ++u) {
+    if (L.agg[u] < 0) continue;
+    nb.each(u, [&](int, int w) {
+      for (int k = L.p_ptr[w]; k < L.p_ptr[w + 1]; ++k)
+        L.r2_ptr[find_col(L.ap_ptr, L.ap_col, u, L.p_col[k]) + 1]++;
+    });
+  }
+  for (int k = 0; k < nnz_ap; ++k) L.r2_ptr[k + 1] += L.r2_ptr[k];
+  L.r2.resize(L.r2_ptr[nnz_ap]);
+  {
+    std::vector<int> fill(L.r2_ptr.begin(), L.r2_ptr.end() - 1);
+    for (int u = 0; u < n; ++u) {
+      if (L.agg[u] < 0) continue;
+      nb.each(u, [&](int a, int w) {
+        for (int k = L.p_ptr[w]; k < L.p_ptr[w + 1]; ++k) {
+          const int b = find_col(L.ap_ptr, L.ap_col, u, L.p_col[k]);
+          L.r2[fill[b]++] = make_int2(a, k);
+        }
+      });
+    }
+  }
+  // ---- next level: pattern of P^T A P (upper half from the products) ----
+  std::vector<std::vector<int>> upper(nn);
+  for (int c = 0; c < nn; ++c) {
+    buf.clear();
+    for (int t = L.pt_ptr[c]; t < L.pt_ptr[c + 1]; ++t) {
+      const int u = L.pt_row[t];
+      for (int k = L.ap_ptr[u]; k < L.ap_ptr[u + 1]; ++k)
+        if (L.ap_col[k] >= c) buf.push_back(L.ap_col[k]);
+    }
+    buf.push_back(c);
+    std::sort(buf.begin(), buf.end());
+    buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+    upper[c] = buf;
+  }
+  std::vector<std::vector<int>> lower(nn);
+  for (int c = 0; c < nn; ++c)
+    for (int d : upper[c])
+      if (d != c) lower[d].push_back(c);
+  next.a_ptr.assign(nn + 1, 0);
+  for (int c = 0; c < nn; ++c) next.a_ptr[c + 1] = next.a_ptr[c] + (int)(upper[c].size() + lower[c].size());
+  const int nnz_next = next.a_ptr[nn];
+  next.a_col.resize(nnz_next);
+  next.a_src.assign(nnz_next, -1);
+  // row c: the diagonal, then the other columns ascending
+  for (int c = 0; c < nn; ++c) {
+    int k = next.a_ptr[c];
+    next.a_col[k++] = c;
+    std::vector<int> rest;
+    for (int d : lower[c]) rest.push_back(d);
+    for (int d : upper[c])
+      if (d != c) rest.push_back(d);
+    std::sort(rest.begin(), rest.end());
+    for (int d : rest) next.a_col[k++] = d;
+  }
+  auto blk_of = [&](int c, int d) {
+    if (c == d) return next.a_ptr[c];
+    for (int k = next.a_ptr[c] + 1; k < next.a_ptr[c + 1]; ++k)
+      if (next.a_col[k] == d) return k;
+    return -1;
+  };
+  for (int c = 0; c < nn; ++c)
+    for (int k = next.a_ptr[c] + 1; k < next.a_ptr[c + 1]; ++k)
+      if (next.a_col[k] < c) next.a_src[k] = blk_of(next.a_col[k], c);
+  // R3 per upper block (c, d >= c): (P block (u, c), AP block (u, d))
+  L.r3_ptr.assign(nnz_next + 1, 0);
+  std::vector<int> pos(std::max(nn, 1), -1);
+  for (int pass = 0; pass < 2; ++pass) {
+    std::vector<int> fill;
+    if (pass == 1) {
+      for (int k = 0; k < nnz_next; ++k) L.r3_ptr[k + 1] += L.r3_ptr[k];
+      L.r3.resize(L.r3_ptr[nnz_next]);
+      fill.assign(L.r3_ptr.begin(), L.r3_ptr.end() - 1);
+    }
+    for (int c = 0; c < nn; ++c) {
+      for (int k = next.a_ptr[c]; k < next.a_ptr[c + 1]; ++k) pos[next.a_col[k]] = k;
+      for (int t = L.pt_ptr[c]; t < L.pt_ptr[c + 1]; ++t) {
+        const int u = L.pt_row[t], pb = L.pt_blk[t];
+        for (int k = L.ap_ptr[u]; k < L.ap_ptr[u + 1]; ++k) {
+          const int d = L.ap_col[k];
+          if (d < c) continue;
+          const int b = pos[d];
+          if (pass == 0) L.r3_ptr[b + 1]++;
+          else L.r3[fill[b]++] = make_int2(pb, k);
+        }
+      }
+      for (int k = next.a_ptr[c]; k < next.a_ptr[c + 1]; ++k) pos[next.a_col[k]] = -1;
+    }
+  }
+  (void)mark;
+}
+
+struct Uploader {
+  char* base = nullptr;
+  size_t used = 0;
+  std::vector<std::pair<void*, std::pair<const void*, size_t>>> copies;
+  template <class T>
+  T* take(size_t count) {
+    const size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
+    T* p = reinterpret_cast<T*>(base ? base + used : nullptr);
+    used += bytes;
+    return p;
+  }
+  template <class T>
+  const T* put(const std::vector<T>& v) {
+    T* p = take<T>(v.size() > 0 ? v.size() : 1);
+    if (base && !v.empty()) copies.push_back({p, {v.data(), v.size() * sizeof(T)}});
+    return p;
+  }
+};
+
+// Lays out (base == nullptr: only measures) every device array of the
+// hierarchy and records the host-to-device copies.
+void layout(Uploader& U, std::vector<HostLevel>& H, int L, int N, AmgDev& D) {
+  D.L = L;
+  D.nL = H[L].n;
+  for (int l = 0; l <= L; ++l) {
+    HostLevel& h = H[l];
+    AmgLevel& a = D.lv[l];
+    std::memset(&a, 0, sizeof(a));
+    a.n = h.n;
+    a.n_next = h.n_next;
+    const size_t n = (size_t)std::max(h.n, 1);
+    if (l >= 1) {
+      a.nnz_a = h.a_ptr.empty() ? 0 : h.a_ptr[h.n];
+      a.a_ptr = U.put(h.a_ptr);
+      a.a_col = U.put(h.a_col);
+      a.a_src = U.put(h.a_src);
+      a.a64 = U.take<double>((size_t)std::max(a.nnz_a, 1) * BLK64);
+      a.a32 = U.take<float>((size_t)std::max(a.nnz_a, 1) * BLK32);
+      a.dinv64 = U.take<double>(n * BLK64);
+      a.dinv32 = U.take<float>(n * BLK32);
+      a.vr64 = U.take<double>(n * VEC);
+      a.vy64 = U.take<double>(n * VEC);
+      a.vr32 = U.take<float>(n * VEC);
+      a.vy32 = U.take<float>(n * VEC);
+    }
+    a.vx64 = U.take<double>(n * VEC);
+    a.vx32 = U.take<float>(n * VEC);
+    if (l < L) {
+      a.pv64 = U.take<double>(n * VEC);
+      a.pv32 = U.take<float>(n * VEC);
+    }
+    if (l >= 1 && l < L) {
+      a.vs64 = U.take<double>(n * VEC);
+      a.vs32 = U.take<float>(n * VEC);
+    }
+    if (l < L) {
+      a.nnz_p = h.p_ptr[h.n];
+      a.nnz_ap = h.ap_ptr[h.n];
+      a.nnz_next = H[l + 1].a_ptr[h.n_next];
+      a.ref = U.put(h.ref);
+      a.refc = U.put(h.refc);
+      a.agg = U.put(h.agg);
+      a.t64 = U.take<double>(n * BLK64);
+      a.t32 = U.take<float>(n * BLK32);
+      a.p_ptr = U.put(h.p_ptr);
+      a.p_col = U.put(h.p_col);
+      a.p_row = U.put(h.p_row);
+      a.p64 = U.take<double>((size_t)std::max(a.nnz_p, 1) * BLK64);
+      a.p32 = U.take<float>((size_t)std::max(a.nnz_p, 1) * BLK32);
+      a.pt_ptr = U.put(h.pt_ptr);
+      a.pt_row = U.put(h.pt_row);
+      a.pt_blk = U.put(h.pt_blk);
+      a.ap_ptr = U.put(h.ap_ptr);
+      a.ap_col = U.put(h.ap_col);
+      a.ap64 = U.take<double>((size_t)std::max(a.nnz_ap, 1) * BLK64);
+      a.ap32 = U.take<float>((size_t)std::max(a.nnz_ap, 1) * BLK32);
+      a.r1_ptr = U.put(h.r1_ptr);
+      a.r1 = U.put(h.r1);
+      a.r2_ptr = U.put(h.r2_ptr);
+      a.r2 = U.put(h.r2);
+      a.r3_ptr = U.put(h.r3_ptr);
+      a.r3 = U.put(h.r3);
+    }
+  }
+  const size_t nl2 = (size_t)D.nL * D.nL;
+  D.cinv64 = U.take<double>(std::max(nl2, (size_t)1) * BLK64);
+  D.cinv32 = U.take<float>(std::max(nl2, (size_t)1) * BLK32);
+  D.rho = U.take<double>(AMG_MAXL + 1);
+  for (int k = 0; k < 2; ++k) {
+    D.pw64[k] = U.take<double>((size_t)N * VEC);
+    D.pw32[k] = U.take<float>((size_t)N * VEC);
+  }
+  D.flag = U.take<int>(1);
+  D.warm = U.take<int>(2);
+}
+
+}  // namespace
+
+AmgHost* amg_build(int N, int fixed, const int* inc_ptr, const int* inc_code, const int* inc_other,
+                   cudaStream_t s, const char** err) {
+  *err = nullptr;
+  const int K = N - 1;   // free vertices
+  if (K < 1) {
+    *err = "multigrid needs at least one free vertex";
+    return nullptr;
+  }
+  std::vector<HostLevel> H(1);
+  HostLevel& L0 = H[0];
+  L0.n = N;
+  L0.agg.assign(N, -1);
+  L0.ref.resize(N);
+  {
+    int fo = 0;
+    for (int v = 0; v < N; ++v) {
+      L0.ref[v] = v;
+      if (v == fixed) continue;
+      L0.agg[v] = fo / AMG_M;
+      ++fo;
+    }
+  }
+  L0.n_next = (K + AMG_M - 1) / AMG_M;
+  int L = 0;
+  for (;;) {
+    HostLevel& cur = H[L];
+    if (L + 1 > AMG_MAXL) {
+      *err = "graph too large for the multigrid hierarchy";
+      return nullptr;
+    }
+    H.emplace_back();
+    HostLevel& cur2 = H[L];      // (emplace_back may move the vector)
+    HostLevel& nxt = H[L + 1];
+    (void)cur;
+    NbrView nb{L, fixed, inc_ptr, inc_code, inc_other, &cur2.a_ptr, &cur2.a_col};
+    build_level(cur2, nb, nxt);
+    nxt.n = cur2.n_next;
+    // references: the first member of each aggregate
+    nxt.ref.assign(nxt.n, -1);
+    for (int u = 0; u < cur2.n; ++u) {
+      const int c = cur2.agg[u];
+      if (c >= 0 && nxt.ref[c] < 0) nxt.ref[c] = cur2.ref[u];
+    }
+    cur2.refc.assign(cur2.n, 0);
+    for (int u = 0; u < cur2.n; ++u) cur2.refc[u] = cur2.agg[u] >= 0 ? nxt.ref[cur2.agg[u]] : 0;
+    ++L;
+    if (nxt.n <= AMG_CMAX) break;
+    nxt.agg.resize(nxt.n);
+    for (int c = 0; c < nxt.n; ++c) nxt.agg[c] = c / AMG_M;
+    nxt.n_next = (nxt.n + AMG_M - 1) / AMG_M;
+  }
+  AmgHost* A = new AmgHost();
+  Uploader meas;
+  layout(meas, H, L, N, A->h);
+  A->bytes = meas.used + 256;
+  if (cudaMalloc(&A->mem, A->bytes) != cudaSuccess ||
+      cudaMalloc(&A->d, sizeof(AmgDev)) != cudaSuccess) {
+    cudaGetLastError();
+    *err = "device allocation for the multigrid hierarchy failed";
+    amg_free(A);
+    return nullptr;
+  }
+  Uploader up;
+  up.base = A->mem;
+  layout(up, H, L, N, A->h);
+  bool ok = cudaMemsetAsync(A->mem, 0, up.used, s) == cudaSuccess;
+  for (auto& c : up.copies)
+    ok = ok && cudaMemcpyAsync(c.first, c.second.first, c.second.second, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok = ok && cudaMemcpyAsync(A->d, &A->h, sizeof(AmgDev), cudaMemcpyHostToDevice, s) == cudaSuccess;
+  ok = ok && cudaStreamSynchronize(s) == cudaSuccess;   // the host vectors die on return
+  if (!ok) {
+    *err = "uploading the multigrid hierarchy failed";
+    amg_free(A);
+    return nullptr;
+  }
+  return A;
+}
+
+void amg_free(AmgHost* h) {
+  if (!h) return;
+  if (h->mem) cudaFree(h->mem);
+  if (h->d) cudaFree(h->d);
+  delete h;
+}
+const AmgDev* amg_host_desc(const AmgHost* h) { return h ? &h->h : nullptr; }
+const AmgDev* amg_device_desc(const AmgHost* h) { return h ? h->d : nullptr; }
+size_t amg_bytes(const AmgHost* h) { return h ? h->bytes : 0; }
+
+// ---------------------------------------------------------------------------
+// Device: numeric setup
+// ---------------------------------------------------------------------------
+
+// A block of level l for a recipe reference: entry (i, k) is
+// (tr ? p[k * 7 + i] : p[i * 7 + k]) + (i == k ? add : 0).
+// sum over the recipe entries e of (A_e X_e)[i][j].  A_e: level-0 block
+// reference (L0: diagonal + lambda, or an off-diagonal block, maybe
+// transposed; blocks from an earlier launch) or a block of this level's
+// operator (written by this launch); X_e = X + rec[e].y * BLK (written by
+// this launch).  Entries go four at a time so that their loads overlap.
+template <class V, bool L0>
+__device__ __forceinline__ V recipe_ax(const DevGraph& g, const V* Alev, V lam, const int2* rec, int e0, int e1,
+                                       const V* X, int i, int j) {
+  constexpr int BLK = AV<V>::BLK;
+  V acc = V(0);
+  auto arow = [&](int a, V (&r)[7]) {
+    if (L0) {
+      const V* p;
+      bool tr = false;
+      V add = V(0);
+      if (a < 0) {
+        p = AV<V>::diag(g) + (size_t)(-a - 1) * BLK;
+        add = lam;
+      } else {
+        p = AV<V>::off(g) + (size_t)(a >> 1) * BLK;
+        tr = (a & 1) != 0;
+      }
+#pragma unroll
+      for (int k = 0; k < 7; ++k) r[k] = __ldg(p + (tr ? k * 7 + i : i * 7 + k)) + (k == i ? add : V(0));
+    } else {
+      const V* p = Alev + (size_t)a * BLK + i * 7;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) r[k] = __ldcg(p + k);
+    }
+  };
+  int e = e0;
+  for (; e + 4 <= e1; e += 4) {
+    int2 t[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[q] = __ldg(rec + e + q);
+    V ar[4][7], xc[4][7];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      arow(t[q].x, ar[q]);
+      const V* xp = X + (size_t)t[q].y * BLK + j;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) xc[q][k] = __ldcg(xp + k * 7);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < 7; ++k) acc += ar[q][k] * xc[q][k];
+  }
+  for (; e < e1; ++e) {
+    const int2 t = __ldg(rec + e);
+    V ar[7];
+    arow(t.x, ar);
+    const V* xp = X + (size_t)t.y * BLK + j;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) acc += ar[k] * __ldcg(xp + k * 7);
+  }
+  return acc;
+}
+
+// sum over the entries e of (P_e^T Q_e)[i][j], both written by this launch.
+template <class V>
+__device__ __forceinline__ V recipe_ptq(const int2* rec, int e0, int e1, const V* P, const V* Q, int i, int j) {
+  constexpr int BLK = AV<V>::BLK;
+  V acc = V(0);
+  int e = e0;
+  for (; e + 4 <= e1; e += 4) {
+    int2 t[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[q] = __ldg(rec + e + q);
+    V pc[4][7], qc[4][7];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const V* pp = P + (size_t)t[q].x * BLK + i;
+      const V* qp = Q + (size_t)t[q].y * BLK + j;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        pc[q][k] = __ldcg(pp + k * 7);
+        qc[q][k] = __ldcg(qp + k * 7);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < 7; ++k) acc += pc[q][k] * qc[q][k];
+  }
+  for (; e < e1; ++e) {
+    const int2 t = __ldg(rec + e);
+    const V* pp = P + (size_t)t.x * BLK + i;
+    const V* qp = Q + (size_t)t.y * BLK + j;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) acc += __ldcg(pp + k * 7) * __ldcg(qp + k * 7);
+  }
+  return acc;
+}
+
+// Adj(S) in [omega, upsilon, sigma] order: [[R, 0, 0], [t^ R, s R, -t], [0, 0, 1]].
+__device__ __forceinline__ void adj7(const Sim3T<double>& S, double (&A)[7][7]) {
+  double R[9];
+  qmat(S.q, R);
+  const double* t = S.t;
+#pragma unroll
+  for (int i = 0; i < 7; ++i)
+#pragma unroll
+    for (int j = 0; j < 7; ++j) A[i][j] = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    A[0][c] = R[c];
+    A[1][c] = R[3 + c];
+    A[2][c] = R[6 + c];
+    A[3][c] = -t[2] * R[3 + c] + t[1] * R[6 + c];
+    A[4][c] = t[2] * R[0 + c] - t[0] * R[6 + c];
+    A[5][c] = -t[1] * R[0 + c] + t[0] * R[3 + c];
+    A[3][3 + c] = S.s * R[c];
+    A[4][3 + c] = S.s * R[3 + c];
+    A[5][3 + c] = S.s * R[6 + c];
+  }
+  A[3][6] = -t[0];
+  A[4][6] = -t[1];
+  A[5][6] = -t[2];
+  A[6][6] = 1.0;
+}
+
+// Inverse of a symmetric positive definite 7x7 block (Cholesky, in double);
+// returns false (and writes the inverse of the diagonal) if a pivot is not
+// positive.
+template <class V>
+__device__ __forceinline__ bool inv7_spd(const V* B, V* out) {
+  double A[7][7];
+#pragma unroll
+  for (int a = 0; a < 7; ++a)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) A[a][c] = 0.5 * ((double)B[a * 7 + c] + (double)B[c * 7 + a]);
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    double d = A[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+    ok = ok && (d > 0.0);
+    d = sqrt(fmax(d, 1e-300));
+    A[j][j] = d;
+#pragma unroll
+    for (int i = j + 1; i < 7; ++i) {
+      double s = A[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
+      A[i][j] = s / d;
+    }
+  }
+  if (!ok) {
+#pragma unroll
+    for (int a = 0; a < 7; ++a)
+#pragma unroll
+      for (int c = 0; c < 7; ++c) {
+        const double dd = (double)B[a * 8];
+        out[a * 7 + c] = (a == c && dd > 0.0) ? V(1.0 / dd) : V(0);
+      }
+    return false;
+  }
+  // L^-1 (lower), then inv = L^-T L^-1
+  double Li[7][7];
+#pragma unroll
+  for (int c = 0; c < 7; ++c) {
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+      if (i < c) { Li[i][c] = 0.0; continue; }
+      double s = (i == c) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = 0; k < i; ++k)
+        if (k >= c) s -= A[i][k] * Li[k][c];
+      Li[i][c] = s / A[i][i];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 7; ++a)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 7; ++k)
+        if (k >= a && k >= c) s += Li[k][a] * Li[k][c];
+      out[a * 7 + c] = V(s);
+    }
+  return true;
+}
+
+// Per-block partial (one double per block) and its fixed-order grid sum,
+// double-buffered by `set` so that a fast block's next write cannot race a
+// slow block's read.
+__device__ __forceinline__ double grid_sum_after_sync(const double* partial) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  if (threadIdx.x < 32) {
+    for (int b = threadIdx.x; b < gridDim.x; b += 32) acc += __ldcg(partial + b);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (threadIdx.x == 0) red[0] = acc;
+  }
+  __syncthreads();
+  const double r = red[0];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void block_partial(double v, double* partial) {
+  __shared__ double red[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w];
+    partial[blockIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// y = D^-1 A (sc x) for the rows of level l, one warp per row: the lanes
+// take whole blocks of the row (the diagonal block first), the warp sums
+// the partial products, lanes 0..6 apply D^-1.  Returns the thread's part of
+// |y|^2.
+template <class V>
+__device__ double power_step(const DevGraph& g, const AmgLevel& Lv, int l, V lam, const V* x, V sc, V* y) {
+  constexpr int BLK = AV<V>::BLK;
+  const int n = Lv.n;
+  const int lane = threadIdx.x & 31;
+  const int warps = gridDim.x * (blockDim.x >> 5);
+  double nrm = 0.0;
+  for (int u0 = 0; u0 < n; u0 += warps) {
+    const int u = u0 + blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (u >= n) continue;   // whole warps leave together
+    const bool live = !(l == 0 && u == g.fixed);
+    V acc[7];
+#pragma unroll
+    for (int a = 0; a < 7; ++a) acc[a] = V(0);
+    if (live) {
+      if (l == 0) {
+        const int k0 = __ldg(g.inc_ptr + u), ks = __ldg(g.inc_split + u), k1 = __ldg(g.inc_ptr + u + 1);
+        for (int k = k0 - 1 + lane; k < k1; k += 32) {
+          int w = u, code = 0;
+          const V* B;
+          if (k < k0) {
+            B = AV<V>::diag(g) + (size_t)u * BLK;
+          } else {
+            code = __ldg(g.inc_code + k);
+            w = __ldg(g.inc_other + k);
+            B = AV<V>::off(g) + (size_t)(code >> 1) * BLK;
+          }
+          V xv[7];
+#pragma unroll
+          for (int c = 0; c < 7; ++c) xv[c] = sc * __ldcg(x + (size_t)w * VEC + c);
+          const bool tr = k >= ks;
+#pragma unroll
+          for (int a = 0; a < 7; ++a) {
+            V t = (k < k0) ? lam * xv[a] : V(0);
+#pragma unroll
+            for (int c = 0; c < 7; ++c) t += __ldg(B + (tr ? c * 7 + a : a * 7 + c)) * xv[c];
+            acc[a] += t;
+          }
+        }
+      } else {
+        const V* Ab = AV<V>::a(Lv);
+        const int k1 = __ldg(Lv.a_ptr + u + 1);
+        for (int k = __ldg(Lv.a_ptr + u) + lane; k < k1; k += 32) {
+          const int w = __ldg(Lv.a_col + k);
+          V xv[7];
+#pragma unroll
+          for (int c = 0; c < 7; ++c) xv[c] = sc * __ldcg(x + (size_t)w * VEC + c);
+          const V* B = Ab + (size_t)k * BLK;
+#pragma unroll
+          for (int a = 0; a < 7; ++a) {
+            V t = V(0);
+#pragma unroll
+            for (int c = 0; c < 7; ++c) t += __ldcg(B + a * 7 + c) * xv[c];
+            acc[a] += t;
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 7; ++a)
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
+    // y = D^-1 acc (lane a < 7 owns component a; lane 7 writes the pad)
+    if (lane < 8) {
+      V yv = V(0);
+      if (lane < 7 && live) {
+        const V* M = l == 0 ? AV<V>::minv(g) + (size_t)u * BLK : AV<V>::dinv(Lv) + (size_t)u * BLK;
+#pragma unroll
+        for (int c = 0; c < 7; ++c) yv += __ldcg(M + lane * 7 + c) * acc[c];
+      }
+      y[(size_t)u * VEC + lane] = yv;
+      nrm += (double)yv * (double)yv;
+    }
+  }
+  return nrm;
+}
+
+template <class V>
+__global__ void __launch_bounds__(256) k_amg_setup(DevGraph g) {
+  SolverState* st = g.st;
+  if (st->done) return;
+  // the hierarchy descriptor, cached in shared memory
+  __shared__ AmgDev sA;
+  {
+    static_assert(sizeof(AmgDev) % 8 == 0, "descriptor copy by 8-byte words");
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(g.amg);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sA);
+    for (int t = threadIdx.x; t < (int)(sizeof(AmgDev) / 8); t += blockDim.x) dst[t] = src[t];
+    __syncthreads();
+  }
+  const AmgDev& A = sA;
+  unsigned* counter = &st->ticket[T_AMG];
+  int* abort_flag = reinterpret_cast<int*>(&st->ticket[T_AMG_ABORT]);
+  unsigned target = 0;
+  constexpr int BLK = AV<V>::BLK;
+  const V lam = V(st->lambda);
+  const int cur = st->cur;
+  const int warm_slot = sizeof(V) == sizeof(double) ? 0 : 1;
+  const bool warm = __ldcg(g.amg->warm + warm_slot) != 0;
+  double* partial = g.partial;
+  __shared__ V sacc[4][49];
+  extern __shared__ double dense[];   // coarsest operator (block 0 only)
+
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int gthreads = gridDim.x * blockDim.x;
+  // ---- tentative prolongation blocks T = Adj(S_ref S_refc^-1), all levels ----
+  {
+    int base = 0;
+    for (int l = 0; l < A.L; ++l) {
+      const AmgLevel& Lv = A.lv[l];
+      for (int u = gtid; u < Lv.n; u += gthreads) {
+        if (__ldg(Lv.agg + u) < 0) continue;
+        const Sim3T<double> Sr = load_pose(g, cur, __ldg(Lv.ref + u));
+        const Sim3T<double> Sc = load_pose(g, cur, __ldg(Lv.refc + u));
+        double T[7][7];
+        adj7(compose(Sr, inverse(Sc)), T);
+        V* out = AV<V>::t(Lv) + (size_t)u * BLK;
+#pragma unroll
+        for (int i = 0; i < 7; ++i)
+#pragma unroll
+          for (int j = 0; j < 7; ++j) out[i * 7 + j] = V(T[i][j]);
+      }
+      base += Lv.n;
+    }
+    (void)base;
+    if (gtid == 0) *A.flag = 0;
+  }
+  if (!grid_sync(counter, abort_flag, target)) goto timeout;
+
+  for (int l = 0; l < A.L; ++l) {
+    const AmgLevel& Lv = A.lv[l];
+    const AmgLevel& Ln = A.lv[l + 1];
+    // ---- rho(D^-1 A) by power iteration ----
+    double rho;
+    {
+      // start from the vector the previous set-up of this graph ended with
+      // (H, lambda and the poses change little between linearisations),
+      // else from a fixed smooth vector
+      V* x0 = AV<V>::pw(A, 0);
+      V* pv = AV<V>::pv(Lv);
+      const double rho_prev = __ldcg(A.rho + l);   // written after the barriers below
+      double nrm = 0.0;
+      for (int t = gtid; t < Lv.n * VEC; t += gthreads) {
+        const int u = t / VEC, k = t - u * VEC;
+        const bool on = k < 7 && !(l == 0 && u == g.fixed);
+        double v = 0.0;
+        if (on) v = warm ? (double)__ldcg(pv + t) : 1.0 + 0.5 * sin(0.7 * (double)(7 * u + k));
+        x0[t] = V(v);
+        nrm += v * v;
+      }
+      block_partial(nrm, partial);
+      if (!grid_sync(counter, abort_flag, target)) goto timeout;
+      double nx = sqrt(grid_sum_after_sync(partial));
+      if (!(nx > 0.0) || !isfinite(nx)) nx = 0.0;
+      const int its = warm ? AMG_POWER_ITS_WARM : AMG_POWER_ITS;
+      for (int it = 0; it < its; ++it) {
+        const V* xin = AV<V>::pw(A, it & 1);
+        V* yout = AV<V>::pw(A, (it + 1) & 1);
+        const V sc = V(nx > 0.0 ? 1.0 / nx : 0.0);
+        double ny2 = power_step<V>(g, Lv, l, lam, xin, sc, yout);
+        double* pset = partial + ((it + 1) & 1) * gridDim.x;
+        block_partial(ny2, pset);
+        if (!grid_sync(counter, abort_flag, target)) goto timeout;
+        nx = sqrt(grid_sum_after_sync(pset));
+      }
+      rho = nx > 1e-30 ? nx : 1.0;
+      // a few warm iterations approach rho from below; never go under the
+      // previous estimate (an underestimate weakens the smoother's damping)
+      if (warm && rho_prev > rho && isfinite(rho_prev)) rho = rho_prev;
+      if (gtid == 0) A.rho[l] = rho;
+      const V* yl = AV<V>::pw(A, its & 1);
+      for (int t = gtid; t < Lv.n * VEC; t += gthreads) pv[t] = __ldcg(yl + t);
+    }
+    // ---- P = T_agg - 4/(3 rho) D^-1 (A T) ----
+    {
+      const double f = 4.0 / (3.0 * rho);
+      const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
+      const int i = t / 7, j = t - 7 * (t / 7);
+      const bool lane_on = t < 49;
+      const V* Tb = AV<V>::t(Lv);
+      V* Pb = AV<V>::p(Lv);
+      for (int b0 = blockIdx.x * 4; b0 < Lv.nnz_p; b0 += gridDim.x * 4) {
+        const int b = b0 + slot;
+        const bool has = b < Lv.nnz_p;
+        int u = 0, c = 0;
+        if (has && lane_on) {
+          u = __ldg(Lv.p_row + b);
+          c = __ldg(Lv.p_col + b);
+          const int e0 = __ldg(Lv.r1_ptr + b), e1 = __ldg(Lv.r1_ptr + b + 1);
+          sacc[slot][t] = l == 0 ? recipe_ax<V, true>(g, nullptr, lam, Lv.r1, e0, e1, Tb, i, j)
+                                 : recipe_ax<V, false>(g, AV<V>::a(Lv), lam, Lv.r1, e0, e1, Tb, i, j);
+        }
+        __syncthreads();
+        if (has && lane_on) {
+          const V* M = (l == 0 ? AV<V>::minv(g) : AV<V>::dinv(Lv)) + (size_t)u * BLK;
+          V s = V(0);
+#pragma unroll
+          for (int k = 0; k < 7; ++k) s += __ldcg(M + i * 7 + k) * sacc[slot][k * 7 + j];
+          const V tv = (c == __ldg(Lv.agg + u)) ? __ldcg(Tb + (size_t)u * BLK + i * 7 + j) : V(0);
+          Pb[(size_t)b * BLK + i * 7 + j] = tv - V(f) * s;
+        }
+        __syncthreads();
+      }
+    }
+    if (!grid_sync(counter, abort_flag, target)) goto timeout;
+    // ---- AP = A P ----
+    {
+      const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
+      const int i = t / 7, j = t - 7 * (t / 7);
+      const V* Pb = AV<V>::p(Lv);
+      V* APb = AV<V>::ap(Lv);
+      for (int b = blockIdx.x * 4 + slot; b < Lv.nnz_ap; b += gridDim.x * 4) {
+        if (t >= 49) continue;
+        const int e0 = __ldg(Lv.r2_ptr + b), e1 = __ldg(Lv.r2_ptr + b + 1);
+        APb[(size_t)b * BLK + i * 7 + j] = l == 0 ? recipe_ax<V, true>(g, nullptr, lam, Lv.r2, e0, e1, Pb, i, j)
+                                                  : recipe_ax<V, false>(g, AV<V>::a(Lv), lam, Lv.r2, e0, e1, Pb, i, j);
+      }
+    }
+    if (!grid_sync(counter, abort_flag, target)) goto timeout;
+    // ---- A_next = P^T (A P), upper blocks ----
+    {
+      const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
+      const int i = t / 7, j = t - 7 * (t / 7);
+      const V* Pb = AV<V>::p(Lv);
+      const V* APb = AV<V>::ap(Lv);
+      V* An = AV<V>::a(Ln);
+      for (int b = blockIdx.x * 4 + slot; b < Lv.nnz_next; b += gridDim.x * 4) {
+        if (t >= 49) continue;
+        const int e0 = __ldg(Lv.r3_ptr + b), e1 = __ldg(Lv.r3_ptr + b + 1);
+        if (e0 == e1) continue;   // mirrored block
+        An[(size_t)b * BLK + i * 7 + j] = recipe_ptq<V>(Lv.r3, e0, e1, Pb, APb, i, j);
+      }
+    }
+    if (!grid_sync(counter, abort_flag, target)) goto timeout;
+    // ---- mirror the lower blocks; then the next level's D^-1 ----
+    {
+      V* An = AV<V>::a(Ln);
+      for (int t = gtid; t < Lv.nnz_next * 49; t += gthreads) {
+        const int b = t / 49, ij = t - 49 * b;
+        const int src = __ldg(Ln.a_src + b);
+        if (src < 0) continue;
+        const int i = ij / 7, j = ij - 7 * (ij / 7);
+        An[(size_t)b * BLK + i * 7 + j] = __ldcg(An + (size_t)src * BLK + j * 7 + i);
+      }
+    }
+    if (!grid_sync(counter, abort_flag, target)) goto timeout;
+    if (l + 1 < A.L) {
+      const V* An = AV<V>::a(Ln);
+      for (int c = gtid; c < Ln.n; c += gthreads) {
+        V Bl[49];
+        const V* src = An + (size_t)__ldg(Ln.a_ptr + c) * BLK;
+#pragma unroll
+        for (int k = 0; k < 49; ++k) Bl[k] = __ldcg(src + k);
+        inv7_spd<V>(Bl, AV<V>::dinv(Ln) + (size_t)c * BLK);
+      }
+      if (!grid_sync(counter, abort_flag, target)) goto timeout;
+    }
+  }
+  // ---- coarsest level: dense inverse (block 0, Gauss-Jordan on the SPD matrix) ----
+  if (blockIdx.x == 0) {
+    const AmgLevel& Lc = A.lv[A.L];
+    const int nL = Lc.n, n7 = 7 * nL;
+    const V* Ab = AV<V>::a(Lc);
+    for (int t = threadIdx.x; t < n7 * n7; t += blockDim.x) dense[t] = 0.0;
+    __syncthreads();
+    for (int c = 0; c < nL; ++c)
+      for (int k = Lc.a_ptr[c]; k < Lc.a_ptr[c + 1]; ++k) {
+        const int d = Lc.a_col[k];
+        for (int ij = threadIdx.x; ij < 49; ij += blockDim.x) {
+          const int i = ij / 7, j = ij - 7 * (ij / 7);
+          dense[(7 * c + i) * n7 + 7 * d + j] = (double)__ldcg(Ab + (size_t)k * BLK + ij);
+        }
+      }
+    __syncthreads();
+    __shared__ int bad;
+    if (threadIdx.x == 0) bad = 0;
+    __syncthreads();
+    double* colk = dense + (size_t)n7 * n7;   // column k, saved before the pass
+    for (int k = 0; k < n7; ++k) {
+      const double piv = dense[k * n7 + k];
+      if (!(piv > 0.0) || !isfinite(piv)) {   // uniform: every thread reads the same pivot
+        if (threadIdx.x == 0) bad = 1;
+        break;
+      }
+      const double ip = 1.0 / piv;
+      for (int i = threadIdx.x; i < n7; i += blockDim.x) colk[i] = dense[i * n7 + k];
+      __syncthreads();
+      for (int j = threadIdx.x; j < n7; j += blockDim.x) dense[k * n7 + j] = (j == k) ? ip : dense[k * n7 + j] * ip;
+      __syncthreads();
+      for (int t = threadIdx.x; t < n7 * n7; t += blockDim.x) {
+        const int i = t / n7, j = t - n7 * i;
+        if (i == k) continue;
+        const double fik = colk[i];
+        dense[t] = (j == k) ? -fik * ip : dense[t] - fik * dense[k * n7 + j];
+      }
+      __syncthreads();
+    }
+    __syncthreads();
+    V* Ci = AV<V>::cinv(A);
+    const bool ok = bad == 0;
+    for (int t = threadIdx.x; t < nL * nL * 49; t += blockDim.x) {
+      const int cd = t / 49, ij = t - 49 * cd;
+      const int c = cd / nL, d = cd - nL * c;
+      const int i = ij / 7, j = ij - 7 * (ij / 7);
+      const int R = 7 * c + i, C = 7 * d + j;
+      const double v = ok ? 0.5 * (dense[R * n7 + C] + dense[C * n7 + R]) : 0.0;
+      Ci[(size_t)cd * BLK + ij] = V(v);
+    }
+    if (threadIdx.x == 0 && !ok) *A.flag = 1;
+    if (threadIdx.x == 0) A.warm[warm_slot] = 1;
+  }
+  grid_sync_release(&st->ticket[T_AMG_DONE], counter, nullptr);
+  return;
+timeout:
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->status = PGO_ERR_CUDA;
+}
+
+static int amg_sms() {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+cudaError_t launch_amg_setup(const DevGraph& g, const AmgDev& amg, int mixed, cudaStream_t s) {
+  const int blocks = amg_sms();
+  const size_t n7 = (size_t)7 * amg.nL;
+  const size_t smem = (n7 * n7 + n7) * sizeof(double);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(blocks);
+  cfg.blockDim = dim3(256);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (mixed) {
+    cudaError_t e = cudaFuncSetAttribute(k_amg_setup<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaLaunchKernelEx(&cfg, k_amg_setup<float>, g);
+  }
+  cudaError_t e = cudaFuncSetAttribute(k_amg_setup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaLaunchKernelEx(&cfg, k_amg_setup<double>, g);
+}
+
+}  // namespace pgo

@@ -138,6 +138,10 @@ struct pgo_graph {
   bool solved = false;
   bool has_info = false;
   bool lin_valid = false;
+  // multigrid hierarchy, analysed at the first solve that uses it
+  AmgHost* amg = nullptr;
+  bool amg_failed = false;
+  std::vector<int> h_inc_ptr, h_inc_code, h_inc_other;
 };
 
 struct pgo_batch {
@@ -177,39 +181,80 @@ pgo_status check_options(const pgo_solve_options& o) {
     return fail(PGO_ERR_INVALID_ARG, "options: unknown precision %d", o.precision);
   if (!(o.tau > 0) || !(o.pcg_tol > 0) || !(o.refine_tol > 0) || !(o.ftol >= 0) || !(o.gtol >= -1.0))
     return fail(PGO_ERR_INVALID_ARG, "options: tau, pcg_tol, refine_tol must be > 0");
+  if (o.preconditioner != PGO_PRECOND_BLOCK_JACOBI && o.preconditioner != PGO_PRECOND_MULTIGRID)
+    return fail(PGO_ERR_INVALID_ARG, "options: unknown preconditioner %d", o.preconditioner);
   return PGO_OK;
 }
 
-// The linear-solve part of one LM iteration: block-Jacobi preconditioner,
-// then one persistent PCG launch (FP64), or, in mixed precision, FP32 PCG
-// launches inside FP64 iterative refinement (refine_steps passes, each
-// skipped on the device once the FP64 residual meets pcg_tol).
-void enqueue_linear_solve(const DevGraph& g, int mixed, int refine_steps, cudaStream_t s, cudaError_t* err) {
+// The preconditioner set-up and the PCG launches of one linear solve at the
+// current linearisation (amg: multigrid hierarchy, nullptr: block-Jacobi).
+void enqueue_pcg(const DevGraph& g, int mixed, const AmgDev* amg, int from_residual, cudaStream_t s,
+                 cudaError_t* err) {
+  cudaError_t e = launch_pcg(g, mixed, from_residual, amg, s);
+  if (e != cudaSuccess && *err == cudaSuccess) *err = e;
+}
+
+void enqueue_precond(const DevGraph& g, int mixed, const AmgDev* amg, cudaStream_t s, cudaError_t* err) {
   launch_precond(g, mixed, s);
-  if (!mixed) {
-    cudaError_t e = launch_pcg(g, 0, 0, s);
+  if (amg) {
+    cudaError_t e = launch_amg_setup(g, *amg, mixed, s);
     if (e != cudaSuccess && *err == cudaSuccess) *err = e;
+  }
+}
+
+// The linear-solve part of one LM iteration: the preconditioner (block-Jacobi
+// blocks, plus the multigrid hierarchy when enabled), then one persistent PCG
+// launch (FP64), or, in mixed precision, FP32 PCG launches inside FP64
+// iterative refinement (refine_steps passes, each skipped on the device once
+// the FP64 residual meets pcg_tol).
+void enqueue_linear_solve(const DevGraph& g, int mixed, int refine_steps, const AmgDev* amg, cudaStream_t s,
+                          cudaError_t* err) {
+  enqueue_precond(g, mixed, amg, s, err);
+  if (!mixed) {
+    enqueue_pcg(g, 0, amg, 0, s, err);
     return;
   }
   for (int pass = 0; pass < refine_steps; ++pass) {
     launch_refine_residual(g, pass == 0, s);
-    cudaError_t e = launch_pcg(g, 1, 1, s);
-    if (e != cudaSuccess && *err == cudaSuccess) *err = e;
+    enqueue_pcg(g, 1, amg, 1, s, err);
     launch_refine_accumulate(g, s);
   }
 }
 
 // One LM iteration (the body of the WHILE node, or one host-driven step).
-void enqueue_lm_body(const DevGraph& g, int mixed, int refine_steps, cudaStream_t s, unsigned long long lm_cond,
-                     cudaError_t* err) {
+void enqueue_lm_body(const DevGraph& g, int mixed, int refine_steps, const AmgDev* amg, cudaStream_t s,
+                     unsigned long long lm_cond, cudaError_t* err) {
   launch_linearize(g, mixed, s);
   launch_assemble(g, mixed, s);
-  enqueue_linear_solve(g, mixed, refine_steps, s, err);
+  enqueue_linear_solve(g, mixed, refine_steps, amg, s, err);
   launch_update(g, mixed, s);
   launch_cost(g, 1, s, lm_cond);
 }
 
-pgo_status build_solve_graph(pgo_graph* G, int mixed, int refine_steps, cudaGraphExec_t* out) {
+// The hierarchy (host descriptor) if the options ask for multigrid and the
+// graph has one; nullptr selects block-Jacobi.
+const AmgDev* amg_for(const pgo_graph* G, int precond) {
+  return precond == PGO_PRECOND_MULTIGRID && G->amg ? amg_host_desc(G->amg) : nullptr;
+}
+
+// Analyses the multigrid hierarchy of the graph the first time a solve asks
+// for it.  A graph without free vertices has nothing to precondition and
+// keeps block-Jacobi.
+pgo_status ensure_amg(pgo_graph* G, int precond) {
+  if (precond != PGO_PRECOND_MULTIGRID || G->amg || G->amg_failed) return PGO_OK;
+  if (G->N < 2) {
+    G->amg_failed = true;
+    return PGO_OK;
+  }
+  const char* err = nullptr;
+  G->amg = amg_build(G->N, G->fixed, G->h_inc_ptr.data(), G->h_inc_code.data(), G->h_inc_other.data(), G->stream,
+                     &err);
+  if (!G->amg) return fail(PGO_ERR_OOM, "multigrid set-up: %s", err ? err : "unknown error");
+  G->g.amg = amg_device_desc(G->amg);
+  return PGO_OK;
+}
+
+pgo_status build_solve_graph(pgo_graph* G, int mixed, int refine_steps, const AmgDev* amg, cudaGraphExec_t* out) {
   const DevGraph& g = G->g;
   cudaGraph_t graph;
   CUDA_TRY(cudaGraphCreate(&graph, 0));
@@ -224,7 +269,7 @@ pgo_status build_solve_graph(pgo_graph* G, int mixed, int refine_steps, cudaGrap
   if (body) {
     GraphBuilder lb{G->cap_stream};
     cudaError_t le = cudaSuccess;
-    lb.capture(body, [&](cudaStream_t s) { enqueue_lm_body(g, mixed, refine_steps, s, hl, &le); });
+    lb.capture(body, [&](cudaStream_t s) { enqueue_lm_body(g, mixed, refine_steps, amg, s, hl, &le); });
     if (lb.err != cudaSuccess) b.err = lb.err;
     if (le != cudaSuccess) b.err = le;
   }
@@ -240,7 +285,7 @@ pgo_status build_solve_graph(pgo_graph* G, int mixed, int refine_steps, cudaGrap
 
 // A linear solve at a given lambda (pgo_graph_damped_step): linearise, then
 // the same linear-solve sequence as one LM iteration.
-pgo_status build_step_graph(pgo_graph* G, int mixed, int refine_steps, cudaGraphExec_t* out) {
+pgo_status build_step_graph(pgo_graph* G, int mixed, int refine_steps, const AmgDev* amg, cudaGraphExec_t* out) {
   const DevGraph& g = G->g;
   cudaGraph_t graph;
   CUDA_TRY(cudaGraphCreate(&graph, 0));
@@ -249,7 +294,7 @@ pgo_status build_step_graph(pgo_graph* G, int mixed, int refine_steps, cudaGraph
   b.capture(graph, [&](cudaStream_t s) {
     launch_linearize(g, mixed, s);
     launch_assemble(g, mixed, s);
-    enqueue_linear_solve(g, mixed, refine_steps, s, &le);
+    enqueue_linear_solve(g, mixed, refine_steps, amg, s, &le);
   });
   if (le != cudaSuccess) b.err = le;
   if (b.err != cudaSuccess) {
@@ -264,7 +309,7 @@ pgo_status build_step_graph(pgo_graph* G, int mixed, int refine_steps, cudaGraph
 
 // Host-driven LM loop with plain stream launches (schedule 1): the same
 // kernels, for profilers that cannot look inside conditional graph nodes.
-pgo_status run_eager(pgo_graph* G, int mixed, int refine_steps, int max_iters) {
+pgo_status run_eager(pgo_graph* G, int mixed, int refine_steps, int max_iters, const AmgDev* amg) {
   const DevGraph& g = G->g;
   cudaStream_t s = G->stream;
   cudaError_t le = cudaSuccess;
@@ -274,7 +319,7 @@ pgo_status run_eager(pgo_graph* G, int mixed, int refine_steps, int max_iters) {
     CUDA_TRY(cudaMemcpyAsync(G->h_state, g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     if (G->h_state->done || G->h_state->it >= max_iters) break;
-    enqueue_lm_body(g, mixed, refine_steps, s, 0, &le);
+    enqueue_lm_body(g, mixed, refine_steps, amg, s, 0, &le);
     CUDA_TRY(le);
     CUDA_TRY(cudaGetLastError());
   }
@@ -282,7 +327,7 @@ pgo_status run_eager(pgo_graph* G, int mixed, int refine_steps, int max_iters) {
 }
 
 // Re-solve at the last linearisation: state reset, then the linear solve.
-pgo_status build_resolve_graph(pgo_graph* G, int mixed, int refine_steps, cudaGraphExec_t* out) {
+pgo_status build_resolve_graph(pgo_graph* G, int mixed, int refine_steps, const AmgDev* amg, cudaGraphExec_t* out) {
   const DevGraph& g = G->g;
   cudaGraph_t graph;
   CUDA_TRY(cudaGraphCreate(&graph, 0));
@@ -290,7 +335,7 @@ pgo_status build_resolve_graph(pgo_graph* G, int mixed, int refine_steps, cudaGr
   cudaError_t le = cudaSuccess;
   b.capture(graph, [&](cudaStream_t s) {
     launch_resolve_reset(g, s);
-    enqueue_linear_solve(g, mixed, refine_steps, s, &le);
+    enqueue_linear_solve(g, mixed, refine_steps, amg, s, &le);
   });
   if (le != cudaSuccess) b.err = le;
   if (b.err != cudaSuccess) {
@@ -303,17 +348,18 @@ pgo_status build_resolve_graph(pgo_graph* G, int mixed, int refine_steps, cudaGr
   return PGO_OK;
 }
 
-pgo_status get_exec(pgo_graph* G, int kind, int mixed, int refine_steps, cudaGraphExec_t* out) {
-  const long long key = ((long long)kind << 32) | ((long long)mixed << 16) | (mixed ? refine_steps : 0);
+pgo_status get_exec(pgo_graph* G, int kind, int mixed, int refine_steps, const AmgDev* amg, cudaGraphExec_t* out) {
+  const long long key = ((long long)kind << 32) | ((long long)(amg != nullptr) << 24) | ((long long)mixed << 16) |
+                        (mixed ? refine_steps : 0);
   auto it = G->execs.find(key);
   if (it != G->execs.end()) {
     *out = it->second;
     return PGO_OK;
   }
   cudaGraphExec_t ex = nullptr;
-  pgo_status st = kind == 0   ? build_solve_graph(G, mixed, refine_steps, &ex)
-                  : kind == 1 ? build_step_graph(G, mixed, refine_steps, &ex)
-                              : build_resolve_graph(G, mixed, refine_steps, &ex);
+  pgo_status st = kind == 0   ? build_solve_graph(G, mixed, refine_steps, amg, &ex)
+                  : kind == 1 ? build_step_graph(G, mixed, refine_steps, amg, &ex)
+                              : build_resolve_graph(G, mixed, refine_steps, amg, &ex);
   if (st != PGO_OK) return st;
   G->execs[key] = ex;
   *out = ex;
@@ -388,6 +434,7 @@ pgo_status pgo_default_options(pgo_solve_options* opt) {
   opt->refine_tol = 1e-6;
   opt->polish_iters = 0;
   opt->schedule = -1;
+  opt->preconditioner = PGO_PRECOND_MULTIGRID;
   return PGO_OK;
 }
 
@@ -485,6 +532,9 @@ pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
   pgo_graph* G = new pgo_graph();
   G->N = N;
   G->E = E;
+  G->h_inc_ptr = inc_ptr;
+  G->h_inc_code = inc_code;
+  G->h_inc_other = inc_other;
   G->fixed = d->fixed_vertex;
   G->stream = (cudaStream_t)d->stream;
   G->has_info = d->info != nullptr;
@@ -617,6 +667,7 @@ void pgo_graph_destroy(pgo_graph* G) {
   if (G->h_state) cudaFreeHost(G->h_state);
   if (G->h_opt) cudaFreeHost(G->h_opt);
   if (G->arena.base) cudaFree(G->arena.base);
+  amg_free(G->amg);
   delete G;
 }
 
@@ -747,7 +798,9 @@ pgo_status pgo_graph_damped_step(pgo_graph* G, const pgo_solve_options* opt, dou
   if (st != PGO_OK) return st;
   const int mixed = o.precision == PGO_MIXED;
   cudaGraphExec_t ex;
-  st = get_exec(G, 1, mixed, o.refine_steps, &ex);
+  st = ensure_amg(G, o.preconditioner);
+  if (st != PGO_OK) return st;
+  st = get_exec(G, 1, mixed, o.refine_steps, amg_for(G, o.preconditioner), &ex);
   if (st != PGO_OK) return st;
   st = prepare_standalone(G, o, lambda);
   if (st != PGO_OK) return st;
@@ -789,9 +842,12 @@ static pgo_status run_polish(pgo_graph* G, const pgo_solve_options& o) {
   double b0 = 0.0, g0 = 0.0;
   pgo_status st = linearize_here(&b0, &g0);
   if (st != PGO_OK) return st;
+  const AmgDev* amg = amg_for(G, o.preconditioner);
   for (int k = 0; k < o.polish_iters && g0 > o.gtol; ++k) {
-    launch_precond(g, 0, s);
-    CUDA_TRY(launch_pcg(g, 0, 0, s));       // delta = -H^-1 b (x64)
+    cudaError_t le = cudaSuccess;
+    enqueue_precond(g, 0, amg, s, &le);
+    enqueue_pcg(g, 0, amg, 0, s, &le);      // delta = -H^-1 b (x64)
+    CUDA_TRY(le);
     bool improved = false;
     double b1 = 0.0, g1 = 0.0;
     for (int half = 0; half < 4 && !improved; ++half) {
@@ -827,7 +883,9 @@ pgo_status pgo_graph_resolve(pgo_graph* G, const pgo_solve_options* opt, double 
   if (st != PGO_OK) return st;
   const int mixed = o.precision == PGO_MIXED;
   cudaGraphExec_t ex;
-  st = get_exec(G, 2, mixed, o.refine_steps, &ex);
+  st = ensure_amg(G, o.preconditioner);
+  if (st != PGO_OK) return st;
+  st = get_exec(G, 2, mixed, o.refine_steps, amg_for(G, o.preconditioner), &ex);
   if (st != PGO_OK) return st;
   cudaStream_t s = G->stream;
   fill_dev_options(o, G->h_opt);
@@ -893,8 +951,10 @@ pgo_status pgo_solve(pgo_graph* G, const pgo_solve_options* opt, pgo_report* rep
   const int mixed = o.precision == PGO_MIXED;
   const bool eager = o.schedule == 1;
   cudaGraphExec_t ex = nullptr;
+  st = ensure_amg(G, o.preconditioner);
+  if (st != PGO_OK) return st;
   if (!eager) {
-    st = get_exec(G, 0, mixed, o.refine_steps, &ex);
+    st = get_exec(G, 0, mixed, o.refine_steps, amg_for(G, o.preconditioner), &ex);
     if (st != PGO_OK) return st;
   }
   cudaStream_t s = G->stream;
@@ -902,7 +962,7 @@ pgo_status pgo_solve(pgo_graph* G, const pgo_solve_options* opt, pgo_report* rep
   CUDA_TRY(cudaMemcpyAsync(G->g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaEventRecord(G->ev0, s));
   if (eager) {
-    st = run_eager(G, mixed, o.refine_steps, o.max_iters);
+    st = run_eager(G, mixed, o.refine_steps, o.max_iters, amg_for(G, o.preconditioner));
     if (st != PGO_OK) return st;
   } else {
     CUDA_TRY(cudaGraphLaunch(ex, s));
@@ -966,8 +1026,11 @@ pgo_status pgo_backward(pgo_graph* G, const pgo_solve_options* opt, const double
   launch_assemble_mode(g, 1, s);      // diagonal blocks
   launch_adj_rhs(g, dl, layout, s);   // b = -dL/dx
   cudaError_t le = cudaSuccess;
-  launch_precond(g, 0, s);
-  le = launch_pcg(g, 0, 0, s);        // mu = H^-1 dL/dx  (x64)
+  st = ensure_amg(G, o.preconditioner);
+  if (st != PGO_OK) return st;
+  const AmgDev* amg = amg_for(G, o.preconditioner);
+  enqueue_precond(g, 0, amg, s, &le);
+  enqueue_pcg(g, 0, amg, 0, s, &le);  // mu = H^-1 dL/dx  (x64)
   CUDA_TRY(le);
   double* om = dL_dmeas ? (mem_space == PGO_MEM_DEVICE ? dL_dmeas : d_out_meas) : nullptr;
   double* ow = dL_dweight ? (mem_space == PGO_MEM_DEVICE ? dL_dweight : d_out_w) : nullptr;

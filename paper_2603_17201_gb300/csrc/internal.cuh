@@ -23,7 +23,7 @@ constexpr int CONTRIB = 36; // per edge-side: 28 upper-triangular H entries + 7 
 // Reduction tickets (one per reducing kernel family).
 enum Ticket {
   T_ASSEMBLE = 0, T_PCG_INIT, T_PCG_SPMV, T_PCG_UPDATE, T_UPDATE, T_COST, T_REFINE,
-  T_COST_STATELESS, T_POLISH, T_MISC, T_COUNT
+  T_COST_STATELESS, T_POLISH, T_MISC, T_AMG, T_AMG_ABORT, T_AMG_DONE, T_COUNT
 };
 
 // Device-resident solver state (LM + PCG scalars); one per graph.
@@ -49,6 +49,77 @@ struct DevOptions {
   int max_iters, precision, pcg_max_iters, refine_steps, polish_iters;
   double tau, lambda_init, ftol, gtol, pcg_tol, refine_tol;
   double lambda_fixed;   // lambda of a standalone re-solve
+};
+
+// ---- smoothed-aggregation multigrid preconditioner ----
+// Level 0 is the damped normal matrix over the vertices; level l + 1 has one
+// node per aggregate of AMG_M consecutive level-l nodes, with 7 coarse
+// unknowns each (the aggregate's rigid Sim(3) motion), down to at most
+// AMG_CMAX nodes, which are solved exactly.
+constexpr int AMG_M = 4;
+constexpr int AMG_CMAX = 8;
+constexpr int AMG_MAXL = 12;
+constexpr int AMG_POWER_ITS = 12;       // first set-up of a graph
+constexpr int AMG_POWER_ITS_WARM = 3;   // later set-ups, from the previous vector
+
+struct AmgLevel {
+  int n, n_next;          // nodes at this level and at the next
+  int nnz_a, nnz_p, nnz_ap, nnz_next;
+  // operator of levels >= 1: block-CSR, full rows, the diagonal block first;
+  // a_src[k] >= 0: block k is the transpose of block a_src[k]
+  const int* a_ptr;
+  const int* a_col;
+  const int* a_src;
+  double* a64;
+  float* a32;
+  double* dinv64;         // levels >= 1: inverse diagonal blocks
+  float* dinv32;
+  double* t64;            // tentative prolongation block per node
+  float* t32;
+  const int* ref;         // reference vertex of each node
+  const int* refc;        // reference vertex of the node's aggregate
+  const int* agg;         // next-level node of each node (-1: the fixed vertex)
+  // smoothed prolongation P (n x n_next): block-CSR, its row per block, CSC
+  const int* p_ptr;
+  const int* p_col;
+  const int* p_row;
+  double* p64;
+  float* p32;
+  const int* pt_ptr;
+  const int* pt_row;
+  const int* pt_blk;
+  // A P (n x n_next), block-CSR
+  const int* ap_ptr;
+  const int* ap_col;
+  double* ap64;
+  float* ap32;
+  // numeric recipes (CSR lists of index pairs per output block)
+  const int* r1_ptr;      // per P block: (A ref, node w) terms of A T
+  const int2* r1;
+  const int* r2_ptr;      // per AP block: (A ref, P block)
+  const int2* r2;
+  const int* r3_ptr;      // per next-level block (upper half): (P block, AP block)
+  const int2* r3;
+  // V-cycle vectors (n x VEC): restricted residual, pre-smoothed iterate,
+  // residual after pre-smoothing, result
+  double *vr64, *vx64, *vs64, *vy64;
+  float *vr32, *vx32, *vs32, *vy32;
+  // power-iteration vector kept from the previous set-up (warm start)
+  double* pv64;
+  float* pv32;
+};
+
+struct AmgDev {
+  int L;                  // smoothing levels 0..L-1; level L is the coarsest
+  int nL;                 // nodes at the coarsest level
+  AmgLevel lv[AMG_MAXL + 1];
+  double* cinv64;         // dense inverse of the coarsest operator (nL x nL blocks)
+  float* cinv32;
+  double* rho;            // per level: power-iteration estimate of rho(D^-1 A)
+  double* pw64[2];        // power-iteration vectors
+  float* pw32[2];
+  int* flag;              // nonzero: the coarsest factorisation failed
+  int* warm;              // [0] FP64, [1] FP32: a previous set-up left pv vectors
 };
 
 // Device view of one graph.
@@ -87,6 +158,7 @@ struct DevGraph {
   int partial_cap;
   SolverState* st;
   DevOptions* opt;
+  const AmgDev* amg;      // multigrid hierarchy (device), or nullptr
 };
 
 // ---- batched form (one thread block solves one graph at a time) ----
@@ -135,7 +207,18 @@ void launch_set_meas(const DevGraph& g, const int* perm, const double* meas8, co
 void launch_state_ctl(const DevGraph& g, int op, cudaStream_t s);
 void launch_scale_x(const DevGraph& g, double f, cudaStream_t s);
 void launch_precond(const DevGraph& g, int mixed, cudaStream_t s);
-cudaError_t launch_pcg(const DevGraph& g, int mixed, int from_residual, cudaStream_t s);
+// amg: host copy of the hierarchy (nullptr: block-Jacobi preconditioner)
+cudaError_t launch_pcg(const DevGraph& g, int mixed, int from_residual, const AmgDev* amg, cudaStream_t s);
+cudaError_t launch_amg_setup(const DevGraph& g, const AmgDev& amg, int mixed, cudaStream_t s);
+// Symbolic multigrid hierarchy of a graph (host analysis + one device
+// allocation); returns the host copy of the device descriptor.
+struct AmgHost;
+AmgHost* amg_build(int N, int fixed, const int* inc_ptr, const int* inc_code, const int* inc_other,
+                   cudaStream_t s, const char** err);
+void amg_free(AmgHost* h);
+const AmgDev* amg_host_desc(const AmgHost* h);
+const AmgDev* amg_device_desc(const AmgHost* h);
+size_t amg_bytes(const AmgHost* h);
 int pcg_partials_needed(int N);
 void launch_refine_residual(const DevGraph& g, int first, cudaStream_t s);
 void launch_refine_accumulate(const DevGraph& g, cudaStream_t s);

@@ -19,6 +19,8 @@
 // The grid barrier is a monotone arrival counter (release add, acquire poll)
 // with a bounded spin: on timeout the kernel records PGO_ERR_CUDA in the
 // state and every block returns.
+#include "amg.cuh"
+#include "gridsync.cuh"
 #include "phases.cuh"
 
 namespace pgo {
@@ -109,48 +111,6 @@ __device__ __forceinline__ void load_p(const float* z, const float* pp, size_t b
   }
 }
 
-// ---- grid barrier ---------------------------------------------------------
-__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
-  unsigned v;
-  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
-  return v;
-}
-__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
-  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
-__device__ __forceinline__ unsigned long long globaltimer_ns() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-
-constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s: only reached on a fault
-
-// All blocks of the (co-resident) grid arrive; returns false if the wait
-// exceeded the time limit or another block reported a timeout.
-__device__ __forceinline__ bool grid_sync(unsigned* counter, int* abort_flag, unsigned& target) {
-  __shared__ int ok;
-  __syncthreads();
-  target += gridDim.x;
-  if (threadIdx.x == 0) {
-    ok = 1;
-    red_release_add(counter, 1u);
-    const unsigned long long t0 = globaltimer_ns();
-    unsigned spins = 0;
-    while (ld_acquire_u32(counter) < target) {
-      if ((++spins & 255u) == 0u &&
-          (globaltimer_ns() - t0 > kBarrierTimeoutNs || *(volatile int*)abort_flag)) {
-        atomicExch(abort_flag, 1);
-        ok = 0;
-        break;
-      }
-    }
-  }
-  __syncthreads();
-  return ok != 0;
-}
-
 template <class S>
 struct PcgShared {
   S red[32 * 2];
@@ -211,6 +171,7 @@ struct PcgArgs {
   int inner;           // tolerance: 0 -> pcg_tol, 1 -> refine_tol
   int rows_per_block;  // contiguous block-row range per block
   int cap_entries;     // off-diagonal blocks staged in shared memory per block
+  int amg;             // 1: multigrid V-cycle preconditioner, 0: block-Jacobi
 };
 
 // Plain (generic-address) 7x7 block loads: the block may sit in shared or
@@ -284,6 +245,368 @@ __device__ __forceinline__ void stage_blocks(V* dst, const V* src_base, const in
   }
 }
 
+// ---- multigrid V-cycle (inside the persistent PCG kernel) -----------------
+// Level-0 context: the block's rows and its staged operator.
+template <class V>
+struct L0Ctx {
+  const V* s_diag;
+  const V* s_minv;
+  const V* s_off;
+  const int* s_code;
+  const int* s_other;
+  const V* off;
+  int nst, e0, row0, row1;
+  V lam;
+};
+
+// 8-vector from L2 (vectors written by other blocks of this launch).
+__device__ __forceinline__ void ld8(const double* p, double (&x)[8]) {
+  const double2* p2 = reinterpret_cast<const double2*>(p);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double2 a = __ldcg(p2 + k);
+    x[2 * k] = a.x;
+    x[2 * k + 1] = a.y;
+  }
+}
+__device__ __forceinline__ void ld8(const float* p, float (&x)[8]) {
+  const float4* p4 = reinterpret_cast<const float4*>(p);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float4 a = __ldcg(p4 + k);
+    x[4 * k] = a.x;
+    x[4 * k + 1] = a.y;
+    x[4 * k + 2] = a.z;
+    x[4 * k + 3] = a.w;
+  }
+}
+
+template <class V, int G>
+__device__ __forceinline__ void group_reduce7(V (&y)[7], unsigned gmG) {
+#pragma unroll
+  for (int a2 = 0; a2 < 7; ++a2)
+#pragma unroll
+    for (int o2 = G / 2; o2 > 0; o2 >>= 1) y[a2] += __shfl_xor_sync(gmG, y[a2], o2);
+}
+
+// y = (H + lambda I) x for level-0 row v over the row's G lanes (x from L2);
+// after the call every lane of the group holds the row's 7 outputs.
+template <class V, int G>
+__device__ __forceinline__ void row_spmv0(const DevGraph& g, const L0Ctx<V>& c, int v, bool has, int sl,
+                                          unsigned gmG, const V* x, V (&y)[7]) {
+  constexpr int BLK = AV<V>::BLK;
+  const int k0 = has ? __ldg(g.inc_ptr + v) : 0, k1 = has ? __ldg(g.inc_ptr + v + 1) : -1;
+  const int ks = has ? __ldg(g.inc_split + v) : 0;
+#pragma unroll
+  for (int a2 = 0; a2 < 7; ++a2) y[a2] = V(0);
+  for (int k = k0 - 1 + sl; k < ks; k += G) {
+    const bool dg = k < k0;
+    const int l = k - c.e0;
+    int u = v;
+    const V* Bp;
+    if (dg) {
+      Bp = c.s_diag + (size_t)(v - c.row0) * BLK;
+    } else if (l < c.nst) {
+      u = c.s_other[l];
+      Bp = c.s_off + (size_t)l * BLK;
+    } else {
+      u = __ldg(g.inc_other + k);
+      Bp = c.off + (size_t)(__ldg(g.inc_code + k) >> 1) * BLK;
+    }
+    V pu[8];
+    ld8(x + (size_t)u * VEC, pu);
+    if (dg) {
+#pragma unroll
+      for (int a2 = 0; a2 < 7; ++a2) y[a2] += c.lam * pu[a2];
+    }
+    bmv<false>(Bp, pu, y);
+  }
+  for (int k = ks + sl; k < k1; k += G) {
+    const int l = k - c.e0;
+    int u;
+    const V* Bp;
+    if (l < c.nst) {
+      u = c.s_other[l];
+      Bp = c.s_off + (size_t)l * BLK;
+    } else {
+      u = __ldg(g.inc_other + k);
+      Bp = c.off + (size_t)(__ldg(g.inc_code + k) >> 1) * BLK;
+    }
+    V pu[8];
+    ld8(x + (size_t)u * VEC, pu);
+    bmv<true>(Bp, pu, y);
+  }
+  group_reduce7<V, G>(y, gmG);
+}
+
+// y[k] for a lane-dependent k without dynamic register indexing.
+template <class V>
+__device__ __forceinline__ V pick7(const V (&y)[7], int k) {
+  V r = y[0];
+#pragma unroll
+  for (int i = 1; i < 7; ++i)
+    if (k == i) r = y[i];
+  return r;
+}
+
+// out[a] = sum_c M[a][c] v[c] for the components a this lane stores.
+template <class V>
+__device__ __forceinline__ V dmul_row(const V* M, int a, const V (&v)[7]) {
+  V acc = V(0);
+#pragma unroll
+  for (int c = 0; c < 7; ++c) acc += M[a * 7 + c] * v[c];
+  return acc;
+}
+
+// Rows [r0, r1) of a coarse level, one warp per row (coarse rows have tens
+// of entries and few rows per block: a full warp keeps the latency of each
+// phase to about one entry per lane).
+constexpr int GC = 32;
+
+// The V(1,1) cycle after the caller has stored the level-0 pre-smoothed
+// iterate x0 = w0 D0^-1 r for its rows: residual and restriction down the
+// levels (the pre-smoothing of each coarser level is fused into the
+// restriction), the dense coarsest solve, then on the way up the
+// prolongation fused with the post-smoothing, using
+// r - A (x + P y) = s - (A P) y with s = r - A x kept from the way down.
+// Writes z for the block's rows and adds r.z to rz_loc.  Returns false on a
+// barrier timeout.
+template <class V, class S, int G>
+__device__ bool vcycle_rest(const DevGraph& g, const AmgDev& A, const L0Ctx<V>& c0, const V* r0v, V* s0, V* z,
+                            S& rz_loc, unsigned* counter, int* abort_flag, unsigned& target) {
+  constexpr int BLK = AV<V>::BLK;
+  const int sl = threadIdx.x & (G - 1);
+  const int sslot = threadIdx.x / G;
+  const int nsslots = blockDim.x / G;
+  const unsigned gmG = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << (threadIdx.x & (32 - G)));
+  const int cl = threadIdx.x & 31;          // coarse levels: lane in the row's warp
+  const int cslot = threadIdx.x >> 5;
+  const int ncslots = blockDim.x >> 5;
+  const unsigned full = 0xffffffffu;
+  const int L = A.L;
+  auto range = [&](int n, int& r0, int& r1) {
+    const int rpb = (n + gridDim.x - 1) / gridDim.x;
+    r0 = min((int)blockIdx.x * rpb, n);
+    r1 = min(r0 + rpb, n);
+  };
+  for (int l = 0; l < L; ++l) {
+    const AmgLevel& Lv = A.lv[l];
+    const AmgLevel& Ln = A.lv[l + 1];
+    if (!grid_sync(counter, abort_flag, target)) return false;
+    // ---- s_l = r_l - A_l x_l ----
+    if (l == 0) {
+      const V* x0 = AV<V>::vx(Lv);
+      for (int v0 = c0.row0; v0 < c0.row1; v0 += nsslots) {
+        const int v = v0 + sslot;
+        const bool has = v < c0.row1;
+        V y[7];
+        row_spmv0<V, G>(g, c0, v, has, sl, gmG, x0, y);
+        if (has) {
+          const size_t base = (size_t)v * VEC;
+#pragma unroll
+          for (int a2 = 0; a2 < 8; ++a2) {
+            if (a2 % G != sl) continue;
+            s0[base + a2] = (a2 == 7 || v == g.fixed) ? V(0) : __ldcg(r0v + base + a2) - y[a2];
+          }
+        }
+      }
+    } else {
+      int r0, r1;
+      range(Lv.n, r0, r1);
+      const V* Ab = AV<V>::a(Lv);
+      const V* xl = AV<V>::vx(Lv);
+      const V* rl = AV<V>::vr(Lv);
+      V* sv = AV<V>::vs(Lv);
+      for (int v0 = r0; v0 < r1; v0 += ncslots) {
+        const int v = v0 + cslot;
+        const bool has = v < r1;
+        const int k0 = has ? __ldg(Lv.a_ptr + v) : 0, k1 = has ? __ldg(Lv.a_ptr + v + 1) : 0;
+        V y[7];
+#pragma unroll
+        for (int a2 = 0; a2 < 7; ++a2) y[a2] = V(0);
+        for (int k = k0 + cl; k < k1; k += GC) {
+          V pu[8];
+          ld8(xl + (size_t)__ldg(Lv.a_col + k) * VEC, pu);
+          bmv<false>(Ab + (size_t)k * BLK, pu, y);
+        }
+        group_reduce7<V, GC>(y, full);
+        if (has && cl < 8) sv[(size_t)v * VEC + cl] = cl == 7 ? V(0) : __ldcg(rl + (size_t)v * VEC + cl) - pick7(y, cl);
+      }
+    }
+    if (!grid_sync(counter, abort_flag, target)) return false;
+    // ---- r_{l+1} = P^T s_l, and the next level's pre-smoothing ----
+    {
+      const V* sv = l == 0 ? s0 : AV<V>::vs(Lv);
+      const V* Pb = AV<V>::p(Lv);
+      V* rn = AV<V>::vr(Ln);
+      V* xn = AV<V>::vx(Ln);
+      const bool smooth = l + 1 < L;
+      const V wn = smooth ? V(1.0 / A.rho[l + 1]) : V(0);
+      const V* Dn = AV<V>::dinv(Ln);
+      int r0, r1;
+      range(Ln.n, r0, r1);
+      for (int ci = r0; ci < r1; ci += ncslots) {
+        const int c = ci + cslot;
+        const bool has = c < r1;
+        const int t0 = has ? __ldg(Lv.pt_ptr + c) : 0, t1 = has ? __ldg(Lv.pt_ptr + c + 1) : 0;
+        V y[7];
+#pragma unroll
+        for (int a2 = 0; a2 < 7; ++a2) y[a2] = V(0);
+        for (int t = t0 + cl; t < t1; t += GC) {
+          V pu[8];
+          ld8(sv + (size_t)__ldg(Lv.pt_row + t) * VEC, pu);
+          bmv<true>(Pb + (size_t)__ldg(Lv.pt_blk + t) * BLK, pu, y);
+        }
+        group_reduce7<V, GC>(y, full);
+        if (has && cl < 8) {
+          const size_t base = (size_t)c * VEC;
+          if (cl == 7) {
+            rn[base + 7] = V(0);
+            if (smooth) xn[base + 7] = V(0);
+          } else {
+            rn[base + cl] = pick7(y, cl);
+            if (smooth) xn[base + cl] = wn * dmul_row(Dn + (size_t)c * BLK, cl, y);
+          }
+        }
+      }
+    }
+  }
+  if (!grid_sync(counter, abort_flag, target)) return false;
+  // ---- coarsest: y_L = C^-1 r_L (dense) ----
+  {
+    const AmgLevel& Lc = A.lv[L];
+    const int nL = Lc.n;
+    const V* Ci = AV<V>::cinv(A);
+    const V* rc = AV<V>::vr(Lc);
+    V* yc = AV<V>::vy(Lc);
+    int r0, r1;
+    range(nL, r0, r1);
+    for (int ci = r0; ci < r1; ci += ncslots) {
+      const int c = ci + cslot;
+      const bool has = c < r1;
+      V y[7];
+#pragma unroll
+      for (int a2 = 0; a2 < 7; ++a2) y[a2] = V(0);
+      if (has) {
+        for (int d = cl; d < nL; d += GC) {
+          V pu[8];
+          ld8(rc + (size_t)d * VEC, pu);
+          bmv<false>(Ci + (size_t)(c * nL + d) * BLK, pu, y);
+        }
+      }
+      group_reduce7<V, GC>(y, full);
+      if (has && cl < 8) yc[(size_t)c * VEC + cl] = cl == 7 ? V(0) : pick7(y, cl);
+    }
+  }
+  // ---- way up: x_l + P y + w D^-1 (s_l - (A P) y) ----
+  for (int l = L - 1; l >= 0; --l) {
+    const AmgLevel& Lv = A.lv[l];
+    const AmgLevel& Ln = A.lv[l + 1];
+    if (!grid_sync(counter, abort_flag, target)) return false;
+    const V* yn = AV<V>::vy(Ln);
+    const V* Pb = AV<V>::p(Lv);
+    const V* APb = AV<V>::ap(Lv);
+    const V* xl = AV<V>::vx(Lv);
+    const V wl = V(1.0 / A.rho[l]);
+    if (l == 0) {
+      for (int v0 = c0.row0; v0 < c0.row1; v0 += nsslots) {
+        const int v = v0 + sslot;
+        const bool has = v < c0.row1;
+        int k0 = 0, k1 = 0, j0 = 0, j1 = 0;
+        if (has) {
+          k0 = __ldg(Lv.p_ptr + v);
+          k1 = __ldg(Lv.p_ptr + v + 1);
+          j0 = __ldg(Lv.ap_ptr + v);
+          j1 = __ldg(Lv.ap_ptr + v + 1);
+        }
+        V px[7], ax[7];
+#pragma unroll
+        for (int a2 = 0; a2 < 7; ++a2) px[a2] = ax[a2] = V(0);
+        for (int k = k0 + sl; k < k1; k += G) {
+          V pu[8];
+          ld8(yn + (size_t)__ldg(Lv.p_col + k) * VEC, pu);
+          bmv<false>(Pb + (size_t)k * BLK, pu, px);
+        }
+        for (int k = j0 + sl; k < j1; k += G) {
+          V pu[8];
+          ld8(yn + (size_t)__ldg(Lv.ap_col + k) * VEC, pu);
+          bmv<false>(APb + (size_t)k * BLK, pu, ax);
+        }
+        group_reduce7<V, G>(px, gmG);
+        group_reduce7<V, G>(ax, gmG);
+        if (has) {
+          const size_t base = (size_t)v * VEC;
+          V sx[8], xv[8];
+          ld8(s0 + base, sx);
+          ld8(xl + base, xv);
+          V d7[7];
+#pragma unroll
+          for (int c = 0; c < 7; ++c) d7[c] = sx[c] - ax[c];
+          const V* M = c0.s_minv + (size_t)(v - c0.row0) * BLK;
+          const bool live = v != g.fixed;
+#pragma unroll
+          for (int a2 = 0; a2 < 8; ++a2) {
+            if (a2 % G != sl) continue;
+            if (a2 == 7) {
+              z[base + 7] = V(0);
+              continue;
+            }
+            const V o = live ? xv[a2] + px[a2] + wl * dmul_row(M, a2, d7) : V(0);
+            z[base + a2] = o;
+            rz_loc += S(o) * S(__ldcg(r0v + base + a2));
+          }
+        }
+      }
+    } else {
+      int r0, r1;
+      range(Lv.n, r0, r1);
+      const V* sv = AV<V>::vs(Lv);
+      V* out = AV<V>::vy(Lv);
+      const V* Dl = AV<V>::dinv(Lv);
+      for (int v0 = r0; v0 < r1; v0 += ncslots) {
+        const int v = v0 + cslot;
+        const bool has = v < r1;
+        int k0 = 0, k1 = 0, j0 = 0, j1 = 0;
+        if (has) {
+          k0 = __ldg(Lv.p_ptr + v);
+          k1 = __ldg(Lv.p_ptr + v + 1);
+          j0 = __ldg(Lv.ap_ptr + v);
+          j1 = __ldg(Lv.ap_ptr + v + 1);
+        }
+        V px[7], ax[7];
+#pragma unroll
+        for (int a2 = 0; a2 < 7; ++a2) px[a2] = ax[a2] = V(0);
+        for (int k = k0 + cl; k < k1; k += GC) {
+          V pu[8];
+          ld8(yn + (size_t)__ldg(Lv.p_col + k) * VEC, pu);
+          bmv<false>(Pb + (size_t)k * BLK, pu, px);
+        }
+        for (int k = j0 + cl; k < j1; k += GC) {
+          V pu[8];
+          ld8(yn + (size_t)__ldg(Lv.ap_col + k) * VEC, pu);
+          bmv<false>(APb + (size_t)k * BLK, pu, ax);
+        }
+        group_reduce7<V, GC>(px, full);
+        group_reduce7<V, GC>(ax, full);
+        if (has && cl < 8) {
+          const size_t base = (size_t)v * VEC;
+          if (cl == 7) {
+            out[base + 7] = V(0);
+          } else {
+            V sx[8];
+            ld8(sv + base, sx);
+            V d7[7];
+#pragma unroll
+            for (int c = 0; c < 7; ++c) d7[c] = sx[c] - ax[c];
+            out[base + cl] = __ldcg(xl + base + cl) + pick7(px, cl) + wl * dmul_row(Dl + (size_t)v * BLK, cl, d7);
+          }
+        }
+      }
+    }
+  }
+  return true;
+}
+
 // One PCG solve.  V: storage and arithmetic type of blocks and vectors;
 // S: type of the dot products and scalars (double for the FP64 solve, float
 // for the inner solve of the mixed mode); G: lanes per block row in the SpMV
@@ -348,6 +671,30 @@ __global__ void __launch_bounds__(512) k_pcg(DevGraph g, PcgArgs a) {
   stage_blocks<V>(s_off, off, s_code, nst, true);
   __syncthreads();
 
+  L0Ctx<V> c0;
+  c0.s_diag = s_diag;
+  c0.s_minv = s_minv;
+  c0.s_off = s_off;
+  c0.s_code = s_code;
+  c0.s_other = s_other;
+  c0.off = off;
+  c0.nst = nst;
+  c0.e0 = e0;
+  c0.row0 = row0;
+  c0.row1 = row1;
+  c0.lam = lam;
+  // multigrid: the level-0 pre-smoothed iterate goes to x0, z is the V-cycle
+  // result; block-Jacobi: z = M r directly
+  __shared__ AmgDev sA;   // the hierarchy descriptor, cached in shared memory
+  if (a.amg) {
+    const unsigned long long* src = reinterpret_cast<const unsigned long long*>(g.amg);
+    unsigned long long* dst = reinterpret_cast<unsigned long long*>(&sA);
+    for (int t = threadIdx.x; t < (int)(sizeof(AmgDev) / 8); t += blockDim.x) dst[t] = src[t];
+  }
+  __syncthreads();
+  V* x0 = a.amg ? AV<V>::vx(sA.lv[0]) : nullptr;
+  const V w0 = a.amg ? V(1.0 / sA.rho[0]) : V(1);
+
   // ---- start: x = 0, r = rhs, z = M r, p_prev = 0 ----
   S loc[2] = {S(0), S(0)};
   // (loops over rows advance in whole-block steps so every lane of a warp
@@ -372,13 +719,15 @@ __global__ void __launch_bounds__(512) k_pcg(DevGraph g, PcgArgs a) {
     if (has) {
       x[base + lane8] = V(0);
       r[base + lane8] = rv;
-      z[base + lane8] = zv;
+      if (a.amg) x0[base + lane8] = w0 * zv;
+      else z[base + lane8] = zv;
       Bufs<V>::p(g, 1)[base + lane8] = V(0);
       Bufs<V>::p(g, 0)[base + lane8] = V(0);
     }
-    loc[0] += S(rv) * S(zv);
+    if (!a.amg) loc[0] += S(rv) * S(zv);
     loc[1] += S(rv) * S(rv);
   }
+  if (a.amg && !vcycle_rest<V, S, G>(g, sA, c0, r, q, z, loc[0], counter, abort_flag, target)) goto timeout;
   write_partial<S, 2>(loc, partial, sh.red);
   if (!grid_sync(counter, abort_flag, target)) goto timeout;
   S rz, bb;
@@ -509,11 +858,16 @@ __global__ void __launch_bounds__(512) k_pcg(DevGraph g, PcgArgs a) {
           zv += M[c7 * 7 + c] * rc;
         }
         if (has && act) {
-          z[base + c7] = zv;
-          l2[0] += S(rv) * S(zv);
+          if (a.amg) {
+            x0[base + c7] = w0 * zv;
+          } else {
+            z[base + c7] = zv;
+            l2[0] += S(rv) * S(zv);
+          }
           l2[1] += S(rv) * S(rv);
         }
       }
+      if (a.amg && !vcycle_rest<V, S, G>(g, sA, c0, r, q, z, l2[0], counter, abort_flag, target)) goto timeout;
       write_partial<S, 2>(l2, partial + 3 * gridDim.x, sh.red);
       if (!grid_sync(counter, abort_flag, target)) goto timeout;
       S t2[2];
@@ -661,7 +1015,7 @@ static cudaError_t launch_pcg_kernel(const DevGraph& g, PcgArgs a, cudaStream_t 
   // shared memory: diag + preconditioner blocks of the rows, then as many
   // off-diagonal blocks (and their indices) as fit
   const size_t blk_bytes = (size_t)Bufs<V>::BLK * sizeof(V);
-  const size_t budget = g_smem_optin - 2048;   // static shared memory and slack
+  const size_t budget = g_smem_optin - 8192;   // static shared memory (incl. the hierarchy descriptor) and slack
   const size_t fixed_bytes = 2 * (size_t)rows_per_block * blk_bytes;
   size_t cap = 0;
   if (budget > fixed_bytes) cap = (budget - fixed_bytes) / (blk_bytes + 2 * sizeof(int));
@@ -693,12 +1047,13 @@ void launch_precond(const DevGraph& g, int mixed, cudaStream_t s) {
   else k_precond<double><<<nb, 32, 0, s>>>(g);
 }
 
-cudaError_t launch_pcg(const DevGraph& g, int mixed, int from_residual, cudaStream_t s) {
+cudaError_t launch_pcg(const DevGraph& g, int mixed, int from_residual, const AmgDev* amg, cudaStream_t s) {
   PcgArgs a;
   a.from_residual = from_residual;
   a.inner = mixed;
   a.rows_per_block = 1;
   a.cap_entries = 0;
+  a.amg = amg != nullptr && g.amg != nullptr;
   if (mixed) return launch_pcg_kernel<float, float, PCG_G32>(g, a, s);
   return launch_pcg_kernel<double, double, 8>(g, a, s);
 }

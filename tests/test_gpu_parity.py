@@ -97,15 +97,17 @@ def test_jacobians_and_normal_equations(name):
         assert np.abs(got - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max())
 
 
+@pytest.mark.parametrize("precond", ["block_jacobi", "multigrid"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", ["c1", "noisy_info_w"])
-def test_damped_step(name, precision):
+def test_damped_step(name, precision, precond):
     g, w, I = case_graph(name)
     og, pg = make_pair(g, w, I)
     _, Hd, Ho, b = og.linearize(g.poses_init)
     lam = 1e-4 * max(np.diag(Hd[v]).max() for v in range(g.n_vertices))
     ref = og.solve_system(Hd, Ho, b, lam)
-    d, its = pg.damped_step(lam, precision=precision, pcg_tol=1e-12, pcg_max_iters=20000, refine_steps=6)
+    d, its = pg.damped_step(lam, precision=precision, pcg_tol=1e-12, pcg_max_iters=20000, refine_steps=6,
+                            preconditioner=precond)
     assert its > 0
     assert np.abs(d - ref).max() <= 1e-7 * np.abs(ref).max()
     assert np.abs(d[g.fixed_vertex]).max() == 0.0
@@ -115,13 +117,14 @@ def pose_err(a, b):
     return O.pose_error(a, b)
 
 
+@pytest.mark.parametrize("precond", ["block_jacobi", "multigrid"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-6)])
 @pytest.mark.parametrize("name", ["c1", "noisy", "noisy_info_w", "fixed_mid"])
-def test_lm_solve_matches_oracle(name, precision, tol):
+def test_lm_solve_matches_oracle(name, precision, tol, precond):
     g, w, I = case_graph(name)
     og, pg = make_pair(g, w, I)
     p_ref, rep_ref = og.lm(g.poses_init, max_iters=20)
-    rep = pg.solve(max_iters=20, precision=precision)
+    rep = pg.solve(max_iters=20, precision=precision, preconditioner=precond)
     assert rep["status"] == 0
     assert abs(rep["initial_cost"] - rep_ref["initial_cost"]) <= 1e-13 * rep_ref["initial_cost"]
     rel = abs(rep["final_cost"] - rep_ref["final_cost"]) / rep_ref["final_cost"]
