@@ -34,10 +34,10 @@ SCHED = {"graph": -1, "eager": 1}
 MAX_ITERS = 20
 METRIC = "Sim(3) PGO ms/solve & edges/s at rel cost <=1e-6: mixed vs plain FP64, one GB300"
 UNIT = "edges/s"
-# DRAM bytes (read + write) of one roofline launch from an ncu capture of
-# `bench.py --roofline-only` (profiles/k_pcg_float_c2_figure8_2k.md); None
-# whenever the kernel has changed since the counters were taken.
-TRAFFIC_PER_LAUNCH = 7.76e6
+# DRAM bytes (read + write) of one PCG iteration of the roofline kernel from an
+# ncu capture of `bench.py --roofline-only`; None whenever the kernel has
+# changed since the counters were taken.
+TRAFFIC_PER_ITERATION = None
 
 
 def parse():
@@ -49,8 +49,8 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--roofline-only", action="store_true",
-                    help="only the roofline leg: linearise once, then one 400-iteration FP32 PCG launch "
-                         "(the launch an ncu capture of the dominant kernel should see first)")
+                    help="only the roofline leg: linearise once, then the capped FP32 PCG re-solves "
+                         "(an ncu capture of k_pcg should take the second launch: 40 iterations)")
     ap.add_argument("--schedule", default="graph", choices=["graph", "eager"],
                     help="graph: one CUDA graph per solve (default); eager: host-driven launches "
                          "(for profilers that cannot see inside conditional graph nodes)")
@@ -130,13 +130,22 @@ def measured_peaks():
         return {"hbm_gbs": 6800.0}, "fallback"
 
 
-def pcg_bytes_per_iter(n_vertices, n_edges, value_bytes):
-    """Algorithmic DRAM bytes of one PCG iteration (see the design notes):
-    each off-diagonal 7x7 block read once (it serves both rows), the diagonal
-    and preconditioner blocks read once, and 11 vertex-vector passes of 7
-    values (z, p_prev read; q, p written; x, p, r, q read; x, r, z written)."""
-    blk = 49 * value_bytes
-    return n_edges * blk + 2 * n_vertices * blk + 11 * n_vertices * 7 * value_bytes
+def vcycle_pcg_bytes_per_iter(info, n_vertices, n_edges, value_bytes):
+    """Algorithmic bytes of one PCG iteration preconditioned by the V(1,1)
+    multigrid cycle (see the design notes).  Level 0: the stored operator
+    (one block per edge plus the diagonal blocks) read twice (the CG product
+    and the cycle's residual), D^-1 twice (pre- and post-smoothing), P twice
+    (restriction, prolongation), A P once, and 18 passes over 7-vectors (11 of
+    the CG, 7 of the cycle).  Each coarser smoothing level: its operator
+    once, P twice, A P once, D^-1 twice and 8 vector passes.  The coarsest
+    level: its dense inverse once and 2 vector passes."""
+    blk, vec = 49 * value_bytes, 7 * value_bytes
+    N, E, L = n_vertices, n_edges, len(info) - 1
+    b = (2 * (E + N) + 2 * N + 2 * info[0]["p_blocks"] + info[0]["ap_blocks"]) * blk + 18 * N * vec
+    for lv in info[1:L]:
+        b += (lv["a_blocks"] + 2 * lv["p_blocks"] + lv["ap_blocks"] + 2 * lv["nodes"]) * blk + 8 * lv["nodes"] * vec
+    b += info[L]["nodes"] ** 2 * blk + 2 * info[L]["nodes"] * vec
+    return b
 
 
 def oracle_reference(g, max_iters):
@@ -148,16 +157,19 @@ def oracle_reference(g, max_iters):
 
 
 def roofline_leg(pg, N, E, stream, flush, torch, reps=5):
-    """Average duration of the dominant kernel (the FP32 PCG of the mixed
-    solve): re-solve the damped system at the current linearisation with a
-    fixed iteration count (one k_pcg launch of `cap` iterations plus the tiny
-    preconditioner and residual kernels), timed with CUDA events on the
-    graph's stream; algorithmic bytes per launch = cap x per-iteration bytes."""
+    """Per-iteration duration of the dominant kernel, the FP32 PCG of the
+    mixed solve with its multigrid V-cycle: re-solve the damped system at the
+    current linearisation twice per repetition, with PCG caps of 10 and 40
+    iterations (tolerance 0, one refinement pass), each a single k_pcg launch
+    after the same preconditioner set-up; CUDA events on the graph's stream
+    time both, and the difference divided by the difference in iterations is
+    the time of one PCG iteration.  achieved = algorithmic bytes per iteration
+    / that time."""
     peaks, peak_kind = measured_peaks()
-    cap, lam = 400, 1e-3
-    kw = dict(precision="mixed", pcg_tol=1e-30, refine_tol=1e-30, refine_steps=1, pcg_max_iters=cap)
-    durs = []
-    for _ in range(reps):
+    lam = 1e-3
+    info = pg.multigrid_info()
+    def timed(cap):
+        kw = dict(precision="mixed", pcg_tol=1e-30, refine_tol=1e-30, refine_steps=1, pcg_max_iters=cap)
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -165,15 +177,23 @@ def roofline_leg(pg, N, E, stream, flush, torch, reps=5):
         pg.resolve_async(lam, **kw)
         e1.record(stream)
         e1.synchronize()
-        durs.append(e0.elapsed_time(e1))
-    launch_ms = statistics.median(durs)
-    bytes_launch = cap * pcg_bytes_per_iter(N, E, 4)
-    achieved = bytes_launch / (launch_ms * 1e-3) / 1e9
+        its = pg.resolve(lam, allow_cap=True, **kw)[1]
+        return e0.elapsed_time(e1), its
+    per_it = []
+    for _ in range(reps):
+        t_lo, i_lo = timed(10)
+        t_hi, i_hi = timed(40)
+        if i_hi > i_lo:
+            per_it.append((t_hi - t_lo) / (i_hi - i_lo))
+    it_ms = statistics.median(per_it) if per_it else float("nan")
+    bytes_it = vcycle_pcg_bytes_per_iter(info, N, E, 4)
+    achieved = bytes_it / (it_ms * 1e-3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-            "traffic": TRAFFIC_PER_LAUNCH, "kernel": "k_pcg<float,float,16> (mixed inner PCG)",
-            "peak_kind": peak_kind, "us_per_pcg_iteration": 1e3 * launch_ms / cap,
-            "algorithmic_bytes_per_launch": bytes_launch, "iterations_per_launch": cap}
+            "traffic": TRAFFIC_PER_ITERATION,
+            "kernel": "k_pcg<float,float,16> (mixed inner PCG with the V(1,1) multigrid cycle), per iteration",
+            "peak_kind": peak_kind, "us_per_pcg_iteration": 1e3 * it_ms,
+            "algorithmic_bytes_per_iteration": bytes_it, "multigrid_levels": [lv["nodes"] for lv in info]}
 
 
 def run_roofline_only(args):

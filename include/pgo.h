@@ -214,6 +214,18 @@ pgo_status pgo_graph_resolve(pgo_graph* g, const pgo_solve_options* opt, double 
  * graph's stream); use after a pgo_solve called with report == NULL. */
 pgo_status pgo_graph_report(pgo_graph* g, pgo_report* report);
 
+/* Shape of the graph's multigrid hierarchy (PGO_PRECOND_MULTIGRID; analysed
+ * at the first solve that uses it, or by this call).  *n_levels receives the
+ * number of levels including the coarsest (at most 13); for each level k the
+ * host arrays (each with room for 13 entries, nullable) receive its nodes,
+ * the 7x7 blocks of its operator (level 0: the graph's stored blocks, one
+ * per edge plus one per vertex), of its prolongation P and of A P (0 at the
+ * coarsest level).  No counterpart in the paper: it sizes the preconditioner
+ * for memory planning and for the roofline accounting of the PCG.
+ * PGO_ERR_STATE if the graph has no free vertex. */
+pgo_status pgo_graph_multigrid_info(pgo_graph* g, int32_t* n_levels, int32_t* nodes, int64_t* a_blocks,
+                                    int64_t* p_blocks, int64_t* ap_blocks);
+
 /* Run Levenberg-Marquardt from the current estimate (Sec. IV-F, Sec. VI) and
  * keep the result as the new current estimate.  opt NULL = defaults.
  * report (host, nullable) is filled after synchronising.  poses_out

@@ -246,6 +246,18 @@ class PoseGraph:
         o = L.default_options(**opts)
         L.check(self._lib.pgo_graph_resolve(self._h, ctypes.byref(o), float(lam), None, None, L.PGO_MEM_HOST))
 
+    def multigrid_info(self):
+        """Shape of the multigrid hierarchy: list of dicts (nodes, blocks of
+        the operator, of P and of A P) per level, the coarsest last."""
+        n = ctypes.c_int32()
+        nodes = np.zeros(13, np.int32)
+        a, p, ap = (np.zeros(13, np.int64) for _ in range(3))
+        L.check(self._lib.pgo_graph_multigrid_info(self._h, ctypes.byref(n), ctypes.c_void_p(nodes.ctypes.data),
+                                                   ctypes.c_void_p(a.ctypes.data), ctypes.c_void_p(p.ctypes.data),
+                                                   ctypes.c_void_p(ap.ctypes.data)))
+        return [dict(nodes=int(nodes[k]), a_blocks=int(a[k]), p_blocks=int(p[k]), ap_blocks=int(ap[k]))
+                for k in range(n.value)]
+
     def solve_report(self):
         """Report of the last solve (synchronises the graph's stream)."""
         rep = L.Report()

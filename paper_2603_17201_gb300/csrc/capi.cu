@@ -929,6 +929,24 @@ static void fill_report(pgo_graph* G, pgo_report* report) {
   report->ms_total = ms;
 }
 
+pgo_status pgo_graph_multigrid_info(pgo_graph* G, int32_t* n_levels, int32_t* nodes, int64_t* a_blocks,
+                                    int64_t* p_blocks, int64_t* ap_blocks) {
+  if (!G || !n_levels) return fail(PGO_ERR_INVALID_ARG, "graph or n_levels is NULL");
+  pgo_status st = ensure_amg(G, PGO_PRECOND_MULTIGRID);
+  if (st != PGO_OK) return st;
+  if (!G->amg) return fail(PGO_ERR_STATE, "the graph has no free vertex: no multigrid hierarchy");
+  const AmgDev* D = amg_host_desc(G->amg);
+  *n_levels = D->L + 1;
+  for (int l = 0; l <= D->L; ++l) {
+    const AmgLevel& a = D->lv[l];
+    if (nodes) nodes[l] = a.n;
+    if (a_blocks) a_blocks[l] = l == 0 ? (int64_t)G->E + G->N : a.nnz_a;
+    if (p_blocks) p_blocks[l] = l < D->L ? a.nnz_p : 0;
+    if (ap_blocks) ap_blocks[l] = l < D->L ? a.nnz_ap : 0;
+  }
+  return PGO_OK;
+}
+
 pgo_status pgo_graph_report(pgo_graph* G, pgo_report* report) {
   if (!G || !report) return fail(PGO_ERR_INVALID_ARG, "graph or report is NULL");
   if (!G->solved) return fail(PGO_ERR_STATE, "no solve has run on this graph");
