@@ -61,18 +61,19 @@ struct HostLevel {
 // k >= 0 is incidence code k (stored block k >> 1, transposed if k & 1).
 // Levels >= 1: the index of the stored block.
 struct NbrView {
-  int level, fixed;
+  int level;
+  const std::vector<char>* fixed;              // level 0: gauge vertices
   const int *inc_ptr, *inc_code, *inc_other;   // level 0
   const std::vector<int>* a_ptr;               // levels >= 1
   const std::vector<int>* a_col;
   template <class F>
   void each(int u, F f) const {
     if (level == 0) {
-      if (u == fixed) return;
+      if ((*fixed)[u]) return;
       f(-(u + 1), u);
       for (int k = inc_ptr[u]; k < inc_ptr[u + 1]; ++k) {
         const int w = inc_other[k];
-        if (w != fixed) f(inc_code[k], w);
+        if (!(*fixed)[w]) f(inc_code[k], w);
       }
     } else {
       for (int k = (*a_ptr)[u]; k < (*a_ptr)[u + 1]; ++k) f(k, (*a_col)[k]);
@@ -270,9 +271,12 @@ struct Uploader {
 
 // Lays out (base == nullptr: only measures) every device array of the
 // hierarchy and records the host-to-device copies.
-void layout(Uploader& U, std::vector<HostLevel>& H, int L, int N, AmgDev& D) {
+void layout(Uploader& U, std::vector<HostLevel>& H, int L, int N, const std::vector<int>& seg_off, int nseg,
+            AmgDev& D) {
   D.L = L;
   D.nL = H[L].n;
+  D.nseg = nseg;
+  D.seg_off = U.put(seg_off);
   for (int l = 0; l <= L; ++l) {
     HostLevel& h = H[l];
     AmgLevel& a = D.lv[l];
@@ -333,74 +337,108 @@ void layout(Uploader& U, std::vector<HostLevel>& H, int L, int N, AmgDev& D) {
       a.r3 = U.put(h.r3);
     }
   }
-  const size_t nl2 = (size_t)D.nL * D.nL;
+  // one dense coarsest inverse per segment (segment s at s * AMG_CMAX^2 blocks)
+  const size_t nl2 = nseg == 1 ? (size_t)D.nL * D.nL : (size_t)nseg * AMG_CMAX * AMG_CMAX;
   D.cinv64 = U.take<double>(std::max(nl2, (size_t)1) * BLK64);
   D.cinv32 = U.take<float>(std::max(nl2, (size_t)1) * BLK32);
-  D.rho = U.take<double>(AMG_MAXL + 1);
+  D.rho = U.take<double>((size_t)nseg * (AMG_MAXL + 1));
   for (int k = 0; k < 2; ++k) {
     D.pw64[k] = U.take<double>((size_t)N * VEC);
     D.pw32[k] = U.take<float>((size_t)N * VEC);
   }
-  D.flag = U.take<int>(1);
-  D.warm = U.take<int>(2);
+  D.flag = U.take<int>(nseg);
+  D.warm = U.take<int>(2 * (size_t)nseg);
 }
 
 }  // namespace
 
-AmgHost* amg_build(int N, int fixed, const int* inc_ptr, const int* inc_code, const int* inc_other,
-                   cudaStream_t s, const char** err) {
+AmgHost* amg_build(int N, int nseg, const int* seg_v0, const int* seg_nv, const int* seg_fixed, const int* inc_ptr,
+                   const int* inc_code, const int* inc_other, cudaStream_t s, const char** err) {
   *err = nullptr;
-  const int K = N - 1;   // free vertices
+  // Segments are independent graphs on consecutive vertex ranges (one for a
+  // single graph; one per graph of a batch): aggregates never cross a
+  // segment, so every level is block-diagonal over the segments.  All
+  // segments coarsen the same number of times, until none has more than
+  // AMG_CMAX nodes (a small segment shrinks to one node and stays there).
+  std::vector<char> fixed(N, 0);
+  int K = 0;
+  for (int g = 0; g < nseg; ++g) {
+    fixed[seg_fixed[g]] = 1;
+    K += seg_nv[g] - 1;
+  }
   if (K < 1) {
     *err = "multigrid needs at least one free vertex";
     return nullptr;
   }
   std::vector<HostLevel> H(1);
-  HostLevel& L0 = H[0];
-  L0.n = N;
-  L0.agg.assign(N, -1);
-  L0.ref.resize(N);
+  std::vector<int> seg_off;                  // (levels) x (nseg + 1) node offsets
+  std::vector<int> cnt(nseg), cnt_next(nseg);
   {
-    int fo = 0;
-    for (int v = 0; v < N; ++v) {
-      L0.ref[v] = v;
-      if (v == fixed) continue;
-      L0.agg[v] = fo / AMG_M;
-      ++fo;
+    HostLevel& L0 = H[0];
+    L0.n = N;
+    L0.agg.assign(N, -1);
+    L0.ref.resize(N);
+    int base = 0;
+    for (int g = 0; g < nseg; ++g) {
+      int fo = 0;
+      for (int v = seg_v0[g]; v < seg_v0[g] + seg_nv[g]; ++v) {
+        L0.ref[v] = v;
+        if (fixed[v]) continue;
+        L0.agg[v] = base + fo / AMG_M;
+        ++fo;
+      }
+      cnt_next[g] = (fo + AMG_M - 1) / AMG_M;
+      base += cnt_next[g];
     }
+    L0.n_next = base;
+    for (int g = 0; g <= nseg; ++g) seg_off.push_back(g < nseg ? seg_v0[g] : N);
   }
-  L0.n_next = (K + AMG_M - 1) / AMG_M;
   int L = 0;
   for (;;) {
-    HostLevel& cur = H[L];
     if (L + 1 > AMG_MAXL) {
       *err = "graph too large for the multigrid hierarchy";
       return nullptr;
     }
     H.emplace_back();
-    HostLevel& cur2 = H[L];      // (emplace_back may move the vector)
+    HostLevel& cur = H[L];       // (emplace_back may move the vector)
     HostLevel& nxt = H[L + 1];
-    (void)cur;
-    NbrView nb{L, fixed, inc_ptr, inc_code, inc_other, &cur2.a_ptr, &cur2.a_col};
-    build_level(cur2, nb, nxt);
-    nxt.n = cur2.n_next;
+    NbrView nb{L, &fixed, inc_ptr, inc_code, inc_other, &cur.a_ptr, &cur.a_col};
+    build_level(cur, nb, nxt);
+    nxt.n = cur.n_next;
     // references: the first member of each aggregate
     nxt.ref.assign(nxt.n, -1);
-    for (int u = 0; u < cur2.n; ++u) {
-      const int c = cur2.agg[u];
-      if (c >= 0 && nxt.ref[c] < 0) nxt.ref[c] = cur2.ref[u];
+    for (int u = 0; u < cur.n; ++u) {
+      const int c = cur.agg[u];
+      if (c >= 0 && nxt.ref[c] < 0) nxt.ref[c] = cur.ref[u];
     }
-    cur2.refc.assign(cur2.n, 0);
-    for (int u = 0; u < cur2.n; ++u) cur2.refc[u] = cur2.agg[u] >= 0 ? nxt.ref[cur2.agg[u]] : 0;
+    cur.refc.assign(cur.n, 0);
+    for (int u = 0; u < cur.n; ++u) cur.refc[u] = cur.agg[u] >= 0 ? nxt.ref[cur.agg[u]] : 0;
     ++L;
-    if (nxt.n <= AMG_CMAX) break;
+    cnt = cnt_next;
+    {
+      int o = 0;
+      for (int g = 0; g < nseg; ++g) {
+        seg_off.push_back(o);
+        o += cnt[g];
+      }
+      seg_off.push_back(o);
+    }
+    int most = 0;
+    for (int g = 0; g < nseg; ++g) most = std::max(most, cnt[g]);
+    if (most <= AMG_CMAX) break;
     nxt.agg.resize(nxt.n);
-    for (int c = 0; c < nxt.n; ++c) nxt.agg[c] = c / AMG_M;
-    nxt.n_next = (nxt.n + AMG_M - 1) / AMG_M;
+    int base = 0, o = 0;
+    for (int g = 0; g < nseg; ++g) {
+      for (int c = 0; c < cnt[g]; ++c) nxt.agg[o + c] = base + c / AMG_M;
+      o += cnt[g];
+      cnt_next[g] = (cnt[g] + AMG_M - 1) / AMG_M;
+      base += cnt_next[g];
+    }
+    nxt.n_next = base;
   }
   AmgHost* A = new AmgHost();
   Uploader meas;
-  layout(meas, H, L, N, A->h);
+  layout(meas, H, L, N, seg_off, nseg, A->h);
   A->bytes = meas.used + 256;
   if (cudaMalloc(&A->mem, A->bytes) != cudaSuccess ||
       cudaMalloc(&A->d, sizeof(AmgDev)) != cudaSuccess) {
@@ -411,7 +449,7 @@ AmgHost* amg_build(int N, int fixed, const int* inc_ptr, const int* inc_code, co
   }
   Uploader up;
   up.base = A->mem;
-  layout(up, H, L, N, A->h);
+  layout(up, H, L, N, seg_off, nseg, A->h);
   bool ok = cudaMemsetAsync(A->mem, 0, up.used, s) == cudaSuccess;
   for (auto& c : up.copies)
     ok = ok && cudaMemcpyAsync(c.first, c.second.first, c.second.second, cudaMemcpyHostToDevice, s) == cudaSuccess;
@@ -441,192 +479,6 @@ size_t amg_bytes(const AmgHost* h) { return h ? h->bytes : 0; }
 
 // A block of level l for a recipe reference: entry (i, k) is
 // (tr ? p[k * 7 + i] : p[i * 7 + k]) + (i == k ? add : 0).
-// sum over the recipe entries e of (A_e X_e)[i][j].  A_e: level-0 block
-// reference (L0: diagonal + lambda, or an off-diagonal block, maybe
-// transposed; blocks from an earlier launch) or a block of this level's
-// operator (written by this launch); X_e = X + rec[e].y * BLK (written by
-// this launch).  Entries go four at a time so that their loads overlap.
-template <class V, bool L0>
-__device__ __forceinline__ V recipe_ax(const DevGraph& g, const V* Alev, V lam, const int2* rec, int e0, int e1,
-                                       const V* X, int i, int j) {
-  constexpr int BLK = AV<V>::BLK;
-  V acc = V(0);
-  auto arow = [&](int a, V (&r)[7]) {
-    if (L0) {
-      const V* p;
-      bool tr = false;
-      V add = V(0);
-      if (a < 0) {
-        p = AV<V>::diag(g) + (size_t)(-a - 1) * BLK;
-        add = lam;
-      } else {
-        p = AV<V>::off(g) + (size_t)(a >> 1) * BLK;
-        tr = (a & 1) != 0;
-      }
-#pragma unroll
-      for (int k = 0; k < 7; ++k) r[k] = __ldg(p + (tr ? k * 7 + i : i * 7 + k)) + (k == i ? add : V(0));
-    } else {
-      const V* p = Alev + (size_t)a * BLK + i * 7;
-#pragma unroll
-      for (int k = 0; k < 7; ++k) r[k] = __ldcg(p + k);
-    }
-  };
-  int e = e0;
-  for (; e + 4 <= e1; e += 4) {
-    int2 t[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) t[q] = __ldg(rec + e + q);
-    V ar[4][7], xc[4][7];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      arow(t[q].x, ar[q]);
-      const V* xp = X + (size_t)t[q].y * BLK + j;
-#pragma unroll
-      for (int k = 0; k < 7; ++k) xc[q][k] = __ldcg(xp + k * 7);
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int k = 0; k < 7; ++k) acc += ar[q][k] * xc[q][k];
-  }
-  for (; e < e1; ++e) {
-    const int2 t = __ldg(rec + e);
-    V ar[7];
-    arow(t.x, ar);
-    const V* xp = X + (size_t)t.y * BLK + j;
-#pragma unroll
-    for (int k = 0; k < 7; ++k) acc += ar[k] * __ldcg(xp + k * 7);
-  }
-  return acc;
-}
-
-// sum over the entries e of (P_e^T Q_e)[i][j], both written by this launch.
-template <class V>
-__device__ __forceinline__ V recipe_ptq(const int2* rec, int e0, int e1, const V* P, const V* Q, int i, int j) {
-  constexpr int BLK = AV<V>::BLK;
-  V acc = V(0);
-  int e = e0;
-  for (; e + 4 <= e1; e += 4) {
-    int2 t[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) t[q] = __ldg(rec + e + q);
-    V pc[4][7], qc[4][7];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const V* pp = P + (size_t)t[q].x * BLK + i;
-      const V* qp = Q + (size_t)t[q].y * BLK + j;
-#pragma unroll
-      for (int k = 0; k < 7; ++k) {
-        pc[q][k] = __ldcg(pp + k * 7);
-        qc[q][k] = __ldcg(qp + k * 7);
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q)
-#pragma unroll
-      for (int k = 0; k < 7; ++k) acc += pc[q][k] * qc[q][k];
-  }
-  for (; e < e1; ++e) {
-    const int2 t = __ldg(rec + e);
-    const V* pp = P + (size_t)t.x * BLK + i;
-    const V* qp = Q + (size_t)t.y * BLK + j;
-#pragma unroll
-    for (int k = 0; k < 7; ++k) acc += __ldcg(pp + k * 7) * __ldcg(qp + k * 7);
-  }
-  return acc;
-}
-
-// Adj(S) in [omega, upsilon, sigma] order: [[R, 0, 0], [t^ R, s R, -t], [0, 0, 1]].
-__device__ __forceinline__ void adj7(const Sim3T<double>& S, double (&A)[7][7]) {
-  double R[9];
-  qmat(S.q, R);
-  const double* t = S.t;
-#pragma unroll
-  for (int i = 0; i < 7; ++i)
-#pragma unroll
-    for (int j = 0; j < 7; ++j) A[i][j] = 0.0;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    A[0][c] = R[c];
-    A[1][c] = R[3 + c];
-    A[2][c] = R[6 + c];
-    A[3][c] = -t[2] * R[3 + c] + t[1] * R[6 + c];
-    A[4][c] = t[2] * R[0 + c] - t[0] * R[6 + c];
-    A[5][c] = -t[1] * R[0 + c] + t[0] * R[3 + c];
-    A[3][3 + c] = S.s * R[c];
-    A[4][3 + c] = S.s * R[3 + c];
-    A[5][3 + c] = S.s * R[6 + c];
-  }
-  A[3][6] = -t[0];
-  A[4][6] = -t[1];
-  A[5][6] = -t[2];
-  A[6][6] = 1.0;
-}
-
-// Inverse of a symmetric positive definite 7x7 block (Cholesky, in double);
-// returns false (and writes the inverse of the diagonal) if a pivot is not
-// positive.
-template <class V>
-__device__ __forceinline__ bool inv7_spd(const V* B, V* out) {
-  double A[7][7];
-#pragma unroll
-  for (int a = 0; a < 7; ++a)
-#pragma unroll
-    for (int c = 0; c < 7; ++c) A[a][c] = 0.5 * ((double)B[a * 7 + c] + (double)B[c * 7 + a]);
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < 7; ++j) {
-    double d = A[j][j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
-    ok = ok && (d > 0.0);
-    d = sqrt(fmax(d, 1e-300));
-    A[j][j] = d;
-#pragma unroll
-    for (int i = j + 1; i < 7; ++i) {
-      double s = A[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
-      A[i][j] = s / d;
-    }
-  }
-  if (!ok) {
-#pragma unroll
-    for (int a = 0; a < 7; ++a)
-#pragma unroll
-      for (int c = 0; c < 7; ++c) {
-        const double dd = (double)B[a * 8];
-        out[a * 7 + c] = (a == c && dd > 0.0) ? V(1.0 / dd) : V(0);
-      }
-    return false;
-  }
-  // L^-1 (lower), then inv = L^-T L^-1
-  double Li[7][7];
-#pragma unroll
-  for (int c = 0; c < 7; ++c) {
-#pragma unroll
-    for (int i = 0; i < 7; ++i) {
-      if (i < c) { Li[i][c] = 0.0; continue; }
-      double s = (i == c) ? 1.0 : 0.0;
-#pragma unroll
-      for (int k = 0; k < i; ++k)
-        if (k >= c) s -= A[i][k] * Li[k][c];
-      Li[i][c] = s / A[i][i];
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < 7; ++a)
-#pragma unroll
-    for (int c = 0; c < 7; ++c) {
-      double s = 0.0;
-#pragma unroll
-      for (int k = 0; k < 7; ++k)
-        if (k >= a && k >= c) s += Li[k][a] * Li[k][c];
-      out[a * 7 + c] = V(s);
-    }
-  return true;
-}
-
 // Per-block partial (one double per block) and its fixed-order grid sum,
 // double-buffered by `set` so that a fast block's next write cannot race a
 // slow block's read.

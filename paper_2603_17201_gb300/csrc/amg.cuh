@@ -1,7 +1,7 @@
 // Precision accessors of the multigrid hierarchy (shared by the setup and
 // the V-cycle inside the PCG kernel).
 #pragma once
-#include "internal.cuh"
+#include "phases.cuh"
 
 namespace pgo {
 
@@ -45,5 +45,195 @@ struct AV<float> {
   static __device__ __forceinline__ float* vy(const AmgLevel& L) { return L.vy32; }
   static __device__ __forceinline__ float* pv(const AmgLevel& L) { return L.pv32; }
 };
+
+// sum over the recipe entries e of (A_e X_e)[i][j].  A_e: level-0 block
+// reference (L0: diagonal + lambda, or an off-diagonal block, maybe
+// transposed) or a block of this level's operator; X_e = X + rec[e].y * BLK.
+// NC: the level-0 blocks come from an earlier launch and may be read through
+// the non-coherent cache; everything else is read from L2.  Entries go four
+// at a time so that their loads overlap.
+template <class V, bool L0, bool NC = true>
+__device__ __forceinline__ V recipe_ax(const DevGraph& g, const V* Alev, V lam, const int2* rec, int e0, int e1,
+                                       const V* X, int i, int j) {
+  constexpr int BLK = AV<V>::BLK;
+  V acc = V(0);
+  auto arow = [&](int a, V (&r)[7]) {
+    if (L0) {
+      const V* p;
+      bool tr = false;
+      V add = V(0);
+      if (a < 0) {
+        p = AV<V>::diag(g) + (size_t)(-a - 1) * BLK;
+        add = lam;
+      } else {
+        p = AV<V>::off(g) + (size_t)(a >> 1) * BLK;
+        tr = (a & 1) != 0;
+      }
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const V* q = p + (tr ? k * 7 + i : i * 7 + k);
+        r[k] = (NC ? __ldg(q) : __ldcg(q)) + (k == i ? add : V(0));
+      }
+    } else {
+      const V* p = Alev + (size_t)a * BLK + i * 7;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) r[k] = __ldcg(p + k);
+    }
+  };
+  int e = e0;
+  for (; e + 4 <= e1; e += 4) {
+    int2 t[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[q] = __ldg(rec + e + q);
+    V ar[4][7], xc[4][7];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      arow(t[q].x, ar[q]);
+      const V* xp = X + (size_t)t[q].y * BLK + j;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) xc[q][k] = __ldcg(xp + k * 7);
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < 7; ++k) acc += ar[q][k] * xc[q][k];
+  }
+  for (; e < e1; ++e) {
+    const int2 t = __ldg(rec + e);
+    V ar[7];
+    arow(t.x, ar);
+    const V* xp = X + (size_t)t.y * BLK + j;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) acc += ar[k] * __ldcg(xp + k * 7);
+  }
+  return acc;
+}
+
+// sum over the entries e of (P_e^T Q_e)[i][j], both written by this launch.
+template <class V>
+__device__ __forceinline__ V recipe_ptq(const int2* rec, int e0, int e1, const V* P, const V* Q, int i, int j) {
+  constexpr int BLK = AV<V>::BLK;
+  V acc = V(0);
+  int e = e0;
+  for (; e + 4 <= e1; e += 4) {
+    int2 t[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) t[q] = __ldg(rec + e + q);
+    V pc[4][7], qc[4][7];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const V* pp = P + (size_t)t[q].x * BLK + i;
+      const V* qp = Q + (size_t)t[q].y * BLK + j;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        pc[q][k] = __ldcg(pp + k * 7);
+        qc[q][k] = __ldcg(qp + k * 7);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+#pragma unroll
+      for (int k = 0; k < 7; ++k) acc += pc[q][k] * qc[q][k];
+  }
+  for (; e < e1; ++e) {
+    const int2 t = __ldg(rec + e);
+    const V* pp = P + (size_t)t.x * BLK + i;
+    const V* qp = Q + (size_t)t.y * BLK + j;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) acc += __ldcg(pp + k * 7) * __ldcg(qp + k * 7);
+  }
+  return acc;
+}
+
+// Adj(S) in [omega, upsilon, sigma] order: [[R, 0, 0], [t^ R, s R, -t], [0, 0, 1]].
+__device__ __forceinline__ void adj7(const Sim3T<double>& S, double (&A)[7][7]) {
+  double R[9];
+  qmat(S.q, R);
+  const double* t = S.t;
+#pragma unroll
+  for (int i = 0; i < 7; ++i)
+#pragma unroll
+    for (int j = 0; j < 7; ++j) A[i][j] = 0.0;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    A[0][c] = R[c];
+    A[1][c] = R[3 + c];
+    A[2][c] = R[6 + c];
+    A[3][c] = -t[2] * R[3 + c] + t[1] * R[6 + c];
+    A[4][c] = t[2] * R[0 + c] - t[0] * R[6 + c];
+    A[5][c] = -t[1] * R[0 + c] + t[0] * R[3 + c];
+    A[3][3 + c] = S.s * R[c];
+    A[4][3 + c] = S.s * R[3 + c];
+    A[5][3 + c] = S.s * R[6 + c];
+  }
+  A[3][6] = -t[0];
+  A[4][6] = -t[1];
+  A[5][6] = -t[2];
+  A[6][6] = 1.0;
+}
+
+// Inverse of a symmetric positive definite 7x7 block (Cholesky, in double);
+// returns false (and writes the inverse of the diagonal) if a pivot is not
+// positive.
+template <class V>
+__device__ __forceinline__ bool inv7_spd(const V* B, V* out) {
+  double A[7][7];
+#pragma unroll
+  for (int a = 0; a < 7; ++a)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) A[a][c] = 0.5 * ((double)B[a * 7 + c] + (double)B[c * 7 + a]);
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < 7; ++j) {
+    double d = A[j][j];
+#pragma unroll
+    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
+    ok = ok && (d > 0.0);
+    d = sqrt(fmax(d, 1e-300));
+    A[j][j] = d;
+#pragma unroll
+    for (int i = j + 1; i < 7; ++i) {
+      double s = A[i][j];
+#pragma unroll
+      for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
+      A[i][j] = s / d;
+    }
+  }
+  if (!ok) {
+#pragma unroll
+    for (int a = 0; a < 7; ++a)
+#pragma unroll
+      for (int c = 0; c < 7; ++c) {
+        const double dd = (double)B[a * 8];
+        out[a * 7 + c] = (a == c && dd > 0.0) ? V(1.0 / dd) : V(0);
+      }
+    return false;
+  }
+  // L^-1 (lower), then inv = L^-T L^-1
+  double Li[7][7];
+#pragma unroll
+  for (int c = 0; c < 7; ++c) {
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+      if (i < c) { Li[i][c] = 0.0; continue; }
+      double s = (i == c) ? 1.0 : 0.0;
+#pragma unroll
+      for (int k = 0; k < i; ++k)
+        if (k >= c) s -= A[i][k] * Li[k][c];
+      Li[i][c] = s / A[i][i];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 7; ++a)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      double s = 0.0;
+#pragma unroll
+      for (int k = 0; k < 7; ++k)
+        if (k >= a && k >= c) s += Li[k][a] * Li[k][c];
+      out[a * 7 + c] = V(s);
+    }
+  return true;
+}
 
 }  // namespace pgo

@@ -13,6 +13,7 @@
 //
 // Schedules (picked by the autotuner in the host runtime): G lanes per block
 // row in the SpMV (4, 8 or 16) and NT threads per block (256 or 512).
+#include "amg_cta.cuh"
 #include "phases.cuh"
 
 namespace pgo {
@@ -94,7 +95,7 @@ __device__ __forceinline__ void bmv7(const V* B, const V (&p)[7], V (&y)[7]) {
 // |r| / |rhs|.  Returns the iteration count.
 template <class V, int G>
 __device__ int cta_pcg(const DevGraph& g, int v0, int v1, int fixed, double lam, int from_res, double tol,
-                       int maxit, double* sh) {
+                       int maxit, double* sh, const AmgDev* A, int sg) {
   constexpr int BLK = BBufs<V>::BLK;
   const V* off = BBufs<V>::off(g);
   const V* diag = BBufs<V>::diag(g);
@@ -107,6 +108,34 @@ __device__ int cta_pcg(const DevGraph& g, int v0, int v1, int fixed, double lam,
   const V vl = V(lam);
   // start: x = 0, r = rhs, z = M r, p = z
   double d2[2] = {0.0, 0.0};
+  if (A) {
+    // multigrid: z = one V-cycle of the graph's segment (q is its scratch)
+    for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+      const size_t b = (size_t)v * VEC;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        x[b + k] = V(0);
+        r[b + k] = (v == fixed) ? V(0) : V(from_res ? g.res64[b + k] : -g.b[b + k]);
+      }
+      x[b + 7] = V(0);
+      r[b + 7] = V(0);
+    }
+    __syncthreads();
+    cta_vcycle<V, G>(g, *A, sg, fixed, vl, r, q, z);
+    for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+      const size_t b = (size_t)v * VEC;
+      V lrz = V(0), lrr = V(0);
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        const V zv = z[b + k], rv = r[b + k];
+        p[b + k] = zv;
+        lrz += rv * zv;
+        lrr += rv * rv;
+      }
+      d2[0] += (double)lrz;
+      d2[1] += (double)lrr;
+    }
+  } else
   for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
     const size_t b = (size_t)v * VEC;
     V rv[7], zv[7];
@@ -138,6 +167,8 @@ __device__ int cta_pcg(const DevGraph& g, int v0, int v1, int fixed, double lam,
   const double bb = d2[1];
   if (!(bb > 0.0) || !(rz > 0.0)) return 0;
   const double tol2 = tol * tol;
+  double rr_best = bb;   // multigrid stall test (see k_pcg)
+  int stall = 0;
   const int sl = threadIdx.x & (G - 1);
   const int rows_step = blockDim.x / G;
   const unsigned gm = G >= 32 ? 0xffffffffu : (((1u << G) - 1u) << (threadIdx.x & (32 - G)));
@@ -195,6 +226,30 @@ __device__ int cta_pcg(const DevGraph& g, int v0, int v1, int fixed, double lam,
     if (!(pq[0] > 0.0)) break;
     const V alpha = V(rz / pq[0]);
     double t2[2] = {0.0, 0.0};
+    if (A) {
+      for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        if (v == fixed) continue;
+        const size_t b = (size_t)v * VEC;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+          x[b + k] += alpha * p[b + k];
+          r[b + k] = r[b + k] - alpha * q[b + k];
+        }
+      }
+      __syncthreads();
+      cta_vcycle<V, G>(g, *A, sg, fixed, vl, r, q, z);
+      for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        const size_t b = (size_t)v * VEC;
+        V lrz = V(0), lrr = V(0);
+#pragma unroll
+        for (int k = 0; k < 7; ++k) {
+          lrz += r[b + k] * z[b + k];
+          lrr += r[b + k] * r[b + k];
+        }
+        t2[0] += (double)lrz;
+        t2[1] += (double)lrr;
+      }
+    } else
     for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
       if (v == fixed) continue;
       const size_t b = (size_t)v * VEC;
@@ -224,6 +279,14 @@ __device__ int cta_pcg(const DevGraph& g, int v0, int v1, int fixed, double lam,
     const double beta = (rz > 0.0) ? t2[0] / rz : 0.0;
     rz = t2[0];
     if (!(t2[1] > tol2 * bb) || !(rz > 0.0) || !isfinite(t2[1])) break;
+    if (A) {
+      if (t2[1] < 0.81 * rr_best) {
+        rr_best = t2[1];
+        stall = 0;
+      } else if (++stall >= 20) {
+        break;
+      }
+    }
     const V vb2 = V(beta);
     for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
       const size_t b = (size_t)v * VEC;
@@ -286,7 +349,8 @@ __device__ double cta_cost(const DevGraph& g, int buf, int e0, int e1, double* s
 
 // The complete LM solve of one graph by one thread block.
 template <int MIXED, int G>
-__device__ void solve_graph(const DevGraph& g, const BatchArgs& a, int gi, double* sh) {
+__device__ void solve_graph(const DevGraph& g, const BatchArgs& a, int gi, double* sh, double* dense) {
+  const AmgDev* A = a.amg ? g.amg : nullptr;
   const DevOptions* o = g.opt;
   const int v0 = a.v0[gi], v1 = v0 + a.nv[gi];
   const int e0 = a.e0[gi], e1 = e0 + a.ne[gi];
@@ -328,15 +392,19 @@ __device__ void solve_graph(const DevGraph& g, const BatchArgs& a, int gi, doubl
       else precond_vertex<double>(g, v, fixed, lambda, g.minv64 + (size_t)v * BLK64);
     }
     __syncthreads();
+    if (A) {
+      if (MIXED) cta_amg_setup<float>(g, *A, gi, fixed, lambda, cur, sh, dense);
+      else cta_amg_setup<double>(g, *A, gi, fixed, lambda, cur, sh, dense);
+    }
     const double* dx;
     if (!MIXED) {
-      pcg_total += cta_pcg<double, G>(g, v0, v1, fixed, lambda, 0, o->pcg_tol, o->pcg_max_iters, sh);
+      pcg_total += cta_pcg<double, G>(g, v0, v1, fixed, lambda, 0, o->pcg_tol, o->pcg_max_iters, sh, A, gi);
       dx = g.x64;
     } else {
       for (int pass = 0; pass < o->refine_steps; ++pass) {
         const double rr = cta_refine_residual(g, v0, v1, fixed, lambda, pass == 0, sh);
         if (pass > 0 && !(rr > o->pcg_tol * o->pcg_tol * bnorm2)) break;
-        pcg_total += cta_pcg<float, G>(g, v0, v1, fixed, lambda, 1, o->refine_tol, o->pcg_max_iters, sh);
+        pcg_total += cta_pcg<float, G>(g, v0, v1, fixed, lambda, 1, o->refine_tol, o->pcg_max_iters, sh, A, gi);
         for (int t = v0 * VEC + threadIdx.x; t < v1 * VEC; t += blockDim.x) g.dx64[t] += (double)g.x32[t];
         __syncthreads();
       }
@@ -400,13 +468,14 @@ template <int MIXED, int G, int NT>
 __global__ void __launch_bounds__(NT, 1) k_batch_lm(DevGraph g, BatchArgs a) {
   __shared__ double sh[(NT / 32) * 2 + 8];
   __shared__ int s_next;
+  extern __shared__ double dense[];   // multigrid: the coarsest inverse of the current graph
   for (;;) {
     if (threadIdx.x == 0) s_next = (int)atomicAdd(a.queue, 1u);
     __syncthreads();
     const int q = s_next;
     __syncthreads();
     if (q >= a.n_graphs) return;
-    solve_graph<MIXED, G>(g, a, a.order[q], sh);
+    solve_graph<MIXED, G>(g, a, a.order[q], sh, dense);
   }
 }
 
@@ -466,9 +535,11 @@ cudaError_t launch_batch_lm(const DevGraph& g, const BatchArgs& a, int schedule,
   const int blocks = a.n_graphs < sms ? a.n_graphs : sms;
   // explicit dispatch in list order
   int idx = 0;
+  const size_t n7 = 7 * AMG_CMAX;
+  const size_t smem = a.amg ? (n7 * n7 + n7) * sizeof(double) : 0;
 #define PGO_D(M, G, NT)                                   \
   if (schedule == idx) {                                  \
-    k_batch_lm<M, G, NT><<<blocks, NT, 0, s>>>(g, a);     \
+    k_batch_lm<M, G, NT><<<blocks, NT, smem, s>>>(g, a);  \
     return cudaGetLastError();                            \
   }                                                       \
   ++idx;

@@ -151,10 +151,13 @@ struct pgo_batch {
   BatchArgs args{};                // device pointers
   void* meta = nullptr;            // device allocation holding the per-graph arrays
   double* saved_poses = nullptr;   // autotuning: the estimate to restore after each trial
-  int schedule = -1;               // tuned schedule per precision
-  int tuned[2] = {-1, -1};
-  float tune_ms[2] = {0.f, 0.f};
+  int schedule = -1;               // tuned schedule per precision and preconditioner
+  int tuned[4] = {-1, -1, -1, -1}; // [mixed + 2 * multigrid]
+  float tune_ms[4] = {0.f, 0.f, 0.f, 0.f};
   std::map<int, cudaGraphExec_t> execs;
+  std::vector<int> fixed;          // gauge vertex of each graph (concatenated index)
+  bool amg_failed = false;
+  bool schedule_amg = false;       // the last solve used multigrid
 };
 
 namespace {
@@ -247,8 +250,9 @@ pgo_status ensure_amg(pgo_graph* G, int precond) {
     return PGO_OK;
   }
   const char* err = nullptr;
-  G->amg = amg_build(G->N, G->fixed, G->h_inc_ptr.data(), G->h_inc_code.data(), G->h_inc_other.data(), G->stream,
-                     &err);
+  const int v0 = 0, nv = G->N, fx = G->fixed;
+  G->amg = amg_build(G->N, 1, &v0, &nv, &fx, G->h_inc_ptr.data(), G->h_inc_code.data(), G->h_inc_other.data(),
+                     G->stream, &err);
   if (!G->amg) return fail(PGO_ERR_OOM, "multigrid set-up: %s", err ? err : "unknown error");
   G->g.amg = amg_device_desc(G->amg);
   return PGO_OK;
@@ -1183,6 +1187,7 @@ pgo_status pgo_batch_create(int32_t n_graphs, const pgo_graph_desc* descs, void*
   B->nv = nv;
   B->ne = ne;
   B->v0 = v0;
+  B->fixed = fixed;
   // processing order: largest graphs first (longest-processing-time rule)
   std::vector<int> order(n_graphs);
   std::iota(order.begin(), order.end(), 0);
@@ -1239,8 +1244,33 @@ void pgo_batch_destroy(pgo_batch* B) {
   delete B;
 }
 
-static pgo_status batch_exec(pgo_batch* B, int schedule, cudaGraphExec_t* out) {
-  auto it = B->execs.find(schedule);
+// The multigrid hierarchy of the batch: one segment per graph, so that every
+// level stays block-diagonal over the graphs (analysed at the first batch
+// solve that asks for it).  False when the batch has no free vertex.
+static pgo_status ensure_batch_amg(pgo_batch* B, bool* have) {
+  pgo_graph* G = B->G;
+  *have = false;
+  if (B->amg_failed) return PGO_OK;
+  if (!G->amg) {
+    int K = 0;
+    for (int k = 0; k < B->n; ++k) K += B->nv[k] - 1;
+    if (K < 1) {
+      B->amg_failed = true;
+      return PGO_OK;
+    }
+    const char* err = nullptr;
+    G->amg = amg_build(G->N, B->n, B->v0.data(), B->nv.data(), B->fixed.data(), G->h_inc_ptr.data(),
+                       G->h_inc_code.data(), G->h_inc_other.data(), G->stream, &err);
+    if (!G->amg) return fail(PGO_ERR_OOM, "batch multigrid set-up: %s", err ? err : "unknown error");
+    G->g.amg = amg_device_desc(G->amg);
+  }
+  *have = true;
+  return PGO_OK;
+}
+
+static pgo_status batch_exec(pgo_batch* B, int schedule, bool amg, cudaGraphExec_t* out) {
+  const int key = schedule * 2 + (amg ? 1 : 0);
+  auto it = B->execs.find(key);
   if (it != B->execs.end()) {
     *out = it->second;
     return PGO_OK;
@@ -1250,10 +1280,12 @@ static pgo_status batch_exec(pgo_batch* B, int schedule, cudaGraphExec_t* out) {
   CUDA_TRY(cudaGraphCreate(&graph, 0));
   GraphBuilder gb{G->cap_stream};
   cudaError_t le = cudaSuccess;
+  BatchArgs args = B->args;
+  args.amg = amg ? 1 : 0;
   gb.capture(graph, [&](cudaStream_t s) {
-    launch_batch_reset(G->g, B->args, s);
-    cudaMemsetAsync(B->args.queue, 0, sizeof(unsigned), s);
-    le = launch_batch_lm(G->g, B->args, schedule, s);
+    launch_batch_reset(G->g, args, s);
+    cudaMemsetAsync(args.queue, 0, sizeof(unsigned), s);
+    le = launch_batch_lm(G->g, args, schedule, s);
   });
   if (le != cudaSuccess) gb.err = le;
   if (gb.err != cudaSuccess) {
@@ -1264,7 +1296,7 @@ static pgo_status batch_exec(pgo_batch* B, int schedule, cudaGraphExec_t* out) {
   cudaError_t e = cudaGraphInstantiate(&ex, graph, 0);
   cudaGraphDestroy(graph);
   if (e != cudaSuccess) return fail(PGO_ERR_CUDA, "instantiating the batch graph: %s", cudaGetErrorString(e));
-  B->execs[schedule] = ex;
+  B->execs[key] = ex;
   *out = ex;
   return PGO_OK;
 }
@@ -1272,7 +1304,7 @@ static pgo_status batch_exec(pgo_batch* B, int schedule, cudaGraphExec_t* out) {
 // Autotuner: time one LM iteration (PCG capped at 40 iterations) of the
 // whole batch for every schedule of the requested precision and keep the
 // fastest; the estimate is restored after every trial.
-static pgo_status batch_autotune(pgo_batch* B, const pgo_solve_options& o, int mixed) {
+static pgo_status batch_autotune(pgo_batch* B, const pgo_solve_options& o, int mixed, bool amg) {
   pgo_graph* G = B->G;
   cudaStream_t s = G->stream;
   const size_t nbytes = sizeof(D4) * (size_t)G->N;
@@ -1291,7 +1323,7 @@ static pgo_status batch_autotune(pgo_batch* B, const pgo_solve_options& o, int m
   for (int sc = 0; sc < batch_schedule_count(); ++sc) {
     if (batch_schedule_mixed(sc) != mixed) continue;
     cudaGraphExec_t ex;
-    pgo_status st = batch_exec(B, sc, &ex);
+    pgo_status st = batch_exec(B, sc, amg, &ex);
     if (st != PGO_OK) return st;
     float ms = 0.f;
     for (int rep = 0; rep < 2; ++rep) {   // first run warms up
@@ -1311,8 +1343,8 @@ static pgo_status batch_autotune(pgo_batch* B, const pgo_solve_options& o, int m
     }
   }
   if (best_s < 0) return fail(PGO_ERR_STATE, "no batch schedule for this precision");
-  B->tuned[mixed] = best_s;
-  B->tune_ms[mixed] = best;
+  B->tuned[mixed + 2 * amg] = best_s;
+  B->tune_ms[mixed + 2 * amg] = best;
   return PGO_OK;
 }
 
@@ -1328,20 +1360,27 @@ pgo_status pgo_batch_solve(pgo_batch* B, const pgo_solve_options* opt, pgo_repor
   pgo_graph* G = B->G;
   cudaStream_t s = G->stream;
   const int mixed = o.precision == PGO_MIXED;
+  bool amg = false;
+  if (o.preconditioner == PGO_PRECOND_MULTIGRID) {
+    st = ensure_batch_amg(B, &amg);
+    if (st != PGO_OK) return st;
+  }
+  const int tk = mixed + 2 * (amg ? 1 : 0);
   int sc = o.schedule;
   if (sc >= 0) {
     if (sc >= batch_schedule_count() || batch_schedule_mixed(sc) != mixed)
       return fail(PGO_ERR_INVALID_ARG, "schedule %d does not exist for this precision", sc);
   } else {
-    if (B->tuned[mixed] < 0) {
-      st = batch_autotune(B, o, mixed);
+    if (B->tuned[tk] < 0) {
+      st = batch_autotune(B, o, mixed, amg);
       if (st != PGO_OK) return st;
     }
-    sc = B->tuned[mixed];
+    sc = B->tuned[tk];
   }
   B->schedule = sc;
+  B->schedule_amg = amg;
   cudaGraphExec_t ex;
-  st = batch_exec(B, sc, &ex);
+  st = batch_exec(B, sc, amg, &ex);
   if (st != PGO_OK) return st;
   fill_dev_options(o, G->h_opt);
   CUDA_TRY(cudaMemcpyAsync(G->g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
@@ -1388,7 +1427,7 @@ pgo_status pgo_batch_schedule(const pgo_batch* B, int32_t* lanes, int32_t* threa
   if (B->schedule < 0) return fail(PGO_ERR_STATE, "no batch solve has run");
   if (lanes) *lanes = batch_schedule_lanes(B->schedule);
   if (threads) *threads = batch_schedule_threads(B->schedule);
-  if (tune_ms) *tune_ms = B->tune_ms[batch_schedule_mixed(B->schedule)];
+  if (tune_ms) *tune_ms = B->tune_ms[batch_schedule_mixed(B->schedule) + 2 * (B->schedule_amg ? 1 : 0)];
   return PGO_OK;
 }
 

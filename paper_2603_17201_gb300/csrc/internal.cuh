@@ -112,14 +112,17 @@ struct AmgLevel {
 struct AmgDev {
   int L;                  // smoothing levels 0..L-1; level L is the coarsest
   int nL;                 // nodes at the coarsest level
+  int nseg;               // independent segments (graphs of a batch; 1 otherwise)
+  const int* seg_off;     // (L + 1) x (nseg + 1): first node of each segment per level
   AmgLevel lv[AMG_MAXL + 1];
-  double* cinv64;         // dense inverse of the coarsest operator (nL x nL blocks)
-  float* cinv32;
-  double* rho;            // per level: power-iteration estimate of rho(D^-1 A)
+  double* cinv64;         // dense inverse of the coarsest operator (nL x nL blocks;
+  float* cinv32;          // per segment AMG_CMAX^2 blocks when nseg > 1)
+  double* rho;            // per segment and level: estimate of rho(D^-1 A)
   double* pw64[2];        // power-iteration vectors
   float* pw32[2];
-  int* flag;              // nonzero: the coarsest factorisation failed
-  int* warm;              // [0] FP64, [1] FP32: a previous set-up left pv vectors
+  int* flag;              // per segment, nonzero: the coarsest factorisation failed
+  int* warm;              // per segment [2 s] FP64, [2 s + 1] FP32: a previous
+                          // set-up left pv vectors
 };
 
 // Device view of one graph.
@@ -177,6 +180,7 @@ struct BatchArgs {
   const int* order;    // processing order (largest first)
   unsigned* queue;     // work counter (zeroed before the launch)
   BatchGraphState* gst;
+  int amg;             // 1: multigrid (g.amg holds one segment per graph), 0: block-Jacobi
 };
 
 int batch_schedule_count();
@@ -213,8 +217,8 @@ cudaError_t launch_amg_setup(const DevGraph& g, const AmgDev& amg, int mixed, cu
 // Symbolic multigrid hierarchy of a graph (host analysis + one device
 // allocation); returns the host copy of the device descriptor.
 struct AmgHost;
-AmgHost* amg_build(int N, int fixed, const int* inc_ptr, const int* inc_code, const int* inc_other,
-                   cudaStream_t s, const char** err);
+AmgHost* amg_build(int N, int nseg, const int* seg_v0, const int* seg_nv, const int* seg_fixed, const int* inc_ptr,
+                   const int* inc_code, const int* inc_other, cudaStream_t s, const char** err);
 void amg_free(AmgHost* h);
 const AmgDev* amg_host_desc(const AmgHost* h);
 const AmgDev* amg_device_desc(const AmgHost* h);

@@ -12,13 +12,14 @@
 
 namespace pgo {
 
-// K1: one thread per edge.
-__global__ void __launch_bounds__(128) k_linearize(DevGraph g, int mixed) {
+// K1: one thread per edge (MIXED: FP32 Jacobians and H products).
+template <int MIXED>
+__global__ void __launch_bounds__(128) k_linearize(DevGraph g) {
   const SolverState* st = g.st;
   if (st->done || !st->need_lin) return;
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.E) return;
-  linearize_edge(g, st->cur, e, mixed);
+  linearize_edge(g, st->cur, e, MIXED);
 }
 
 // K2: 8 lanes per vertex gather the incident edge-side contributions in edge
@@ -206,7 +207,8 @@ void launch_cost(const DevGraph& g, int mode, cudaStream_t s, unsigned long long
 
 void launch_linearize(const DevGraph& g, int mixed, cudaStream_t s) {
   if (g.E == 0) return;
-  k_linearize<<<(g.E + 127) / 128, 128, 0, s>>>(g, mixed);
+  if (mixed) k_linearize<1><<<(g.E + 127) / 128, 128, 0, s>>>(g);
+  else k_linearize<0><<<(g.E + 127) / 128, 128, 0, s>>>(g);
 }
 
 void launch_assemble(const DevGraph& g, int mixed, cudaStream_t s) {

@@ -742,6 +742,11 @@ __global__ void __launch_bounds__(512) k_pcg(DevGraph g, PcgArgs a) {
     int it = 0;
     bool done = !(bb > S(0)) || !(rz > S(0));
     const S tol2 = S(tol * tol);
+    // multigrid: stop once |r| has not dropped by 10% for 20 iterations (an
+    // FP32 solve at a tiny lambda reaches its rounding floor above the
+    // tolerance; the FP64 refinement and the LM gain ratio handle the rest)
+    S rr_best = bb;
+    int stall = 0;
     while (!done) {
       // ---- SpMV: q = (H + lambda I) p, p = z + beta p_prev ----
       const V* pprev = Bufs<V>::p(g, (it + 1) & 1);
@@ -876,6 +881,14 @@ __global__ void __launch_bounds__(512) k_pcg(DevGraph g, PcgArgs a) {
       rz = t2[0];
       ++it;
       done = !(t2[1] > tol2 * bb) || !(rz > S(0)) || !isfinite((double)t2[1]);
+      if (a.amg && !done) {
+        if (t2[1] < S(0.81) * rr_best) {
+          rr_best = t2[1];
+          stall = 0;
+        } else if (++stall >= 20) {
+          done = true;
+        }
+      }
       if (!done && it >= maxit) {
         done = true;
         if (blockIdx.x == 0 && threadIdx.x == 0) st->pcg_hit_cap = 1;

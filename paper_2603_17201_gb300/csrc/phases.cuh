@@ -15,7 +15,60 @@ static __device__ __constant__ unsigned char c_up_c[28] = {0, 1, 2, 3, 4, 5, 6, 
 // K1 for one edge: residual and exact Jacobians (poses in buffer `cur`), the
 // off-diagonal (i, j) block w A_i^T A_j (FP64, and FP32 in mixed mode) and
 // the two edge-side contributions [upper(w A^T A), w A^T r].
+// Mixed precision: FP64 residual, FP32 Jacobians and H products (the
+// off-diagonal block also kept promoted in FP64 for the refinement residual),
+// the gradient sum A^T r in FP64 from the FP32 Jacobians.
+__device__ __forceinline__ void linearize_edge_mixed(const DevGraph& g, int cur, int e) {
+  double r[7];
+  float Ai[7][7], Aj[7][7];
+  edge_jacobians_mixed(g, cur, e, r, Ai, Aj);
+  const float w = (float)g.w[e];
+  double* off = g.off64 + (size_t)e * BLK64;
+  float* off32 = g.off32 + (size_t)e * BLK32;
+#pragma unroll
+  for (int a = 0; a < 7; ++a) {
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      float s = 0.f;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) s += Ai[k][a] * Aj[k][c];
+      s *= w;
+      off32[a * 7 + c] = s;
+      off[a * 7 + c] = (double)s;
+    }
+  }
+  const double wd = g.w[e];
+  double* ci = g.contrib + (size_t)e * 2 * CONTRIB;
+  double* cj = ci + CONTRIB;
+#pragma unroll
+  for (int a = 0; a < 7; ++a) {
+#pragma unroll
+    for (int c = a; c < 7; ++c) {
+      float si = 0.f, sj = 0.f;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) {
+        si += Ai[k][a] * Ai[k][c];
+        sj += Aj[k][a] * Aj[k][c];
+      }
+      ci[upk(a, c)] = (double)(w * si);
+      cj[upk(a, c)] = (double)(w * sj);
+    }
+    double gi = 0.0, gj = 0.0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) {
+      gi += (double)Ai[k][a] * r[k];
+      gj += (double)Aj[k][a] * r[k];
+    }
+    ci[28 + a] = wd * gi;
+    cj[28 + a] = wd * gj;
+  }
+}
+
 __device__ __forceinline__ void linearize_edge(const DevGraph& g, int cur, int e, int mixed) {
+  if (mixed) {
+    linearize_edge_mixed(g, cur, e);
+    return;
+  }
   double r[7], Ai[7][7], Aj[7][7];
   edge_jacobians(g, cur, e, r, Ai, Aj);
   const double w = g.w[e];

@@ -1,6 +1,8 @@
 """Batched form (Sec. IV-F solve over many graphs in one persistent launch):
-every graph of an uneven batch against its own oracle solve, the schedules
-the autotuner chooses from, and agreement with single-graph GPU solves."""
+every graph of an uneven batch against its own oracle solve with either
+preconditioner (the multigrid hierarchy is one segment per graph), the
+schedules the autotuner chooses from, and agreement with single-graph GPU
+solves."""
 import numpy as np
 import pytest
 
@@ -30,12 +32,13 @@ def uneven_batch(n=12, seed0=50):
     return gs
 
 
+@pytest.mark.parametrize("precond", ["block_jacobi", "multigrid"])
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-9), ("mixed", 1e-6)])
-def test_batch_matches_oracle_per_graph(precision, tol):
+def test_batch_matches_oracle_per_graph(precision, tol, precond):
     from paper_2603_17201_gb300 import PoseGraphBatch
     gs = uneven_batch()
     b = PoseGraphBatch(gs)
-    reps, poses = b.solve(max_iters=20, precision=precision)
+    reps, poses = b.solve(max_iters=20, precision=precision, preconditioner=precond)
     lanes, threads, _ = b.schedule()
     assert lanes in (4, 8, 16) and threads in (256, 512)
     for g, rep, p in zip(gs, reps, poses):

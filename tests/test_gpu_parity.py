@@ -97,6 +97,20 @@ def test_jacobians_and_normal_equations(name):
         assert np.abs(got - ref).max() <= 1e-10 * max(1.0, np.abs(ref).max())
 
 
+@pytest.mark.parametrize("name", CASES)
+def test_mixed_normal_equations(name):
+    """Mixed precision: FP32 Jacobians and H products, FP64 residual and
+    gradient sum; H within FP32 rounding of the FP64 oracle (1e-5 of the
+    largest entry) and b likewise."""
+    g, w, I = case_graph(name)
+    og, pg = make_pair(g, w, I)
+    lin = pg.linearize("mixed", jacobians=False)
+    _, Hd, Ho, b = og.linearize(g.poses_init)
+    for got, ref in ((lin["h_diag"], Hd), (lin["h_off"], Ho), (lin["b"], b)):
+        err = np.abs(got - ref).max() / max(1.0, np.abs(ref).max())
+        assert err <= 1e-5, err
+
+
 @pytest.mark.parametrize("precond", ["block_jacobi", "multigrid"])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 @pytest.mark.parametrize("name", ["c1", "noisy_info_w"])
@@ -105,6 +119,12 @@ def test_damped_step(name, precision, precond):
     og, pg = make_pair(g, w, I)
     _, Hd, Ho, b = og.linearize(g.poses_init)
     lam = 1e-4 * max(np.diag(Hd[v]).max() for v in range(g.n_vertices))
+    if precision == "mixed":
+        # the mixed mode solves its own FP32-Jacobian normal equations (bounded
+        # against the FP64 ones in test_mixed_normal_equations): the exact
+        # solve of exactly that system is the reference
+        lin = pg.linearize("mixed", jacobians=False)
+        Hd, Ho, b = lin["h_diag"], lin["h_off"], lin["b"]
     ref = og.solve_system(Hd, Ho, b, lam)
     d, its = pg.damped_step(lam, precision=precision, pcg_tol=1e-12, pcg_max_iters=20000, refine_steps=6,
                             preconditioner=precond)
