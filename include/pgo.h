@@ -110,9 +110,10 @@ typedef struct {
   int32_t pcg_max_iters;  /* PCG iteration cap per linear solve (5000) */
   int32_t refine_steps;   /* PGO_MIXED: FP64 iterative-refinement passes (3) */
   double refine_tol;      /* PGO_MIXED: inner FP32 PCG relative tolerance (1e-6) */
-  int32_t polish_iters;   /* undamped Newton steps after LM, each kept only
-                             while it lowers |b|_inf (0; use >0 before
-                             pgo_backward) */
+  int32_t polish_iters;   /* undamped Newton steps after LM on the full
+                             Hessian (second-order residual terms included),
+                             each kept only while it lowers |b|_2 (0; use > 0
+                             before pgo_backward) */
   int32_t schedule;       /* kernel schedule id; -1 = library default */
   int32_t preconditioner; /* pgo_preconditioner (PGO_PRECOND_MULTIGRID) */
 } pgo_solve_options;

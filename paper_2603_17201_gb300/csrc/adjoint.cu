@@ -157,8 +157,9 @@ __device__ __forceinline__ Sim3T<D1> seed_dir(const Sim3T<double>& P, int k) {
 // Full-Hessian contributions of one edge: the 14x14 block d g_e / d(x_i, x_j)
 // column by column (one nested-dual pass per direction).  Diagonal blocks go
 // to the contribution slots (symmetrised upper triangles), the (i, j) block
-// symmetrised as (H_ij + H_ji^T) / 2 to off64.  The gradient slots are zero.
-__global__ void __launch_bounds__(64) k_adj_hessian(DevGraph g) {
+// symmetrised as (H_ij + H_ji^T) / 2 to off64.  The gradient slots receive the
+// edge gradient g_e itself (with_grad: the Newton polish) or zero (adjoint).
+__global__ void __launch_bounds__(64) k_adj_hessian(DevGraph g, int with_grad) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= g.E) return;
   const int cur = g.st->cur;
@@ -166,6 +167,7 @@ __global__ void __launch_bounds__(64) k_adj_hessian(DevGraph g) {
   const double w = g.w[e];
   const double* L = g.L ? g.L + (size_t)e * 28 : nullptr;
   double H[14][14];   // H[row][col] = d g_row / d x_col
+  double gv[14];      // g_e (the value part, the same in every pass)
   const Sim3T<D1> Zd = seed_dir(Z, -1);
   for (int col = 0; col < 14; ++col) {
     const Sim3T<D1> Pi = seed_dir(Si, col < 7 ? col : -1);
@@ -174,6 +176,9 @@ __global__ void __launch_bounds__(64) k_adj_hessian(DevGraph g) {
     edge_gradient(Pi, Pj, Zd, w, L, gg);
 #pragma unroll
     for (int row = 0; row < 14; ++row) H[row][col] = gg[row].d[0];
+    if (col == 0)
+#pragma unroll
+      for (int row = 0; row < 14; ++row) gv[row] = gg[row].v;
   }
   double* ci = g.contrib + (size_t)e * 2 * CONTRIB;
   double* cj = ci + CONTRIB;
@@ -184,8 +189,8 @@ __global__ void __launch_bounds__(64) k_adj_hessian(DevGraph g) {
       cj[u] = 0.5 * (H[7 + a][7 + c] + H[7 + c][7 + a]);
     }
   for (int k = 28; k < CONTRIB; ++k) {
-    ci[k] = 0.0;
-    cj[k] = 0.0;
+    ci[k] = (with_grad && k < 35) ? gv[k - 28] : 0.0;
+    cj[k] = (with_grad && k < 35) ? gv[7 + k - 28] : 0.0;
   }
   double* off = g.off64 + (size_t)e * BLK64;
   for (int a = 0; a < 7; ++a)
@@ -282,9 +287,9 @@ __global__ void __launch_bounds__(64) k_adj_edges(DevGraph g, const int* perm, d
   o[7] = (gz[6] - (gu[0] * t[0] + gu[1] * t[1] + gu[2] * t[2])) / Z.s;
 }
 
-void launch_adj_hessian(const DevGraph& g, cudaStream_t s) {
+void launch_adj_hessian(const DevGraph& g, int with_grad, cudaStream_t s) {
   if (g.E == 0) return;
-  k_adj_hessian<<<(g.E + 63) / 64, 64, 0, s>>>(g);
+  k_adj_hessian<<<(g.E + 63) / 64, 64, 0, s>>>(g, with_grad);
 }
 void launch_adj_rhs(const DevGraph& g, const double* dL, int layout, cudaStream_t s) {
   k_adj_rhs<<<(g.N + 127) / 128, 128, 0, s>>>(g, dL, layout);

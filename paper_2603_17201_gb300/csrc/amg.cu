@@ -617,6 +617,7 @@ __global__ void __launch_bounds__(256) k_amg_setup(DevGraph g) {
   const bool warm = __ldcg(g.amg->warm + warm_slot) != 0;
   double* partial = g.partial;
   __shared__ V sacc[4][49];
+  __shared__ double smat[4][50];   // D^-1 teams
   extern __shared__ double dense[];   // coarsest operator (block 0 only)
 
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -763,13 +764,14 @@ __global__ void __launch_bounds__(256) k_amg_setup(DevGraph g) {
     }
     if (!grid_sync(counter, abort_flag, target)) goto timeout;
     if (l + 1 < A.L) {
+      // the next level's D^-1: one 64-thread team per node
       const V* An = AV<V>::a(Ln);
-      for (int c = gtid; c < Ln.n; c += gthreads) {
-        V Bl[49];
-        const V* src = An + (size_t)__ldg(Ln.a_ptr + c) * BLK;
-#pragma unroll
-        for (int k = 0; k < 49; ++k) Bl[k] = __ldcg(src + k);
-        inv7_spd<V>(Bl, AV<V>::dinv(Ln) + (size_t)c * BLK);
+      const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
+      for (int c0 = blockIdx.x * 4; c0 < Ln.n; c0 += gridDim.x * 4) {
+        const int c = c0 + slot;
+        const bool has = c < Ln.n;
+        inv7_spd_team<V, true>(An + (size_t)(has ? __ldg(Ln.a_ptr + c) : 0) * BLK,
+                               AV<V>::dinv(Ln) + (size_t)(has ? c : 0) * BLK, has, smat[slot], t);
       }
       if (!grid_sync(counter, abort_flag, target)) goto timeout;
     }

@@ -236,4 +236,45 @@ __device__ __forceinline__ bool inv7_spd(const V* B, V* out) {
   return true;
 }
 
+// Inverse of the SPD 7x7 block `src` into `dst` by a team of 64 threads of a
+// block (thread t < 49 owns entry (t / 7, t % 7)): Gauss-Jordan without
+// pivoting in the team's shared scratch M (50 doubles; M[49] flags a
+// non-positive pivot), then the symmetrised result.  Every thread of the
+// block must call it together (it synchronises the block: the caller's loop
+// needs a block-uniform trip count); `has` false skips the team's arithmetic.
+// A non-positive pivot falls back to the inverse of the diagonal.
+template <class V, bool CG>
+__device__ __forceinline__ void inv7_spd_team(const V* src, V* dst, bool has, double* M, int t) {
+  const int i = t / 7, j = t - 7 * (t / 7);
+  const bool on = has && t < 49;
+  if (on) M[t] = (double)(CG ? __ldcg(src + t) : src[t]);
+  if (t == 0) M[49] = 0.0;
+  __syncthreads();
+  for (int k = 0; k < 7; ++k) {
+    double p = 1.0, mkj = 0.0, fik = 0.0;
+    if (on) {
+      p = M[k * 7 + k];
+      mkj = M[k * 7 + j];
+      fik = M[i * 7 + k];
+    }
+    __syncthreads();
+    if (on) {
+      if (!(p > 0.0)) M[49] = 1.0;   // benign race: every writer stores 1
+      const double ip = 1.0 / p;
+      if (i == k) M[t] = (j == k) ? ip : mkj * ip;
+      else M[t] = (j == k) ? -fik * ip : M[t] - fik * mkj * ip;
+    }
+    __syncthreads();
+  }
+  if (on) {
+    double v = 0.5 * (M[t] + M[j * 7 + i]);
+    if (M[49] != 0.0) {
+      const double d = (double)(CG ? __ldcg(src + i * 8) : src[i * 8]);
+      v = (i == j && d > 0.0) ? 1.0 / d : 0.0;
+    }
+    dst[t] = V(v);
+  }
+  __syncthreads();
+}
+
 }  // namespace pgo

@@ -168,6 +168,7 @@ __device__ void cta_amg_setup(const DevGraph& g, const AmgDev& A, int sg, int fi
                               double* dense) {
   constexpr int BLK = AV<V>::BLK;
   __shared__ V sacc[8][49];
+  __shared__ double smat[8][50];   // D^-1 teams
   const V lam = V(lam_d);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int L = A.L;
@@ -296,15 +297,14 @@ __device__ void cta_amg_setup(const DevGraph& g, const AmgDev& A, int sg, int fi
       __syncthreads();
     }
     if (l + 1 < L) {
+      // the next level's D^-1: one 64-thread team per node
       const V* An = AV<V>::a(Ln);
-      for (int c = c0 + tid; c < c1; c += nt) {
-        V Bl[49];
-        const V* src = An + (size_t)__ldg(Ln.a_ptr + c) * BLK;
-#pragma unroll
-        for (int k = 0; k < 49; ++k) Bl[k] = __ldcg(src + k);
-        inv7_spd<V>(Bl, AV<V>::dinv(Ln) + (size_t)c * BLK);
+      for (int cb = c0; cb < c1; cb += nslots) {
+        const int c = cb + slot;
+        const bool has = c < c1;
+        inv7_spd_team<V, true>(An + (size_t)(has ? __ldg(Ln.a_ptr + c) : 0) * BLK,
+                               AV<V>::dinv(Ln) + (size_t)(has ? c : 0) * BLK, has, smat[slot], t64);
       }
-      __syncthreads();
     }
   }
   cta_coarsest_inverse<V>(A, sg, dense);

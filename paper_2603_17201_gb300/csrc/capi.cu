@@ -821,11 +821,14 @@ pgo_status pgo_graph_damped_step(pgo_graph* G, const pgo_solve_options* opt, dou
   return PGO_OK;
 }
 
-// Undamped Gauss-Newton steps after LM, each kept only while it lowers the
-// gradient norm |b|_2 (LM's cost-based acceptance cannot resolve the last
-// digits of the optimum; the implicit adjoint needs b(x*) ~ 0).  A step that
-// does not lower it is halved up to three times before polishing stops.
-// FP64, host-driven: a few steps with a synchronisation each.
+// Newton steps after LM on the full Hessian (second-order residual terms
+// included, the same exact nested-dual Hessian as the adjoint), each kept
+// only while it lowers the gradient norm |b|_2.  LM's cost-based stop cannot
+// resolve the last digits of the optimum (a tiny change of the measurements
+// changes F by less than ftol F), and Gauss-Newton steps need not lower |b|
+// on noisy, ill-conditioned graphs; the implicit adjoint needs b(x*) ~ 0.  A
+// step that does not lower |b| is halved up to three times before polishing
+// stops.  FP64, host-driven: a few steps with a synchronisation each.
 static pgo_status run_polish(pgo_graph* G, const pgo_solve_options& o) {
   const DevGraph& g = G->g;
   cudaStream_t s = G->stream;
@@ -834,7 +837,7 @@ static pgo_status run_polish(pgo_graph* G, const pgo_solve_options& o) {
   CUDA_TRY(cudaMemcpyAsync(g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
   auto linearize_here = [&](double* b2, double* gmax) -> pgo_status {
     launch_state_ctl(g, 0, s);
-    launch_linearize(g, 0, s);
+    launch_adj_hessian(g, 1, s);
     launch_assemble_mode(g, 2, s);
     CUDA_TRY(cudaGetLastError());
     CUDA_TRY(cudaMemcpyAsync(G->h_state, g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
@@ -1044,7 +1047,7 @@ pgo_status pgo_backward(pgo_graph* G, const pgo_solve_options* opt, const double
   G->h_opt->lambda_fixed = 0.0;
   CUDA_TRY(cudaMemcpyAsync(g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
   launch_state_ctl(g, 0, s);          // done = 0, lambda = 0, tickets cleared
-  launch_adj_hessian(g, s);           // full-Hessian blocks of every edge
+  launch_adj_hessian(g, 0, s);        // full-Hessian blocks of every edge
   launch_assemble_mode(g, 1, s);      // diagonal blocks
   launch_adj_rhs(g, dl, layout, s);   // b = -dL/dx
   cudaError_t le = cudaSuccess;

@@ -200,7 +200,8 @@ void launch_assemble(const DevGraph& g, int mixed, cudaStream_t s);
 // mode 1: full-Hessian assembly for the adjoint; mode 2: polish step
 // (both skip the LM lambda_0 and gradient-stop logic)
 void launch_assemble_mode(const DevGraph& g, int mode, cudaStream_t s);
-void launch_adj_hessian(const DevGraph& g, cudaStream_t s);
+// with_grad: also the edge gradients (Newton polish); 0: zero gradient slots (adjoint)
+void launch_adj_hessian(const DevGraph& g, int with_grad, cudaStream_t s);
 void launch_adj_rhs(const DevGraph& g, const double* dL, int layout, cudaStream_t s);
 void launch_adj_edges(const DevGraph& g, const int* perm, double* dL_dmeas, double* dL_dw, int layout,
                       cudaStream_t s);

@@ -179,3 +179,54 @@ def test_autograd_function_pose8_layout():
                 fdm[k] = (L_at(mp, wt.detach()) - L_at(mm, wt.detach())) / (2 * h)
             assert np.linalg.norm(fdm - gm[e]) <= 1e-5 * max(np.linalg.norm(fdm), 1e-3 * np.abs(gm).max()), \
                 (fdm, gm[e])
+
+
+@pytest.mark.slow
+def test_c5_adjoint_4k_against_fd_and_oracle():
+    """The differentiation workload: the 4,000-keyframe noisy figure-8 graph
+    (67,857 edges, weights 1.0), FP64 forward to convergence, gradients of the
+    final pose-error loss w.r.t. every measurement (left tangent) and weight.
+    Checked against the oracle's adjoint at the same optimum (1e-6 relative to
+    the largest gradient) and against central differences of the whole solve
+    (step 1e-4) on 64 random edges (1e-5, per edge on vector norms, floor 1e-3
+    of the largest gradient)."""
+    g = syn.make_config("c5_figure8_4k_noisy")
+    w = np.ones(g.n_edges)
+    pg = PG(g.n_vertices, g.edge_i, g.edge_j, g.meas, w, None, g.poses_init, 0)
+    rep = pg.solve(**POLISH)
+    assert rep["status"] == 0 and rep["grad_inf_norm"] < 1e-9, rep
+    p_star = pg.get_poses()
+    og = O.OracleGraph(g.n_vertices, g.edge_i, g.edge_j, g.meas, None, None, 0)
+    _, dLdx = og.pose_loss(p_star, g.poses_gt)
+    dz, dw = pg.backward(dLdx, layout="tangent")
+    dz_ref, dw_ref, _ = og.adjoint(p_star, dLdx)
+    assert rel_err(dw, dw_ref) < 1e-6, rel_err(dw, dw_ref)
+    assert rel_err(dz, dz_ref) < 1e-6, rel_err(dz, dz_ref)
+
+    def solve_loss(meas, weight):
+        pg.set_measurements(meas, weight)
+        pg.set_poses(p_star)
+        pg.solve(**POLISH)
+        return og.pose_loss(pg.get_poses(), g.poses_gt)[0]
+
+    # step 1e-4: the loss of a converged 4k-keyframe solve carries ~1e-10 of
+    # rounding, which a 1e-5 step would amplify past the bar; the central
+    # difference's truncation error at 1e-4 is ~1e-8 relative
+    rng = np.random.default_rng(64)
+    h = 1e-4
+    gz, gw = np.abs(dz).max(), np.abs(dw).max()
+    for e in rng.choice(g.n_edges, 64, replace=False):
+        wp, wm = w.copy(), w.copy()
+        wp[e] += h
+        wm[e] -= h
+        fd_w = (solve_loss(g.meas, wp) - solve_loss(g.meas, wm)) / (2 * h)
+        assert abs(fd_w - dw[e]) <= 1e-5 * max(abs(fd_w), 1e-3 * gw), (e, fd_w, dw[e])
+        fd_z = np.zeros(7)
+        for k in range(7):
+            d = np.zeros(7)
+            d[k] = h
+            mp, mm = g.meas.copy(), g.meas.copy()
+            mp[e] = syn.compose(O.exp(d), mp[e])
+            mm[e] = syn.compose(O.exp(-d), mm[e])
+            fd_z[k] = (solve_loss(mp, w) - solve_loss(mm, w)) / (2 * h)
+        assert np.linalg.norm(fd_z - dz[e]) <= 1e-5 * max(np.linalg.norm(fd_z), 1e-3 * gz), (e, fd_z, dz[e])
