@@ -108,7 +108,7 @@ typedef struct {
   double gtol;            /* stop when |b|_inf <= gtol (1e-13) */
   double pcg_tol;         /* PCG: |r| <= pcg_tol * |b| (1e-10) */
   int32_t pcg_max_iters;  /* PCG iteration cap per linear solve (5000) */
-  int32_t refine_steps;   /* PGO_MIXED: FP64 iterative-refinement passes (3) */
+  int32_t refine_steps;   /* PGO_MIXED: FP64 iterative-refinement passes (2) */
   double refine_tol;      /* PGO_MIXED: inner FP32 PCG relative tolerance (1e-6) */
   int32_t polish_iters;   /* undamped Newton steps after LM on the full
                              Hessian (second-order residual terms included),

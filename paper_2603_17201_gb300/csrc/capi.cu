@@ -434,7 +434,7 @@ pgo_status pgo_default_options(pgo_solve_options* opt) {
   opt->gtol = 1e-13;
   opt->pcg_tol = 1e-10;
   opt->pcg_max_iters = 5000;
-  opt->refine_steps = 3;
+  opt->refine_steps = 2;
   opt->refine_tol = 1e-6;
   opt->polish_iters = 0;
   opt->schedule = -1;
