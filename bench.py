@@ -246,7 +246,8 @@ def run_reference(args):
 
 
 # --------------------------------------------------------------------- batched form
-BATCH_SCHEDULES = [(4, 256), (8, 256), (16, 256), (8, 512), (16, 512)]
+BATCH_SCHEDULES = [(4, 256, 1), (8, 256, 1), (16, 256, 1), (8, 512, 1), (16, 512, 1),
+                   (4, 256, 2), (8, 256, 2), (16, 256, 2)]
 
 
 def run_batch(args):
@@ -267,8 +268,8 @@ def run_batch(args):
     for precision in ("fp64", "mixed"):
         b = PoseGraphBatch(gs)
         b.solve(poses=False, max_iters=MAX_ITERS, precision=precision)   # warm-up + autotune
-        lanes, threads, _ = b.schedule()
-        sched = BATCH_SCHEDULES.index((lanes, threads)) + (5 if precision == "mixed" else 0)
+        lanes, threads, bps, _ = b.schedule()
+        sched = BATCH_SCHEDULES.index((lanes, threads, bps)) + (len(BATCH_SCHEDULES) if precision == "mixed" else 0)
         ms, its = [], []
         for _ in range(max(1, args.steps)):
             b = PoseGraphBatch(gs)
@@ -285,7 +286,8 @@ def run_batch(args):
             seq += pg.solve(max_iters=MAX_ITERS, precision=precision)["ms_total"]
         t = statistics.median(ms)
         out[precision] = {"ms_per_batch": t, "ms_per_graph": t / len(gs), "lm_iterations": statistics.median(its),
-                          "graph_edges_per_s": E / (t * 1e-3), "schedule": {"lanes": lanes, "threads": threads},
+                          "graph_edges_per_s": E / (t * 1e-3),
+                          "schedule": {"lanes": lanes, "threads": threads, "blocks_per_sm": bps},
                           "sequential_single_ms_scaled": seq * len(gs) / sample,
                           "sequential_sample": f"first {sample} graphs, single-graph multigrid solves"}
     line = {"metric": "batched Sim(3) PGO: ms per batch of 256 graphs (one persistent launch)", "unit": "ms",

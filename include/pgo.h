@@ -275,9 +275,11 @@ pgo_status pgo_batch_solve(pgo_batch* b, const pgo_solve_options* opt, pgo_repor
                            double* const* poses_out, int32_t out_mem_space);
 
 /* The schedule of the last batch solve: lanes per block row in the SpMV,
- * threads per block, and the autotuner's best trial time in ms (nullable
- * outputs).  PGO_ERR_STATE before the first solve. */
-pgo_status pgo_batch_schedule(const pgo_batch* b, int32_t* lanes, int32_t* threads, float* tune_ms);
+ * threads per block, resident blocks per SM (graphs solved side by side on
+ * one SM), and the autotuner's best trial time in ms (nullable outputs).
+ * PGO_ERR_STATE before the first solve. */
+pgo_status pgo_batch_schedule(const pgo_batch* b, int32_t* lanes, int32_t* threads, int32_t* blocks_per_sm,
+                              float* tune_ms);
 
 /* Stateless cost evaluation (the Sec. IV-F objective) over caller-owned
  * device arrays: n_vertices poses (pose8), n_edges edges (edge_i, edge_j,

@@ -115,7 +115,7 @@ def load(build_if_missing: bool = True):
         lib.pgo_batch_destroy.restype = None
         lib.pgo_batch_solve.argtypes = [vp, ctypes.POINTER(SolveOptions), ctypes.POINTER(Report), vp, c_int32]
         lib.pgo_batch_schedule.argtypes = [vp, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32),
-                                           ctypes.POINTER(ctypes.c_float)]
+                                           ctypes.POINTER(c_int32), ctypes.POINTER(ctypes.c_float)]
         lib.pgo_evaluate_cost.argtypes = [c_int32, c_int32, vp, vp, vp, vp, vp, vp, vp]
         lib.pgo_evaluate_cost_noalloc.argtypes = [c_int32, c_int32, vp, vp, vp, vp, vp, vp, vp]
         for name in EXPORTED:

@@ -343,10 +343,12 @@ class PoseGraphBatch:
         L.check(self._lib.pgo_batch_solve(self._h, ctypes.byref(o), None, None, L.PGO_MEM_HOST))
 
     def schedule(self):
-        """(lanes per block row, threads per block, autotuner best trial ms)."""
-        lanes, threads, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
-        L.check(self._lib.pgo_batch_schedule(self._h, ctypes.byref(lanes), ctypes.byref(threads), ctypes.byref(ms)))
-        return lanes.value, threads.value, ms.value
+        """(lanes per block row, threads per block, blocks per SM, autotuner
+        best trial ms)."""
+        lanes, threads, bps, ms = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_float()
+        L.check(self._lib.pgo_batch_schedule(self._h, ctypes.byref(lanes), ctypes.byref(threads), ctypes.byref(bps),
+                                             ctypes.byref(ms)))
+        return lanes.value, threads.value, bps.value, ms.value
 
 
 class _SolveFunction:

@@ -464,8 +464,8 @@ __device__ void solve_graph(const DevGraph& g, const BatchArgs& a, int gi, doubl
   __syncthreads();
 }
 
-template <int MIXED, int G, int NT>
-__global__ void __launch_bounds__(NT, 1) k_batch_lm(DevGraph g, BatchArgs a) {
+template <int MIXED, int G, int NT, int BPS>
+__global__ void __launch_bounds__(NT, BPS) k_batch_lm(DevGraph g, BatchArgs a) {
   __shared__ double sh[(NT / 32) * 2 + 8];
   __shared__ int s_next;
   extern __shared__ double dense[];   // multigrid: the coarsest inverse of the current graph
@@ -506,16 +506,21 @@ __global__ void k_batch_reset(DevGraph g, BatchArgs a) {
   if (threadIdx.x == 0) a.gst[gi].cur = 0;
 }
 
+// (mixed, lanes per block row, threads per block, blocks per SM): two blocks
+// per SM solve two graphs side by side on one SM (more warps to hide the
+// latency of the block-level phases, half the registers per thread).
 #define PGO_BATCH_SCHEDULES(X) \
-  X(0, 4, 256) X(0, 8, 256) X(0, 16, 256) X(0, 8, 512) X(0, 16, 512) \
-  X(1, 4, 256) X(1, 8, 256) X(1, 16, 256) X(1, 8, 512) X(1, 16, 512)
+  X(0, 4, 256, 1) X(0, 8, 256, 1) X(0, 16, 256, 1) X(0, 8, 512, 1) X(0, 16, 512, 1) \
+  X(0, 4, 256, 2) X(0, 8, 256, 2) X(0, 16, 256, 2) \
+  X(1, 4, 256, 1) X(1, 8, 256, 1) X(1, 16, 256, 1) X(1, 8, 512, 1) X(1, 16, 512, 1) \
+  X(1, 4, 256, 2) X(1, 8, 256, 2) X(1, 16, 256, 2)
 
 struct BatchSchedule {
-  int mixed, lanes, threads;
+  int mixed, lanes, threads, blocks_per_sm;
 };
 
 static const BatchSchedule kSchedules[] = {
-#define PGO_S(M, G, NT) {M, G, NT},
+#define PGO_S(M, G, NT, B) {M, G, NT, B},
     PGO_BATCH_SCHEDULES(PGO_S)
 #undef PGO_S
 };
@@ -524,6 +529,7 @@ int batch_schedule_count() { return (int)(sizeof(kSchedules) / sizeof(kSchedules
 int batch_schedule_mixed(int s) { return kSchedules[s].mixed; }
 int batch_schedule_lanes(int s) { return kSchedules[s].lanes; }
 int batch_schedule_threads(int s) { return kSchedules[s].threads; }
+int batch_schedule_blocks_per_sm(int s) { return kSchedules[s].blocks_per_sm; }
 
 cudaError_t launch_batch_lm(const DevGraph& g, const BatchArgs& a, int schedule, cudaStream_t s) {
   static int sms = 0;
@@ -532,16 +538,18 @@ cudaError_t launch_batch_lm(const DevGraph& g, const BatchArgs& a, int schedule,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   }
-  const int blocks = a.n_graphs < sms ? a.n_graphs : sms;
-  // explicit dispatch in list order
-  int idx = 0;
+  if (schedule < 0 || schedule >= batch_schedule_count()) return cudaErrorInvalidValue;
+  const int slots = sms * kSchedules[schedule].blocks_per_sm;
+  const int blocks = a.n_graphs < slots ? a.n_graphs : slots;
   const size_t n7 = 7 * AMG_CMAX;
   const size_t smem = a.amg ? (n7 * n7 + n7) * sizeof(double) : 0;
-#define PGO_D(M, G, NT)                                   \
-  if (schedule == idx) {                                  \
-    k_batch_lm<M, G, NT><<<blocks, NT, smem, s>>>(g, a);  \
-    return cudaGetLastError();                            \
-  }                                                       \
+  // explicit dispatch in list order
+  int idx = 0;
+#define PGO_D(M, G, NT, B)                                   \
+  if (schedule == idx) {                                     \
+    k_batch_lm<M, G, NT, B><<<blocks, NT, smem, s>>>(g, a);  \
+    return cudaGetLastError();                               \
+  }                                                          \
   ++idx;
   PGO_BATCH_SCHEDULES(PGO_D)
 #undef PGO_D

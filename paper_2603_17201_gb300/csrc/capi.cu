@@ -1425,11 +1425,13 @@ pgo_status pgo_batch_solve(pgo_batch* B, const pgo_solve_options* opt, pgo_repor
   return PGO_OK;
 }
 
-pgo_status pgo_batch_schedule(const pgo_batch* B, int32_t* lanes, int32_t* threads, float* tune_ms) {
+pgo_status pgo_batch_schedule(const pgo_batch* B, int32_t* lanes, int32_t* threads, int32_t* blocks_per_sm,
+                              float* tune_ms) {
   if (!B) return fail(PGO_ERR_INVALID_ARG, "batch is NULL");
   if (B->schedule < 0) return fail(PGO_ERR_STATE, "no batch solve has run");
   if (lanes) *lanes = batch_schedule_lanes(B->schedule);
   if (threads) *threads = batch_schedule_threads(B->schedule);
+  if (blocks_per_sm) *blocks_per_sm = batch_schedule_blocks_per_sm(B->schedule);
   if (tune_ms) *tune_ms = B->tune_ms[batch_schedule_mixed(B->schedule) + 2 * (B->schedule_amg ? 1 : 0)];
   return PGO_OK;
 }

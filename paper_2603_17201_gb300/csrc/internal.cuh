@@ -187,6 +187,7 @@ int batch_schedule_count();
 int batch_schedule_mixed(int s);
 int batch_schedule_lanes(int s);
 int batch_schedule_threads(int s);
+int batch_schedule_blocks_per_sm(int s);
 cudaError_t launch_batch_lm(const DevGraph& g, const BatchArgs& a, int schedule, cudaStream_t s);
 void launch_batch_get_poses(const DevGraph& g, const BatchArgs& a, double* dst, cudaStream_t s);
 void launch_batch_reset(const DevGraph& g, const BatchArgs& a, cudaStream_t s);

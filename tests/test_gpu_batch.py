@@ -39,8 +39,8 @@ def test_batch_matches_oracle_per_graph(precision, tol, precond):
     gs = uneven_batch()
     b = PoseGraphBatch(gs)
     reps, poses = b.solve(max_iters=20, precision=precision, preconditioner=precond)
-    lanes, threads, _ = b.schedule()
-    assert lanes in (4, 8, 16) and threads in (256, 512)
+    lanes, threads, bps, _ = b.schedule()
+    assert lanes in (4, 8, 16) and threads in (256, 512) and bps in (1, 2)
     for g, rep, p in zip(gs, reps, poses):
         og = O.OracleGraph(g.n_vertices, g.edge_i, g.edge_j, g.meas, None, None, g.fixed_vertex)
         p_ref, ref = og.lm(g.poses_init, max_iters=20)
@@ -52,7 +52,7 @@ def test_batch_matches_oracle_per_graph(precision, tol, precond):
         assert np.array_equal(p[f, 4:], g.poses_init[f, 4:])
 
 
-@pytest.mark.parametrize("schedule", list(range(5)))
+@pytest.mark.parametrize("schedule", list(range(8)))
 def test_every_fp64_schedule_agrees(schedule):
     from paper_2603_17201_gb300 import PoseGraphBatch
     gs = uneven_batch(6, seed0=80)
