@@ -1,4 +1,4 @@
-// K6: implicit-adjoint gradients of the optimised poses x*(Z, w).
+// Implicit-adjoint gradients of the optimised poses x*(Z, w).
 //
 // At the optimum the gradient b(x*, Z, w) = sum_e w_e A_e^T Omega_e r_e is
 // zero.  Differentiating that identity gives dx*/dtheta = -H^-1 db/dtheta with

@@ -172,70 +172,6 @@ __device__ __forceinline__ void adj7(const Sim3T<double>& S, double (&A)[7][7]) 
   A[6][6] = 1.0;
 }
 
-// Inverse of a symmetric positive definite 7x7 block (Cholesky, in double);
-// returns false (and writes the inverse of the diagonal) if a pivot is not
-// positive.
-template <class V>
-__device__ __forceinline__ bool inv7_spd(const V* B, V* out) {
-  double A[7][7];
-#pragma unroll
-  for (int a = 0; a < 7; ++a)
-#pragma unroll
-    for (int c = 0; c < 7; ++c) A[a][c] = 0.5 * ((double)B[a * 7 + c] + (double)B[c * 7 + a]);
-  bool ok = true;
-#pragma unroll
-  for (int j = 0; j < 7; ++j) {
-    double d = A[j][j];
-#pragma unroll
-    for (int k = 0; k < j; ++k) d -= A[j][k] * A[j][k];
-    ok = ok && (d > 0.0);
-    d = sqrt(fmax(d, 1e-300));
-    A[j][j] = d;
-#pragma unroll
-    for (int i = j + 1; i < 7; ++i) {
-      double s = A[i][j];
-#pragma unroll
-      for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
-      A[i][j] = s / d;
-    }
-  }
-  if (!ok) {
-#pragma unroll
-    for (int a = 0; a < 7; ++a)
-#pragma unroll
-      for (int c = 0; c < 7; ++c) {
-        const double dd = (double)B[a * 8];
-        out[a * 7 + c] = (a == c && dd > 0.0) ? V(1.0 / dd) : V(0);
-      }
-    return false;
-  }
-  // L^-1 (lower), then inv = L^-T L^-1
-  double Li[7][7];
-#pragma unroll
-  for (int c = 0; c < 7; ++c) {
-#pragma unroll
-    for (int i = 0; i < 7; ++i) {
-      if (i < c) { Li[i][c] = 0.0; continue; }
-      double s = (i == c) ? 1.0 : 0.0;
-#pragma unroll
-      for (int k = 0; k < i; ++k)
-        if (k >= c) s -= A[i][k] * Li[k][c];
-      Li[i][c] = s / A[i][i];
-    }
-  }
-#pragma unroll
-  for (int a = 0; a < 7; ++a)
-#pragma unroll
-    for (int c = 0; c < 7; ++c) {
-      double s = 0.0;
-#pragma unroll
-      for (int k = 0; k < 7; ++k)
-        if (k >= a && k >= c) s += Li[k][a] * Li[k][c];
-      out[a * 7 + c] = V(s);
-    }
-  return true;
-}
-
 // Inverse of the SPD 7x7 block `src` into `dst` by a team of 64 threads of a
 // block (thread t < 49 owns entry (t / 7, t % 7)): Gauss-Jordan without
 // pivoting in the team's shared scratch M (50 doubles; M[49] flags a

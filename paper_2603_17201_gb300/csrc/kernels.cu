@@ -1,8 +1,9 @@
 // Edge and vertex kernels of the Levenberg-Marquardt loop (Sec. IV-F):
-//   K1 k_linearize  edge residual r = log(Z S_i S_j^-1) and its exact
-//                   Jacobians (forward-mode duals through the log map),
+//   k_linearize     edge residual r = log(Z S_i S_j^-1) and its exact
+//                   Jacobians (FP64: forward-mode duals through the log map;
+//                   mixed precision: FP32 from the left-Jacobian series),
 //                   the off-diagonal block and per-edge-side contributions;
-//   K2 k_assemble   deterministic per-vertex gather of the contributions into
+//   k_assemble      deterministic per-vertex gather of the contributions into
 //                   the diagonal blocks H_vv and the gradient b_v;
 //   k_cost          F = sum w r^T Omega r (FP64) and the LM accept/reject rule;
 //   k_update        candidate poses exp(delta) S and the predicted decrease.
@@ -12,7 +13,7 @@
 
 namespace pgo {
 
-// K1: one thread per edge (MIXED: FP32 Jacobians and H products).
+// Linearisation: one thread per edge (MIXED: FP32 Jacobians and H products).
 template <int MIXED>
 __global__ void __launch_bounds__(128) k_linearize(DevGraph g) {
   const SolverState* st = g.st;
@@ -22,7 +23,7 @@ __global__ void __launch_bounds__(128) k_linearize(DevGraph g) {
   linearize_edge(g, st->cur, e, MIXED);
 }
 
-// K2: 8 lanes per vertex gather the incident edge-side contributions in edge
+// Assembly: 8 lanes per vertex gather the incident edge-side contributions in edge
 // order (deterministic), then write H_vv (full symmetric) and b_v.  The last
 // block derives max diag(H), |b|_inf and |b|^2 over the free vertices, sets
 // lambda_0 on the first linearisation and applies the gradient stop test.

@@ -1,20 +1,26 @@
-// K3/K4: damped linear solve (H + lambda I) delta = rhs by block-Jacobi
-// preconditioned conjugate gradients over the block-sparse normal matrix.
+// Damped linear solve (H + lambda I) delta = rhs by preconditioned conjugate
+// gradients over the block-sparse normal matrix, with the block-Jacobi
+// preconditioner or one V(1,1) cycle of the multigrid hierarchy of amg.cu.
 // (The paper's Sec. IV-F keeps an exact LDL^T on the CPU; here the solve
 // stays on the GPU, with no host round trip per iteration.)
 //
 // k_pcg is a persistent cooperative kernel: one launch runs every PCG
 // iteration of one linear solve.  One block per SM owns a contiguous range of
-// block rows; 8 lanes serve one block row and lane a (< 7) owns output
-// component a, so a 7x7 block times a 7-vector costs each lane 7 FMAs with no
-// cross-lane reduction (this matters on GB300, where every FP64 warp
-// instruction occupies the SM's FP64 pipe for ~16 cycles whatever the number
-// of active lanes).  Each stored off-diagonal block (i, j) serves row i as
-// H_ij and row j as H_ij^T; p = z + beta p_prev is formed on the fly.
-// Per iteration: SpMV + local p.q -> grid barrier -> alpha, x/r/z update +
-// local r.z, r.r -> grid barrier -> beta and the stopping test.  Every block
-// reduces the per-block partials itself in the same fixed order, so all
-// blocks take identical decisions and the result is deterministic.
+// block rows and stages their diagonal, preconditioner and off-diagonal
+// blocks in shared memory once per launch.  In the products, G lanes serve a
+// block row: each lane takes whole 7x7 blocks of the row, then the G lanes
+// sum their partial 7-vectors by shuffles (on GB300 an FP64 warp instruction
+// holds the SM sub-partition's FP64 pipe for ~64 cycles whatever the number
+// of active lanes, so lanes are kept busy with whole blocks).  Each stored
+// off-diagonal block (i, j) serves row i as H_ij and row j as H_ij^T; each
+// vertex lists its side-0 entries first, so the two products never diverge
+// within a warp; p = z + beta p_prev is formed on the fly.
+// Per iteration: SpMV + local p.q -> grid barrier -> alpha, x/r update and
+// the preconditioner (block-Jacobi: z = M r locally; multigrid: the cycle's
+// phases, each behind a grid barrier) + local r.z, r.r -> grid barrier ->
+// beta and the stopping test.  Every block reduces the per-block partials
+// itself in the same fixed order, so all blocks take identical decisions and
+// the result is deterministic.
 //
 // The grid barrier is a monotone arrival counter (release add, acquire poll)
 // with a bounded spin: on timeout the kernel records PGO_ERR_CUDA in the
@@ -53,7 +59,7 @@ struct Bufs<float> {
   static constexpr int BLK = BLK32;
 };
 
-// ---- K3: block-Jacobi preconditioner M_v = (H_vv + lambda I)^-1 ----------
+// ---- block-Jacobi preconditioner M_v = (H_vv + lambda I)^-1 ----------
 template <class V>
 __global__ void __launch_bounds__(32) k_precond(DevGraph g) {
   const SolverState* st = g.st;

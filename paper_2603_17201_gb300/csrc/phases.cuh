@@ -12,7 +12,7 @@ __device__ __forceinline__ int upk(int a, int c) { return a * 7 - (a * (a - 1)) 
 static __device__ __constant__ unsigned char c_up_a[28] = {0, 0, 0, 0, 0, 0, 0, 1, 1, 1, 1, 1, 1, 2, 2, 2, 2, 2, 3, 3, 3, 3, 4, 4, 4, 5, 5, 6};
 static __device__ __constant__ unsigned char c_up_c[28] = {0, 1, 2, 3, 4, 5, 6, 1, 2, 3, 4, 5, 6, 2, 3, 4, 5, 6, 3, 4, 5, 6, 4, 5, 6, 5, 6, 6};
 
-// K1 for one edge: residual and exact Jacobians (poses in buffer `cur`), the
+// Linearisation of one edge: residual and exact Jacobians (poses in buffer `cur`), the
 // off-diagonal (i, j) block w A_i^T A_j (FP64, and FP32 in mixed mode) and
 // the two edge-side contributions [upper(w A^T A), w A^T r].
 // Mixed precision: FP64 residual, FP32 Jacobians and H products (the
@@ -112,7 +112,7 @@ __device__ __forceinline__ void linearize_edge(const DevGraph& g, int cur, int e
   }
 }
 
-// K2 for one vertex, lane `lane` of 8: gather the incident contributions in
+// Assembly for one vertex, lane `lane` of 8: gather the incident contributions in
 // incidence order (deterministic), write H_vv (full symmetric) and b_v, and
 // fold max diag, |b|_inf and |b|^2 (free vertices only) into the arguments.
 __device__ __forceinline__ void assemble_vertex(const DevGraph& g, int v, int lane, int mixed, int fixed,
@@ -201,7 +201,7 @@ __device__ __forceinline__ double update_vertex(const DevGraph& g, int cur, int 
   return pr;
 }
 
-// K3 for one vertex: M = (H_vv + lambda I)^-1 by a 7x7 Cholesky in FP64,
+// Block-Jacobi preconditioner for one vertex: M = (H_vv + lambda I)^-1 by a 7x7 Cholesky in FP64,
 // stored as V (the inverse of the damped diagonal if the block is not
 // positive definite); M = 0 on the fixed vertex (its unknowns stay zero).
 template <class V>

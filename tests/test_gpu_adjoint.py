@@ -1,12 +1,11 @@
-"""GPU implicit adjoint (K6) against the oracle's adjoint, closed forms and
+"""GPU implicit adjoint against the oracle's adjoint, closed forms and
 brute-force finite differences of the whole solve, through the C ABI and the
 torch.autograd.Function.
 
 Tolerances: GPU vs oracle adjoint 1e-6 relative to the largest gradient (the
 oracle takes its second derivatives by central differences, the GPU by exact
 nested duals); against finite differences of the solve 1e-5 relative, per
-edge on vector norms with a floor of 1e-3 x the largest gradient (the
-spec bar)."""
+edge on vector norms with a floor of 1e-3 x the largest gradient."""
 import numpy as np
 import pytest
 
