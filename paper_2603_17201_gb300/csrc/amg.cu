@@ -25,6 +25,7 @@
 // device at every linearisation, because H, lambda and the poses change.
 #include <algorithm>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "amg.cuh"
@@ -81,29 +82,103 @@ struct NbrView {
   }
 };
 
-inline int find_col(const std::vector<int>& ptr, const std::vector<int>& col, int row, int c) {
-  const auto b = col.begin() + ptr[row], e = col.begin() + ptr[row + 1];
-  const auto it = std::lower_bound(b, e, c);
-  return (it != e && *it == c) ? (int)(it - col.begin()) : -1;
+
+// Rows [0, n) of a block-sparse product, grouped by column: gen(row, emit)
+// emits terms emit(col, x, y); each row gets its distinct columns ascending
+// (plus `diag_col(row)` when that is >= 0) and each (row, column) block its
+// terms in emission order.  Output: row pointers, columns, per-block term
+// pointers and the terms (int2 {x, y}).  Rows are split into contiguous
+// chunks over host threads and the chunks concatenated in order, so the
+// result does not depend on the thread count.
+template <class Gen, class Diag>
+void group_rows(int n, int ncols, Gen gen, Diag diag_col, std::vector<int>& row_ptr, std::vector<int>& col,
+                std::vector<int>& rec_ptr, std::vector<int2>& rec) {
+  struct Chunk {
+    std::vector<int> row_len, col, blk_len;
+    std::vector<int2> rec;
+  };
+  unsigned hw = std::thread::hardware_concurrency();
+  int T = (int)std::min<unsigned>(hw ? hw : 1, 16);
+  if (n < 512) T = 1;
+  std::vector<Chunk> ch(T);
+  auto work = [&](int t) {
+    const int r0 = (int)((long long)n * t / T), r1 = (int)((long long)n * (t + 1) / T);
+    Chunk& c = ch[t];
+    std::vector<int> slot(std::max(ncols, 1), -1), cols, cnt, fill, td;
+    std::vector<int2> tv;
+    for (int u = r0; u < r1; ++u) {
+      td.clear();
+      tv.clear();
+      gen(u, [&](int d, int x, int y) {
+        td.push_back(d);
+        tv.push_back(make_int2(x, y));
+        if (slot[d] < 0) {
+          slot[d] = 0;
+          cols.push_back(d);
+        }
+      });
+      const int dc = diag_col(u);
+      if (dc >= 0 && slot[dc] < 0) {
+        slot[dc] = 0;
+        cols.push_back(dc);
+      }
+      std::sort(cols.begin(), cols.end());
+      const int m = (int)cols.size();
+      for (int k = 0; k < m; ++k) slot[cols[k]] = k;
+      cnt.assign(m + 1, 0);
+      for (int d : td) cnt[slot[d] + 1]++;
+      for (int k = 0; k < m; ++k) cnt[k + 1] += cnt[k];
+      const size_t base = c.rec.size();
+      c.rec.resize(base + td.size());
+      fill.assign(cnt.begin(), cnt.end() - 1);
+      for (size_t q = 0; q < td.size(); ++q) c.rec[base + fill[slot[td[q]]]++] = tv[q];
+      for (int k = 0; k < m; ++k) {
+        c.col.push_back(cols[k]);
+        c.blk_len.push_back(cnt[k + 1] - cnt[k]);
+        slot[cols[k]] = -1;
+      }
+      c.row_len.push_back(m);
+      cols.clear();
+    }
+  };
+  if (T == 1) {
+    work(0);
+  } else {
+    std::vector<std::thread> th;
+    for (int t = 0; t < T; ++t) th.emplace_back(work, t);
+    for (auto& x : th) x.join();
+  }
+  row_ptr.assign(n + 1, 0);
+  col.clear();
+  rec_ptr.assign(1, 0);
+  rec.clear();
+  int u = 0;
+  for (const Chunk& c : ch) {
+    for (int len : c.row_len) {
+      row_ptr[u + 1] = row_ptr[u] + len;
+      ++u;
+    }
+    col.insert(col.end(), c.col.begin(), c.col.end());
+    for (int len : c.blk_len) rec_ptr.push_back(rec_ptr.back() + len);
+    rec.insert(rec.end(), c.rec.begin(), c.rec.end());
+  }
 }
 
 // Builds P, AP, the recipes and the pattern of the next level for `L`.
+// Recipe entries of an output block keep a fixed order: neighbours in
+// incidence order, then the blocks of their rows in column order.
 void build_level(HostLevel& L, const NbrView& nb, HostLevel& next) {
   const int n = L.n, nn = L.n_next;
-  std::vector<int> mark(std::max(nn, 1), -1), buf;
-  // ---- P pattern: the aggregates of the node and of its neighbours ----
-  L.p_ptr.assign(n + 1, 0);
-  for (int u = 0; u < n; ++u) {
-    buf.clear();
-    if (L.agg[u] >= 0) {
-      buf.push_back(L.agg[u]);
-      nb.each(u, [&](int, int w) { if (L.agg[w] >= 0) buf.push_back(L.agg[w]); });
-      std::sort(buf.begin(), buf.end());
-      buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
-    }
-    L.p_ptr[u + 1] = L.p_ptr[u] + (int)buf.size();
-    L.p_col.insert(L.p_col.end(), buf.begin(), buf.end());
-  }
+  // ---- P pattern (the aggregates of the node and of its neighbours) and R1 ----
+  group_rows(
+      n, nn,
+      [&](int u, auto emit) {
+        if (L.agg[u] < 0) return;
+        nb.each(u, [&](int a, int w) {
+          if (L.agg[w] >= 0) emit(L.agg[w], a, w);
+        });
+      },
+      [&](int u) { return L.agg[u]; }, L.p_ptr, L.p_col, L.r1_ptr, L.r1);
   const int nnz_p = L.p_ptr[n];
   L.p_row.resize(nnz_p);
   for (int u = 0; u < n; ++u)
@@ -115,139 +190,90 @@ void build_level(HostLevel& L, const NbrView& nb, HostLevel& next) {
   L.pt_row.resize(nnz_p);
   L.pt_blk.resize(nnz_p);
   {
-    std::vector<int> fill(L.pt_ptr.begin(), L.pt_ptr.end() - 1);
+    std::vector<int> f(L.pt_ptr.begin(), L.pt_ptr.end() - 1);
     for (int u = 0; u < n; ++u)
       for (int k = L.p_ptr[u]; k < L.p_ptr[u + 1]; ++k) {
-        const int a = fill[L.p_col[k]]++;
-        L.pt_row[a] = u;
-        L.pt_blk[a] = k;
+        const int x = f[L.p_col[k]]++;
+        L.pt_row[x] = u;
+        L.pt_blk[x] = k;
       }
   }
-  // ---- R1: per P block (u, c), the terms A_uw T_w with agg(w) = c ----
-  L.r1_ptr.assign(nnz_p + 1, 0);
-  for (int u = 0; u < n; ++u) {
-    const int k0 = L.p_ptr[u];
-    nb.each(u, [&](int, int w) {
-      if (L.agg[w] >= 0) L.r1_ptr[find_col(L.p_ptr, L.p_col, u, L.agg[w]) + 1]++;
-    });
-    (void)k0;
-  }
-  for (int k = 0; k < nnz_p; ++k) L.r1_ptr[k + 1] += L.r1_ptr[k];
-  L.r1.resize(L.r1_ptr[nnz_p]);
-  {
-    std::vector<int> fill(L.r1_ptr.begin(), L.r1_ptr.end() - 1);
-    for (int u = 0; u < n; ++u)
-      nb.each(u, [&](int a, int w) {
-        if (L.agg[w] < 0) return;
-        const int b = find_col(L.p_ptr, L.p_col, u, L.agg[w]);
-        L.r1[fill[b]++] = make_int2(a, w);
-      });
-  }
   // ---- AP pattern and R2: AP_ud = sum_w A_uw P_wd ----
-  L.ap_ptr.assign(n + 1, 0);
-  for (int u = 0; u < n; ++u) {
-    buf.clear();
-    if (L.agg[u] >= 0)
-      nb.each(u, [&](int, int w) {
-        for (int k = L.p_ptr[w]; k < L.p_ptr[w + 1]; ++k) buf.push_back(L.p_col[k]);
-      });
-    std::sort(buf.begin(), buf.end());
-    buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
-    L.ap_ptr[u + 1] = L.ap_ptr[u] + (int)buf.size();
-    L.ap_col.insert(L.ap_col.end(), buf.begin(), buf.end());
-  }
-  const int nnz_ap = L.ap_ptr[n];
-  L.r2_ptr.assign(nnz_ap + 1, 0);
-  for (int u = 0; u < n; ++u) {
-    if (L.agg[u] < 0) continue;
-    nb.each(u, [&](int, int w) {
-      for (int k = L.p_ptr[w]; k < L.p_ptr[w + 1]; ++k)
-        L.r2_ptr[find_col(L.ap_ptr, L.ap_col, u, L.p_col[k]) + 1]++;
-    });
-  }
-  for (int k = 0; k < nnz_ap; ++k) L.r2_ptr[k + 1] += L.r2_ptr[k];
-  L.r2.resize(L.r2_ptr[nnz_ap]);
-  {
-    std::vector<int> fill(L.r2_ptr.begin(), L.r2_ptr.end() - 1);
-    for (int u = 0; u < n; ++u) {
-      if (L.agg[u] < 0) continue;
-      nb.each(u, [&](int a, int w) {
-        for (int k = L.p_ptr[w]; k < L.p_ptr[w + 1]; ++k) {
-          const int b = find_col(L.ap_ptr, L.ap_col, u, L.p_col[k]);
-          L.r2[fill[b]++] = make_int2(a, k);
+  group_rows(
+      n, nn,
+      [&](int u, auto emit) {
+        if (L.agg[u] < 0) return;
+        nb.each(u, [&](int a, int w) {
+          for (int k = L.p_ptr[w]; k < L.p_ptr[w + 1]; ++k) emit(L.p_col[k], a, k);
+        });
+      },
+      [](int) { return -1; }, L.ap_ptr, L.ap_col, L.r2_ptr, L.r2);
+  // ---- next level: upper half of P^T A P from the products, R3 per upper block ----
+  std::vector<int> up_ptr, up_col, up_r3ptr;
+  std::vector<int2> up_r3;
+  group_rows(
+      nn, nn,
+      [&](int c, auto emit) {
+        for (int t = L.pt_ptr[c]; t < L.pt_ptr[c + 1]; ++t) {
+          const int u = L.pt_row[t], pb = L.pt_blk[t];
+          for (int k = L.ap_ptr[u]; k < L.ap_ptr[u + 1]; ++k)
+            if (L.ap_col[k] >= c) emit(L.ap_col[k], pb, k);
         }
-      });
-    }
-  }
-  // ---- next level: pattern of P^T A P (upper half from the products) ----
-  std::vector<std::vector<int>> upper(nn);
-  for (int c = 0; c < nn; ++c) {
-    buf.clear();
-    for (int t = L.pt_ptr[c]; t < L.pt_ptr[c + 1]; ++t) {
-      const int u = L.pt_row[t];
-      for (int k = L.ap_ptr[u]; k < L.ap_ptr[u + 1]; ++k)
-        if (L.ap_col[k] >= c) buf.push_back(L.ap_col[k]);
-    }
-    buf.push_back(c);
-    std::sort(buf.begin(), buf.end());
-    buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
-    upper[c] = buf;
-  }
-  std::vector<std::vector<int>> lower(nn);
+      },
+      [](int c) { return c; }, up_ptr, up_col, up_r3ptr, up_r3);
+  // lower half by transposition (rows ascending, so each row's lower columns are ascending)
+  std::vector<int> lo_ptr(nn + 1, 0);
   for (int c = 0; c < nn; ++c)
-    for (int d : upper[c])
-      if (d != c) lower[d].push_back(c);
+    for (int k = up_ptr[c] + 1; k < up_ptr[c + 1]; ++k) lo_ptr[up_col[k] + 1]++;
+  for (int c = 0; c < nn; ++c) lo_ptr[c + 1] += lo_ptr[c];
+  std::vector<int> lo_col(lo_ptr[nn]), lo_src(lo_ptr[nn]);   // lower block (d, c): source upper block of row c
+  {
+    std::vector<int> f(lo_ptr.begin(), lo_ptr.end() - 1);
+    for (int c = 0; c < nn; ++c)
+      for (int k = up_ptr[c] + 1; k < up_ptr[c + 1]; ++k) {
+        const int x = f[up_col[k]]++;
+        lo_col[x] = c;
+        lo_src[x] = k;   // upper-list index, turned into a block index below
+      }
+  }
+  // row c: the diagonal, the lower columns, then the upper columns (all ascending)
   next.a_ptr.assign(nn + 1, 0);
-  for (int c = 0; c < nn; ++c) next.a_ptr[c + 1] = next.a_ptr[c] + (int)(upper[c].size() + lower[c].size());
+  for (int c = 0; c < nn; ++c) next.a_ptr[c + 1] = next.a_ptr[c] + (up_ptr[c + 1] - up_ptr[c]) + (lo_ptr[c + 1] - lo_ptr[c]);
   const int nnz_next = next.a_ptr[nn];
   next.a_col.resize(nnz_next);
   next.a_src.assign(nnz_next, -1);
-  // row c: the diagonal, then the other columns ascending
+  std::vector<int> up_blk(up_col.size());   // upper-list index -> block index
   for (int c = 0; c < nn; ++c) {
-    int k = next.a_ptr[c];
-    next.a_col[k++] = c;
-    std::vector<int> rest;
-    for (int d : lower[c]) rest.push_back(d);
-    for (int d : upper[c])
-      if (d != c) rest.push_back(d);
-    std::sort(rest.begin(), rest.end());
-    for (int d : rest) next.a_col[k++] = d;
+    int b = next.a_ptr[c];
+    up_blk[up_ptr[c]] = b;
+    next.a_col[b++] = c;
+    b += lo_ptr[c + 1] - lo_ptr[c];
+    for (int k = up_ptr[c] + 1; k < up_ptr[c + 1]; ++k) {
+      up_blk[k] = b;
+      next.a_col[b++] = up_col[k];
+    }
   }
-  auto blk_of = [&](int c, int d) {
-    if (c == d) return next.a_ptr[c];
-    for (int k = next.a_ptr[c] + 1; k < next.a_ptr[c + 1]; ++k)
-      if (next.a_col[k] == d) return k;
-    return -1;
-  };
-  for (int c = 0; c < nn; ++c)
-    for (int k = next.a_ptr[c] + 1; k < next.a_ptr[c + 1]; ++k)
-      if (next.a_col[k] < c) next.a_src[k] = blk_of(next.a_col[k], c);
-  // R3 per upper block (c, d >= c): (P block (u, c), AP block (u, d))
+  for (int c = 0; c < nn; ++c) {
+    int b = next.a_ptr[c] + 1;
+    for (int x = lo_ptr[c]; x < lo_ptr[c + 1]; ++x, ++b) {
+      next.a_col[b] = lo_col[x];
+      next.a_src[b] = up_blk[lo_src[x]];
+    }
+  }
+  // R3 per block of the next level: upper blocks carry their entries, lower blocks none
   L.r3_ptr.assign(nnz_next + 1, 0);
-  std::vector<int> pos(std::max(nn, 1), -1);
-  for (int pass = 0; pass < 2; ++pass) {
-    std::vector<int> fill;
-    if (pass == 1) {
-      for (int k = 0; k < nnz_next; ++k) L.r3_ptr[k + 1] += L.r3_ptr[k];
-      L.r3.resize(L.r3_ptr[nnz_next]);
-      fill.assign(L.r3_ptr.begin(), L.r3_ptr.end() - 1);
-    }
-    for (int c = 0; c < nn; ++c) {
-      for (int k = next.a_ptr[c]; k < next.a_ptr[c + 1]; ++k) pos[next.a_col[k]] = k;
-      for (int t = L.pt_ptr[c]; t < L.pt_ptr[c + 1]; ++t) {
-        const int u = L.pt_row[t], pb = L.pt_blk[t];
-        for (int k = L.ap_ptr[u]; k < L.ap_ptr[u + 1]; ++k) {
-          const int d = L.ap_col[k];
-          if (d < c) continue;
-          const int b = pos[d];
-          if (pass == 0) L.r3_ptr[b + 1]++;
-          else L.r3[fill[b]++] = make_int2(pb, k);
-        }
+  L.r3.clear();
+  L.r3.reserve(up_r3.size());
+  for (int c = 0; c < nn; ++c) {
+    int k = up_ptr[c];
+    for (int b = next.a_ptr[c]; b < next.a_ptr[c + 1]; ++b) {
+      if (next.a_src[b] < 0) {
+        for (int e = up_r3ptr[k]; e < up_r3ptr[k + 1]; ++e) L.r3.push_back(up_r3[e]);
+        ++k;
       }
-      for (int k = next.a_ptr[c]; k < next.a_ptr[c + 1]; ++k) pos[next.a_col[k]] = -1;
+      L.r3_ptr[b + 1] = (int)L.r3.size();
     }
   }
-  (void)mark;
 }
 
 struct Uploader {
