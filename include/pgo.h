@@ -116,6 +116,9 @@ typedef struct {
                              before pgo_backward) */
   int32_t schedule;       /* kernel schedule id; -1 = library default */
   int32_t preconditioner; /* pgo_preconditioner (PGO_PRECOND_MULTIGRID) */
+  int32_t multigrid_refresh; /* multigrid inside LM: rebuild the coarse levels
+                             at every k-th linearisation, refresh only the
+                             finest level in between (1 = always rebuild) */
 } pgo_solve_options;
 
 /* Solve report. */

@@ -55,7 +55,7 @@ class SolveOptions(ctypes.Structure):
                 ("lambda_init", c_double), ("ftol", c_double), ("gtol", c_double),
                 ("pcg_tol", c_double), ("pcg_max_iters", c_int32), ("refine_steps", c_int32),
                 ("refine_tol", c_double), ("polish_iters", c_int32), ("schedule", c_int32),
-                ("preconditioner", c_int32)]
+                ("preconditioner", c_int32), ("multigrid_refresh", c_int32)]
 
 
 class Report(ctypes.Structure):

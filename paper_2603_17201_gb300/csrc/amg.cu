@@ -619,8 +619,13 @@ __device__ double power_step(const DevGraph& g, const AmgLevel& Lv, int l, V lam
   return nrm;
 }
 
+// lm: the set-up of an LM iteration.  With DevOptions::amg_refresh = k > 1,
+// only every k-th such set-up rebuilds the coarse levels; the others refresh
+// the finest level (its smoothing weight, P and A P) and keep the coarse
+// levels and the coarsest inverse of the last complete set-up, which stay
+// consistent among themselves, so the cycle stays symmetric positive definite.
 template <class V>
-__global__ void __launch_bounds__(256) k_amg_setup(DevGraph g) {
+__global__ void __launch_bounds__(256) k_amg_setup(DevGraph g, int lm) {
   SolverState* st = g.st;
   if (st->done) return;
   // the hierarchy descriptor, cached in shared memory
@@ -641,6 +646,8 @@ __global__ void __launch_bounds__(256) k_amg_setup(DevGraph g) {
   const int cur = st->cur;
   const int warm_slot = sizeof(V) == sizeof(double) ? 0 : 1;
   const bool warm = __ldcg(g.amg->warm + warm_slot) != 0;
+  const int refresh = g.opt->amg_refresh;
+  const bool lagged = lm && warm && refresh > 1 && (st->it % refresh) != 0;
   double* partial = g.partial;
   __shared__ V sacc[4][49];
   __shared__ double smat[4][50];   // D^-1 teams
@@ -651,7 +658,7 @@ __global__ void __launch_bounds__(256) k_amg_setup(DevGraph g) {
   // ---- tentative prolongation blocks T = Adj(S_ref S_refc^-1), all levels ----
   {
     int base = 0;
-    for (int l = 0; l < A.L; ++l) {
+    for (int l = 0; l < (lagged ? 1 : A.L); ++l) {
       const AmgLevel& Lv = A.lv[l];
       for (int u = gtid; u < Lv.n; u += gthreads) {
         if (__ldg(Lv.agg + u) < 0) continue;
@@ -672,7 +679,7 @@ __global__ void __launch_bounds__(256) k_amg_setup(DevGraph g) {
   }
   if (!grid_sync(counter, abort_flag, target)) goto timeout;
 
-  for (int l = 0; l < A.L; ++l) {
+  for (int l = 0; l < (lagged ? 1 : A.L); ++l) {
     const AmgLevel& Lv = A.lv[l];
     const AmgLevel& Ln = A.lv[l + 1];
     // ---- rho(D^-1 A) by power iteration ----
@@ -762,6 +769,7 @@ __global__ void __launch_bounds__(256) k_amg_setup(DevGraph g) {
       }
     }
     if (!grid_sync(counter, abort_flag, target)) goto timeout;
+    if (lagged) break;   // the coarse levels of the last complete set-up stay
     // ---- A_next = P^T (A P), upper blocks ----
     {
       const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
@@ -803,7 +811,7 @@ __global__ void __launch_bounds__(256) k_amg_setup(DevGraph g) {
     }
   }
   // ---- coarsest level: dense inverse (block 0, Gauss-Jordan on the SPD matrix) ----
-  if (blockIdx.x == 0) {
+  if (blockIdx.x == 0 && !lagged) {
     const AmgLevel& Lc = A.lv[A.L];
     const int nL = Lc.n, n7 = 7 * nL;
     const V* Ab = AV<V>::a(Lc);
@@ -872,7 +880,7 @@ static int amg_sms() {
   return sms;
 }
 
-cudaError_t launch_amg_setup(const DevGraph& g, const AmgDev& amg, int mixed, cudaStream_t s) {
+cudaError_t launch_amg_setup(const DevGraph& g, const AmgDev& amg, int mixed, int lm, cudaStream_t s) {
   const int blocks = amg_sms();
   const size_t n7 = (size_t)7 * amg.nL;
   const size_t smem = (n7 * n7 + n7) * sizeof(double);
@@ -889,11 +897,11 @@ cudaError_t launch_amg_setup(const DevGraph& g, const AmgDev& amg, int mixed, cu
   if (mixed) {
     cudaError_t e = cudaFuncSetAttribute(k_amg_setup<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    return cudaLaunchKernelEx(&cfg, k_amg_setup<float>, g);
+    return cudaLaunchKernelEx(&cfg, k_amg_setup<float>, g, lm);
   }
   cudaError_t e = cudaFuncSetAttribute(k_amg_setup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaLaunchKernelEx(&cfg, k_amg_setup<double>, g);
+  return cudaLaunchKernelEx(&cfg, k_amg_setup<double>, g, lm);
 }
 
 }  // namespace pgo

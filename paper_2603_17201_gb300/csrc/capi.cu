@@ -175,6 +175,7 @@ void fill_dev_options(const pgo_solve_options& o, DevOptions* d) {
   d->pcg_tol = o.pcg_tol;
   d->refine_tol = o.refine_tol;
   d->lambda_fixed = 0.0;
+  d->amg_refresh = o.multigrid_refresh;
 }
 
 pgo_status check_options(const pgo_solve_options& o) {
@@ -186,6 +187,7 @@ pgo_status check_options(const pgo_solve_options& o) {
     return fail(PGO_ERR_INVALID_ARG, "options: tau, pcg_tol, refine_tol must be > 0");
   if (o.preconditioner != PGO_PRECOND_BLOCK_JACOBI && o.preconditioner != PGO_PRECOND_MULTIGRID)
     return fail(PGO_ERR_INVALID_ARG, "options: unknown preconditioner %d", o.preconditioner);
+  if (o.multigrid_refresh < 1) return fail(PGO_ERR_INVALID_ARG, "options: multigrid_refresh must be >= 1");
   return PGO_OK;
 }
 
@@ -197,10 +199,10 @@ void enqueue_pcg(const DevGraph& g, int mixed, const AmgDev* amg, int from_resid
   if (e != cudaSuccess && *err == cudaSuccess) *err = e;
 }
 
-void enqueue_precond(const DevGraph& g, int mixed, const AmgDev* amg, cudaStream_t s, cudaError_t* err) {
+void enqueue_precond(const DevGraph& g, int mixed, const AmgDev* amg, cudaStream_t s, cudaError_t* err, int lm = 0) {
   launch_precond(g, mixed, s);
   if (amg) {
-    cudaError_t e = launch_amg_setup(g, *amg, mixed, s);
+    cudaError_t e = launch_amg_setup(g, *amg, mixed, lm, s);
     if (e != cudaSuccess && *err == cudaSuccess) *err = e;
   }
 }
@@ -211,8 +213,8 @@ void enqueue_precond(const DevGraph& g, int mixed, const AmgDev* amg, cudaStream
 // iterative refinement (refine_steps passes, each skipped on the device once
 // the FP64 residual meets pcg_tol).
 void enqueue_linear_solve(const DevGraph& g, int mixed, int refine_steps, const AmgDev* amg, cudaStream_t s,
-                          cudaError_t* err) {
-  enqueue_precond(g, mixed, amg, s, err);
+                          cudaError_t* err, int lm = 0) {
+  enqueue_precond(g, mixed, amg, s, err, lm);
   if (!mixed) {
     enqueue_pcg(g, 0, amg, 0, s, err);
     return;
@@ -229,7 +231,7 @@ void enqueue_lm_body(const DevGraph& g, int mixed, int refine_steps, const AmgDe
                      unsigned long long lm_cond, cudaError_t* err) {
   launch_linearize(g, mixed, s);
   launch_assemble(g, mixed, s);
-  enqueue_linear_solve(g, mixed, refine_steps, amg, s, err);
+  enqueue_linear_solve(g, mixed, refine_steps, amg, s, err, 1);
   launch_update(g, mixed, s);
   launch_cost(g, 1, s, lm_cond);
 }
@@ -439,6 +441,7 @@ pgo_status pgo_default_options(pgo_solve_options* opt) {
   opt->polish_iters = 0;
   opt->schedule = -1;
   opt->preconditioner = PGO_PRECOND_MULTIGRID;
+  opt->multigrid_refresh = 1;
   return PGO_OK;
 }
 

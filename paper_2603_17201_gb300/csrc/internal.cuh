@@ -49,6 +49,7 @@ struct DevOptions {
   int max_iters, precision, pcg_max_iters, refine_steps, polish_iters;
   double tau, lambda_init, ftol, gtol, pcg_tol, refine_tol;
   double lambda_fixed;   // lambda of a standalone re-solve
+  int amg_refresh;       // rebuild the coarse multigrid levels every k-th LM linearisation
 };
 
 // ---- smoothed-aggregation multigrid preconditioner ----
@@ -215,7 +216,9 @@ void launch_scale_x(const DevGraph& g, double f, cudaStream_t s);
 void launch_precond(const DevGraph& g, int mixed, cudaStream_t s);
 // amg: host copy of the hierarchy (nullptr: block-Jacobi preconditioner)
 cudaError_t launch_pcg(const DevGraph& g, int mixed, int from_residual, const AmgDev* amg, cudaStream_t s);
-cudaError_t launch_amg_setup(const DevGraph& g, const AmgDev& amg, int mixed, cudaStream_t s);
+// lm: the set-up of an LM iteration (may keep the coarse levels, see
+// DevOptions::amg_refresh); 0: a standalone solve (always complete)
+cudaError_t launch_amg_setup(const DevGraph& g, const AmgDev& amg, int mixed, int lm, cudaStream_t s);
 // Symbolic multigrid hierarchy of a graph (host analysis + one device
 // allocation); returns the host copy of the device descriptor.
 struct AmgHost;

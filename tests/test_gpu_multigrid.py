@@ -108,3 +108,19 @@ def test_lm_and_resolve_with_both_preconditioners_agree():
         out[pc + "_resolve"] = d
     assert rel(out["multigrid_resolve"], out["block_jacobi_resolve"]) <= 1e-6
     assert out["multigrid"] < out["block_jacobi"]
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_lagged_coarse_levels_reach_the_same_optimum(precision):
+    """multigrid_refresh > 1 keeps the coarse levels of the last complete
+    set-up between rebuilds: a different (still symmetric positive definite)
+    preconditioner, the same LM optimum."""
+    g = syn.make_graph("figure8", 400, seed=31, window=10, n_loops=2, meas_noise=True, loop_min_gap=150,
+                       loop_max_dist=3.0)
+    og, pg = pair(g)
+    _, ref = og.lm(g.poses_init, max_iters=20)
+    for refresh in (1, 3):
+        pg.set_poses(g.poses_init)
+        rep = pg.solve(max_iters=20, precision=precision, multigrid_refresh=refresh)
+        tol = 1e-9 if precision == "fp64" else 1e-6
+        assert abs(rep["final_cost"] - ref["final_cost"]) <= tol * ref["final_cost"], (refresh, rep, ref)
