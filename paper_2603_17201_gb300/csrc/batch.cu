@@ -404,7 +404,11 @@ __device__ void solve_graph(const DevGraph& g, const BatchArgs& a, int gi, doubl
       for (int pass = 0; pass < o->refine_steps; ++pass) {
         const double rr = cta_refine_residual(g, v0, v1, fixed, lambda, pass == 0, sh);
         if (pass > 0 && !(rr > o->pcg_tol * o->pcg_tol * bnorm2)) break;
-        pcg_total += cta_pcg<float, G>(g, v0, v1, fixed, lambda, 1, o->refine_tol, o->pcg_max_iters, sh, A, gi);
+        // inner tolerance: only as tight as |res - H dx| <= pcg_tol |b| needs
+        double itol = o->refine_tol;
+        if (rr > 0.0 && bnorm2 > 0.0) itol = fmax(itol, o->pcg_tol * sqrt(bnorm2 / rr));
+        itol = fmin(itol, 0.5);
+        pcg_total += cta_pcg<float, G>(g, v0, v1, fixed, lambda, 1, itol, o->pcg_max_iters, sh, A, gi);
         for (int t = v0 * VEC + threadIdx.x; t < v1 * VEC; t += blockDim.x) g.dx64[t] += (double)g.x32[t];
         __syncthreads();
       }

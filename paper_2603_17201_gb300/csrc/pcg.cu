@@ -656,7 +656,16 @@ __global__ void __launch_bounds__(512) k_pcg(DevGraph g, PcgArgs a) {
   V* z = Bufs<V>::z(g);
   V* q = Bufs<V>::q(g);
   const V lam = V(st->lambda);
-  const double tol = a.inner ? o->refine_tol : o->pcg_tol;
+  // inner solve of the mixed refinement: relative to its own right-hand side
+  // (the FP64 residual res), only as tight as the outer target needs,
+  // |res - H dx| <= pcg_tol |b|, and never looser than refine_tol demands
+  double tol = o->pcg_tol;
+  if (a.inner) {
+    tol = o->refine_tol;
+    if (a.from_residual && st->ref_rr > 0.0 && st->bnorm2 > 0.0)
+      tol = fmax(tol, o->pcg_tol * sqrt(st->bnorm2 / st->ref_rr));
+    tol = fmin(tol, 0.5);
+  }
   const int maxit = o->pcg_max_iters;
 
   // ---- stage the block's operator in shared memory ----
