@@ -1,0 +1,53 @@
+"""Host logic of bench.py without a GPU: the job time as the maximum over
+ranks with two gloo processes on the CPU (the N > 1 replicas path), the
+whole-job aggregation of replicas and the kernel-launch count of a solve."""
+import os
+import socket
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+torch = pytest.importorskip("torch")
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE="2")
+    sys.path.insert(0, ROOT)
+    import torch.distributed as dist
+
+    import bench
+    dist.init_process_group("gloo", rank=rank, world_size=2)
+    out[rank] = bench.max_over_ranks(10.0 + 5.0 * rank, 2, "cpu")
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_max_over_ranks_with_two_gloo_ranks():
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        out = mgr.dict()
+        mp.spawn(_worker, args=(_free_port(), out), nprocs=2, join=True)
+        assert out[0] == 15.0 and out[1] == 15.0
+
+
+def test_aggregate_replicas_and_launch_count():
+    import bench
+    one = bench.aggregate_replicas(1, 1000, [10, 10], 200.0, 2)
+    two = bench.aggregate_replicas(2, 1000, [10, 10], 200.0, 2)
+    assert one["ms_per_solve"] == 100.0 and one["edges_per_s"] == 1000 * 20 / 0.2
+    assert two["edges_per_s"] == 2 * one["edges_per_s"]   # weak scaling: twice the work in the same time
+    assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
+    assert bench.launches_per_solve("fp64", 11) == 3 + 11 * 7
+    assert bench.launches_per_solve("mixed", 11) == 3 + 11 * 12
