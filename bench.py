@@ -37,7 +37,7 @@ UNIT = "edges/s"
 # DRAM bytes (read + write) of one PCG iteration of the roofline kernel from an
 # ncu capture of `bench.py --roofline-only`; None whenever the kernel has
 # changed since the counters were taken.
-TRAFFIC_PER_ITERATION = 25.595e6 / 9   # DRAM bytes of the 9-iteration roofline launch, per iteration
+TRAFFIC_PER_ITERATION = None
 
 
 def parse():
@@ -163,19 +163,25 @@ def measured_peaks():
 
 def vcycle_pcg_bytes_per_iter(info, n_vertices, n_edges, value_bytes):
     """Algorithmic bytes of one PCG iteration preconditioned by the V(1,1)
-    multigrid cycle (see the design notes).  Level 0: the stored operator
-    (one block per edge plus the diagonal blocks) read twice (the CG product
-    and the cycle's residual), D^-1 twice (pre- and post-smoothing), P twice
-    (restriction, prolongation), A P once, and 18 passes over 7-vectors (11 of
-    the CG, 7 of the cycle).  Each coarser smoothing level: its operator
-    once, P twice, A P once, D^-1 twice and 8 vector passes.  The coarsest
-    level: its dense inverse once and 2 vector passes."""
+    multigrid cycle (see the design notes).  The cycle applies, per level l,
+    the smoothed prolongation Q_l = (I - w D^-1 A) P_l (stored in the pattern
+    of A P) on the way down (restriction) and up, and on level L - 1 the dense
+    W = Q C^-1 Q^T.  Level 0: the stored operator (one block per edge plus the
+    diagonal blocks) read twice (the CG product and the cycle's residual),
+    D^-1 twice (pre- and post-smoothing), Q twice, and 18 passes over
+    7-vectors (11 of the CG, 7 of the cycle).  Each further sparse level: its
+    operator once, Q twice, D^-1 twice and 8 vector passes.  Level L - 1: its
+    operator once, D^-1 twice, W once and 6 vector passes."""
     blk, vec = 49 * value_bytes, 7 * value_bytes
     N, E, L = n_vertices, n_edges, len(info) - 1
-    b = (2 * (E + N) + 2 * N + 2 * info[0]["p_blocks"] + info[0]["ap_blocks"]) * blk + 18 * N * vec
-    for lv in info[1:L]:
-        b += (lv["a_blocks"] + 2 * lv["p_blocks"] + lv["ap_blocks"] + 2 * lv["nodes"]) * blk + 8 * lv["nodes"] * vec
-    b += info[L]["nodes"] ** 2 * blk + 2 * info[L]["nodes"] * vec
+    d = L - 1
+    if d == 0:
+        return (2 * (E + N) + 2 * N + N * N) * blk + 18 * N * vec
+    b = (2 * (E + N) + 2 * N + 2 * info[0]["ap_blocks"]) * blk + 18 * N * vec
+    for lv in info[1:d]:
+        b += (lv["a_blocks"] + 2 * lv["ap_blocks"] + 2 * lv["nodes"]) * blk + 8 * lv["nodes"] * vec
+    nd = info[d]["nodes"]
+    b += (info[d]["a_blocks"] + 2 * nd + nd * nd) * blk + 6 * nd * vec
     return b
 
 

@@ -53,6 +53,7 @@ struct HostLevel {
   std::vector<int> a_ptr, a_col, a_src;     // levels >= 1
   std::vector<int> p_ptr, p_col, p_row, pt_ptr, pt_row, pt_blk;
   std::vector<int> ap_ptr, ap_col;
+  std::vector<int> ap_row, ap_pblk, apt_ptr, apt_row, apt_blk;   // single-graph hierarchies
   std::vector<int> r1_ptr, r2_ptr, r3_ptr;
   std::vector<int2> r1, r2, r3;
 };
@@ -167,7 +168,7 @@ void group_rows(int n, int ncols, Gen gen, Diag diag_col, std::vector<int>& row_
 // Builds P, AP, the recipes and the pattern of the next level for `L`.
 // Recipe entries of an output block keep a fixed order: neighbours in
 // incidence order, then the blocks of their rows in column order.
-void build_level(HostLevel& L, const NbrView& nb, HostLevel& next) {
+void build_level(HostLevel& L, const NbrView& nb, HostLevel& next, bool dense) {
   const int n = L.n, nn = L.n_next;
   // ---- P pattern (the aggregates of the node and of its neighbours) and R1 ----
   group_rows(
@@ -208,6 +209,34 @@ void build_level(HostLevel& L, const NbrView& nb, HostLevel& next) {
         });
       },
       [](int) { return -1; }, L.ap_ptr, L.ap_col, L.r2_ptr, L.r2);
+  if (dense) {
+    // Q = (I - D^-1 A / rho) P lives in the pattern of A P, which contains
+    // that of P (A has every diagonal block): the row of each block, the P
+    // block at the same place (both rows have ascending columns), the CSC
+    const int nnz_ap = L.ap_ptr[n];
+    L.ap_row.resize(nnz_ap);
+    L.ap_pblk.assign(nnz_ap, -1);
+    for (int u = 0; u < n; ++u) {
+      int kp = L.p_ptr[u];
+      for (int k = L.ap_ptr[u]; k < L.ap_ptr[u + 1]; ++k) {
+        L.ap_row[k] = u;
+        while (kp < L.p_ptr[u + 1] && L.p_col[kp] < L.ap_col[k]) ++kp;
+        if (kp < L.p_ptr[u + 1] && L.p_col[kp] == L.ap_col[k]) L.ap_pblk[k] = kp;
+      }
+    }
+    L.apt_ptr.assign(nn + 1, 0);
+    for (int k = 0; k < nnz_ap; ++k) L.apt_ptr[L.ap_col[k] + 1]++;
+    for (int c = 0; c < nn; ++c) L.apt_ptr[c + 1] += L.apt_ptr[c];
+    L.apt_row.resize(nnz_ap);
+    L.apt_blk.resize(nnz_ap);
+    std::vector<int> f(L.apt_ptr.begin(), L.apt_ptr.end() - 1);
+    for (int u = 0; u < n; ++u)
+      for (int k = L.ap_ptr[u]; k < L.ap_ptr[u + 1]; ++k) {
+        const int x = f[L.ap_col[k]]++;
+        L.apt_row[x] = u;
+        L.apt_blk[x] = k;
+      }
+  }
   // ---- next level: upper half of P^T A P from the products, R3 per upper block ----
   std::vector<int> up_ptr, up_col, up_r3ptr;
   std::vector<int2> up_r3;
@@ -355,6 +384,15 @@ void layout(Uploader& U, std::vector<HostLevel>& H, int L, int N, const std::vec
       a.ap_col = U.put(h.ap_col);
       a.ap64 = U.take<double>((size_t)std::max(a.nnz_ap, 1) * BLK64);
       a.ap32 = U.take<float>((size_t)std::max(a.nnz_ap, 1) * BLK32);
+      if (nseg == 1) {
+        a.ap_row = U.put(h.ap_row);
+        a.ap_pblk = U.put(h.ap_pblk);
+        a.apt_ptr = U.put(h.apt_ptr);
+        a.apt_row = U.put(h.apt_row);
+        a.apt_blk = U.put(h.apt_blk);
+        a.q64 = U.take<double>((size_t)std::max(a.nnz_ap, 1) * BLK64);
+        a.q32 = U.take<float>((size_t)std::max(a.nnz_ap, 1) * BLK32);
+      }
       a.r1_ptr = U.put(h.r1_ptr);
       a.r1 = U.put(h.r1);
       a.r2_ptr = U.put(h.r2_ptr);
@@ -367,6 +405,14 @@ void layout(Uploader& U, std::vector<HostLevel>& H, int L, int N, const std::vec
   const size_t nl2 = nseg == 1 ? (size_t)D.nL * D.nL : (size_t)nseg * AMG_CMAX * AMG_CMAX;
   D.cinv64 = U.take<double>(std::max(nl2, (size_t)1) * BLK64);
   D.cinv32 = U.take<float>(std::max(nl2, (size_t)1) * BLK32);
+  D.dense = nseg == 1 ? 1 : 0;
+  if (D.dense) {
+    const size_t nd = (size_t)H[L - 1].n;
+    D.w64 = U.take<double>(nd * nd * BLK64);
+    D.w32 = U.take<float>(nd * nd * BLK32);
+    D.h64 = U.take<double>(nd * D.nL * BLK64);
+    D.h32 = U.take<float>(nd * D.nL * BLK32);
+  }
   D.rho = U.take<double>((size_t)nseg * (AMG_MAXL + 1));
   for (int k = 0; k < 2; ++k) {
     D.pw64[k] = U.take<double>((size_t)N * VEC);
@@ -429,7 +475,7 @@ AmgHost* amg_build(int N, int nseg, const int* seg_v0, const int* seg_nv, const 
     HostLevel& cur = H[L];       // (emplace_back may move the vector)
     HostLevel& nxt = H[L + 1];
     NbrView nb{L, &fixed, inc_ptr, inc_code, inc_other, &cur.a_ptr, &cur.a_col};
-    build_level(cur, nb, nxt);
+    build_level(cur, nb, nxt, nseg == 1);
     nxt.n = cur.n_next;
     // references: the first member of each aggregate
     nxt.ref.assign(nxt.n, -1);
@@ -538,6 +584,12 @@ __device__ __forceinline__ void block_partial(double v, double* partial) {
   __syncthreads();
 }
 
+// Barrier of the 64 threads (two warps) of team `slot` of a 256-thread block
+// (named barriers 1..4; barrier 0 is __syncthreads).
+__device__ __forceinline__ void team_sync(int slot) {
+  asm volatile("bar.sync %0, 64;" ::"r"(slot + 1) : "memory");
+}
+
 // y = D^-1 A (sc x) for the rows of level l, one warp per row: the lanes
 // take whole blocks of the row (the diagonal block first), the warp sums
 // the partial products, lanes 0..6 apply D^-1.  Returns the thread's part of
@@ -625,7 +677,7 @@ __device__ double power_step(const DevGraph& g, const AmgLevel& Lv, int l, V lam
 // levels and the coarsest inverse of the last complete set-up, which stay
 // consistent among themselves, so the cycle stays symmetric positive definite.
 template <class V>
-__global__ void __launch_bounds__(256) k_amg_setup(DevGraph g, int lm) {
+__global__ void __launch_bounds__(256, 1) k_amg_setup(DevGraph g, int lm) {
   SolverState* st = g.st;
   if (st->done) return;
   // the hierarchy descriptor, cached in shared memory
@@ -755,17 +807,42 @@ __global__ void __launch_bounds__(256) k_amg_setup(DevGraph g, int lm) {
       }
     }
     if (!grid_sync(counter, abort_flag, target)) goto timeout;
-    // ---- AP = A P ----
+    // ---- AP = A P; single-graph hierarchies also Q = P - D^-1 (A P) / rho,
+    // from the team's AP block in shared memory (a 64-thread barrier per team) ----
     {
       const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
       const int i = t / 7, j = t - 7 * (t / 7);
+      const bool lane_on = t < 49;
       const V* Pb = AV<V>::p(Lv);
       V* APb = AV<V>::ap(Lv);
+      const V* Dl = l == 0 ? AV<V>::minv(g) : AV<V>::dinv(Lv);
+      V* Qb = AV<V>::q(Lv);
+      const V wl = V(1.0 / rho);
       for (int b = blockIdx.x * 4 + slot; b < Lv.nnz_ap; b += gridDim.x * 4) {
-        if (t >= 49) continue;
-        const int e0 = __ldg(Lv.r2_ptr + b), e1 = __ldg(Lv.r2_ptr + b + 1);
-        APb[(size_t)b * BLK + i * 7 + j] = l == 0 ? recipe_ax<V, true>(g, nullptr, lam, Lv.r2, e0, e1, Pb, i, j)
-                                                  : recipe_ax<V, false>(g, AV<V>::a(Lv), lam, Lv.r2, e0, e1, Pb, i, j);
+        V drow[7], pv = V(0);
+        if (A.dense && lane_on) {
+          const int u = __ldg(Lv.ap_row + b), pb = __ldg(Lv.ap_pblk + b);
+#pragma unroll
+          for (int k = 0; k < 7; ++k) drow[k] = __ldg(Dl + (size_t)u * BLK + i * 7 + k);
+          if (pb >= 0) pv = __ldcg(Pb + (size_t)pb * BLK + i * 7 + j);
+        }
+        if (lane_on) {
+          const int e0 = __ldg(Lv.r2_ptr + b), e1 = __ldg(Lv.r2_ptr + b + 1);
+          const V v = l == 0 ? recipe_ax<V, true>(g, nullptr, lam, Lv.r2, e0, e1, Pb, i, j)
+                             : recipe_ax<V, false>(g, AV<V>::a(Lv), lam, Lv.r2, e0, e1, Pb, i, j);
+          APb[(size_t)b * BLK + i * 7 + j] = v;
+          sacc[slot][t] = v;
+        }
+        if (A.dense) {
+          team_sync(slot);
+          if (lane_on) {
+            V sd = V(0);
+#pragma unroll
+            for (int k = 0; k < 7; ++k) sd += drow[k] * sacc[slot][k * 7 + j];
+            Qb[(size_t)b * BLK + i * 7 + j] = pv - wl * sd;
+          }
+          team_sync(slot);
+        }
       }
     }
     if (!grid_sync(counter, abort_flag, target)) goto timeout;
@@ -862,6 +939,47 @@ __global__ void __launch_bounds__(256) k_amg_setup(DevGraph g, int lm) {
     }
     if (threadIdx.x == 0 && !ok) *A.flag = 1;
     if (threadIdx.x == 0) A.warm[warm_slot] = 1;
+  }
+  // ---- level L - 1: W = Q C^-1 Q^T, the coarse correction as one dense product ----
+  // (a lagged set-up keeps the coarse levels, so W stays unless Q is the finest)
+  if (A.dense && (!lagged || A.L == 1)) {
+    const AmgLevel& Ld = A.lv[A.L - 1];
+    const int nd = Ld.n, nL = A.nL;
+    const V* Qb = AV<V>::q(Ld);
+    const V* Ci = AV<V>::cinv(A);
+    V* Hb = AV<V>::h(A);
+    V* Wb = AV<V>::w(A);
+    const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
+    const int i = t / 7, j = t - 7 * (t / 7);
+    const bool lane_on = t < 49;
+    if (!grid_sync(counter, abort_flag, target)) goto timeout;
+    // H[u][c] = sum over the blocks k of row u of Q: Q_k C^-1[col k][c]
+    for (int b = blockIdx.x * 4 + slot; b < nd * nL; b += gridDim.x * 4) {
+      if (!lane_on) continue;
+      const int u = b / nL, c = b - nL * u;
+      V acc = V(0);
+      for (int k = __ldg(Ld.ap_ptr + u); k < __ldg(Ld.ap_ptr + u + 1); ++k) {
+        const V* qk = Qb + (size_t)k * BLK + i * 7;
+        const V* ck = Ci + ((size_t)__ldg(Ld.ap_col + k) * nL + c) * BLK + j;
+#pragma unroll
+        for (int m = 0; m < 7; ++m) acc += __ldcg(qk + m) * __ldcg(ck + m * 7);
+      }
+      Hb[(size_t)b * BLK + i * 7 + j] = acc;
+    }
+    if (!grid_sync(counter, abort_flag, target)) goto timeout;
+    // W[u][v] = sum over the blocks k of row v of Q: H[u][col k] Q_k^T
+    for (int b = blockIdx.x * 4 + slot; b < nd * nd; b += gridDim.x * 4) {
+      if (!lane_on) continue;
+      const int u = b / nd, v = b - nd * u;
+      V acc = V(0);
+      for (int k = __ldg(Ld.ap_ptr + v); k < __ldg(Ld.ap_ptr + v + 1); ++k) {
+        const V* hk = Hb + ((size_t)u * nL + __ldg(Ld.ap_col + k)) * BLK + i * 7;
+        const V* qk = Qb + (size_t)k * BLK + j * 7;
+#pragma unroll
+        for (int m = 0; m < 7; ++m) acc += __ldcg(hk + m) * __ldcg(qk + m);
+      }
+      Wb[(size_t)b * BLK + i * 7 + j] = acc;
+    }
   }
   grid_sync_release(&st->ticket[T_AMG_DONE], counter, nullptr);
   return;

@@ -18,6 +18,9 @@ struct AV<double> {
   static __device__ __forceinline__ double* t(const AmgLevel& L) { return L.t64; }
   static __device__ __forceinline__ double* p(const AmgLevel& L) { return L.p64; }
   static __device__ __forceinline__ double* ap(const AmgLevel& L) { return L.ap64; }
+  static __device__ __forceinline__ double* q(const AmgLevel& L) { return L.q64; }
+  static __device__ __forceinline__ double* w(const AmgDev& A) { return A.w64; }
+  static __device__ __forceinline__ double* h(const AmgDev& A) { return A.h64; }
   static __device__ __forceinline__ double* cinv(const AmgDev& A) { return A.cinv64; }
   static __device__ __forceinline__ double* pw(const AmgDev& A, int k) { return A.pw64[k]; }
   static __device__ __forceinline__ double* vr(const AmgLevel& L) { return L.vr64; }
@@ -37,6 +40,9 @@ struct AV<float> {
   static __device__ __forceinline__ float* t(const AmgLevel& L) { return L.t32; }
   static __device__ __forceinline__ float* p(const AmgLevel& L) { return L.p32; }
   static __device__ __forceinline__ float* ap(const AmgLevel& L) { return L.ap32; }
+  static __device__ __forceinline__ float* q(const AmgLevel& L) { return L.q32; }
+  static __device__ __forceinline__ float* w(const AmgDev& A) { return A.w32; }
+  static __device__ __forceinline__ float* h(const AmgDev& A) { return A.h32; }
   static __device__ __forceinline__ float* cinv(const AmgDev& A) { return A.cinv32; }
   static __device__ __forceinline__ float* pw(const AmgDev& A, int k) { return A.pw32[k]; }
   static __device__ __forceinline__ float* vr(const AmgLevel& L) { return L.vr32; }

@@ -578,6 +578,7 @@ pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
   g.N = N;
   g.E = E;
   g.fixed = d->fixed_vertex;
+  g.pcg_block_entries = pcg_block_entries(N, G->h_inc_ptr.data());
   int* d_ei = A.take<int>(Ep);
   int* d_ej = A.take<int>(Ep);
   D4* d_zq = A.take<D4>(Ep);

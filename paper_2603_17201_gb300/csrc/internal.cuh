@@ -94,6 +94,16 @@ struct AmgLevel {
   const int* ap_col;
   double* ap64;
   float* ap32;
+  // single-graph hierarchies: Q = (I - D^-1 A / rho) P in the pattern of A P
+  // (the prolongation with the post-smoothing folded in), the row of each
+  // block, the P block at the same place (-1: none) and the CSC of the pattern
+  const int* ap_row;
+  const int* ap_pblk;
+  const int* apt_ptr;
+  const int* apt_row;
+  const int* apt_blk;
+  double* q64;
+  float* q32;
   // numeric recipes (CSR lists of index pairs per output block)
   const int* r1_ptr;      // per P block: (A ref, node w) terms of A T
   const int2* r1;
@@ -118,6 +128,15 @@ struct AmgDev {
   AmgLevel lv[AMG_MAXL + 1];
   double* cinv64;         // dense inverse of the coarsest operator (nL x nL blocks;
   float* cinv32;          // per segment AMG_CMAX^2 blocks when nseg > 1)
+  // single-graph hierarchies (dense != 0): level L - 1 takes its coarse
+  // correction as one dense product, W = Q C^-1 Q^T (n x n blocks, n the
+  // nodes of level L - 1), with H = Q C^-1 (n x nL blocks) on the way
+  int dense;
+  int pad_;
+  double* w64;
+  float* w32;
+  double* h64;
+  float* h32;
   double* rho;            // per segment and level: estimate of rho(D^-1 A)
   double* pw64[2];        // power-iteration vectors
   float* pw32[2];
@@ -129,6 +148,7 @@ struct AmgDev {
 // Device view of one graph.
 struct DevGraph {
   int N, E, fixed;
+  int pcg_block_entries;  // most incidence entries of one PCG row block (0: unknown)
   const int* ei;          // internal (sorted) edge order
   const int* ej;
   const D4* zq;           // measurement quaternion (x, y, z, w), normalised
@@ -215,6 +235,8 @@ void launch_state_ctl(const DevGraph& g, int op, cudaStream_t s);
 void launch_scale_x(const DevGraph& g, double f, cudaStream_t s);
 void launch_precond(const DevGraph& g, int mixed, cudaStream_t s);
 // amg: host copy of the hierarchy (nullptr: block-Jacobi preconditioner)
+// Most incidence entries of one row block of the PCG launch over N rows.
+int pcg_block_entries(int N, const int* inc_ptr);
 cudaError_t launch_pcg(const DevGraph& g, int mixed, int from_residual, const AmgDev* amg, cudaStream_t s);
 // lm: the set-up of an LM iteration (may keep the coarse levels, see
 // DevOptions::amg_refresh); 0: a standalone solve (always complete)

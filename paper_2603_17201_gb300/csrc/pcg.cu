@@ -295,42 +295,23 @@ __device__ __forceinline__ void group_reduce7(V (&y)[7], unsigned gmG) {
     for (int o2 = G / 2; o2 > 0; o2 >>= 1) y[a2] += __shfl_xor_sync(gmG, y[a2], o2);
 }
 
-// y = (H + lambda I) x for level-0 row v over the row's G lanes (x from L2);
-// after the call every lane of the group holds the row's 7 outputs.
-template <class V, int G>
-__device__ __forceinline__ void row_spmv0(const DevGraph& g, const L0Ctx<V>& c, int v, bool has, int sl,
-                                          unsigned gmG, const V* x, V (&y)[7]) {
+// y = (H + lambda I) x for level-0 row v over the row's G lanes; ld(u, xu)
+// loads the 8-vector of vertex u.  The lanes take the row's side-0 entries
+// (the diagonal first), then its side-1 entries (stored transposed): two
+// loops, so that the lanes of a warp never diverge between the two products
+// (walking both sides in lockstep measured slower: its register pressure
+// spills).  An absent row (has == false) has no entries.  After the call
+// every lane of the group holds the row's 7 outputs.
+template <class V, int G, class LD>
+__device__ __forceinline__ void row_prod0(const DevGraph& g, const L0Ctx<V>& c, int v, bool has, int sl,
+                                          unsigned gmG, LD ld, V (&y)[7]) {
   constexpr int BLK = AV<V>::BLK;
   const int k0 = has ? __ldg(g.inc_ptr + v) : 0, k1 = has ? __ldg(g.inc_ptr + v + 1) : -1;
-  const int ks = has ? __ldg(g.inc_split + v) : 0;
+  const int ks = has ? __ldg(g.inc_split + v) : -1;
 #pragma unroll
   for (int a2 = 0; a2 < 7; ++a2) y[a2] = V(0);
-  for (int k = k0 - 1 + sl; k < ks; k += G) {
-    const bool dg = k < k0;
+  auto entry = [&](int k, int& u, const V*& Bp) {
     const int l = k - c.e0;
-    int u = v;
-    const V* Bp;
-    if (dg) {
-      Bp = c.s_diag + (size_t)(v - c.row0) * BLK;
-    } else if (l < c.nst) {
-      u = c.s_other[l];
-      Bp = c.s_off + (size_t)l * BLK;
-    } else {
-      u = __ldg(g.inc_other + k);
-      Bp = c.off + (size_t)(__ldg(g.inc_code + k) >> 1) * BLK;
-    }
-    V pu[8];
-    ld8(x + (size_t)u * VEC, pu);
-    if (dg) {
-#pragma unroll
-      for (int a2 = 0; a2 < 7; ++a2) y[a2] += c.lam * pu[a2];
-    }
-    bmv<false>(Bp, pu, y);
-  }
-  for (int k = ks + sl; k < k1; k += G) {
-    const int l = k - c.e0;
-    int u;
-    const V* Bp;
     if (l < c.nst) {
       u = c.s_other[l];
       Bp = c.s_off + (size_t)l * BLK;
@@ -338,9 +319,27 @@ __device__ __forceinline__ void row_spmv0(const DevGraph& g, const L0Ctx<V>& c, 
       u = __ldg(g.inc_other + k);
       Bp = c.off + (size_t)(__ldg(g.inc_code + k) >> 1) * BLK;
     }
-    V pu[8];
-    ld8(x + (size_t)u * VEC, pu);
-    bmv<true>(Bp, pu, y);
+  };
+  const V* Bd = c.s_diag + (size_t)(has ? v - c.row0 : 0) * BLK;
+  for (int k = k0 - 1 + sl; k < ks; k += G) {
+    int u = v;
+    const V* Bp = Bd;
+    if (k >= k0) entry(k, u, Bp);
+    V xa[8];
+    ld(u, xa);
+    if (k < k0) {
+#pragma unroll
+      for (int a2 = 0; a2 < 7; ++a2) y[a2] += c.lam * xa[a2];
+    }
+    bmv<false>(Bp, xa, y);
+  }
+  for (int k = ks + sl; k < k1; k += G) {
+    int u;
+    const V* Bp;
+    entry(k, u, Bp);
+    V xb[8];
+    ld(u, xb);
+    bmv<true>(Bp, xb, y);
   }
   group_reduce7<V, G>(y, gmG);
 }
@@ -370,13 +369,19 @@ __device__ __forceinline__ V dmul_row(const V* M, int a, const V (&v)[7]) {
 constexpr int GC = 32;
 
 // The V(1,1) cycle after the caller has stored the level-0 pre-smoothed
-// iterate x0 = w0 D0^-1 r for its rows: residual and restriction down the
-// levels (the pre-smoothing of each coarser level is fused into the
-// restriction), the dense coarsest solve, then on the way up the
-// prolongation fused with the post-smoothing, using
-// r - A (x + P y) = s - (A P) y with s = r - A x kept from the way down.
-// Writes z for the block's rows and adds r.z to rz_loc.  Returns false on a
-// barrier timeout.
+// iterate x0 = w0 D0^-1 r for its rows.  With the smoothing weight w_l and
+// Q_l = (I - w_l D_l^-1 A_l) P_l (the prolongation with the post-smoothing
+// folded in; its transpose is the restriction with the pre-smoothing), the
+// cycle on level l is
+//   x_l = w_l D_l^-1 r_l,  f_l = x_l + w_l D_l^-1 (r_l - A_l x_l),
+//   r_{l+1} = Q_l^T r_l,   z_l = f_l + Q_l z_{l+1},
+// and on level d = L - 1, next to the coarsest, z_d = f_d + W r_d with the
+// dense W = Q_d C^-1 Q_d^T of the set-up.  This is the cycle of pre-smoothing,
+// residual, restriction, coarse solve, prolongation and post-smoothing
+// written as one linear map per level: f_l and r_{l+1} both depend on r_l
+// alone, so each level costs one grid barrier on the way down and one on the
+// way up.  Writes z for the block's rows and adds r.z to rz_loc.  Returns
+// false on a barrier timeout.
 template <class V, class S, int G>
 __device__ bool vcycle_rest(const DevGraph& g, const AmgDev& A, const L0Ctx<V>& c0, const V* r0v, V* s0, V* z,
                             S& rz_loc, unsigned* counter, int* abort_flag, unsigned& target) {
@@ -389,224 +394,232 @@ __device__ bool vcycle_rest(const DevGraph& g, const AmgDev& A, const L0Ctx<V>& 
   const int cslot = threadIdx.x >> 5;
   const int ncslots = blockDim.x >> 5;
   const unsigned full = 0xffffffffu;
-  const int L = A.L;
+  const int d = A.L - 1;
   auto range = [&](int n, int& r0, int& r1) {
     const int rpb = (n + gridDim.x - 1) / gridDim.x;
     r0 = min((int)blockIdx.x * rpb, n);
     r1 = min(r0 + rpb, n);
   };
-  for (int l = 0; l < L; ++l) {
+  // level-0 rows of the block: f_0 (kept in s0 for the way up) or, when level
+  // 0 is the dense level, z itself
+  auto level0 = [&](bool dense) {
+    const AmgLevel& L0 = A.lv[0];
+    const V* x0 = AV<V>::vx(L0);
+    const V w0 = V(1.0 / A.rho[0]);
+    const V* Wb = AV<V>::w(A);
+    const int nd = L0.n;
+    for (int v0 = c0.row0; v0 < c0.row1; v0 += nsslots) {
+      const int v = v0 + sslot;
+      const bool has = v < c0.row1;
+      const size_t base = (size_t)(has ? v : c0.row0) * VEC;
+      V rv[8], xv[8];   // the row's own vectors, in flight with the products
+      ld8(r0v + base, rv);
+      ld8(x0 + base, xv);
+      V y[7], wr[7];
+      row_prod0<V, G>(g, c0, v, has, sl, gmG, [&](int u, V (&xu)[8]) { ld8(x0 + (size_t)u * VEC, xu); }, y);
+#pragma unroll
+      for (int a2 = 0; a2 < 7; ++a2) wr[a2] = V(0);
+      if (dense && has) {
+        for (int u = sl; u < nd; u += G) {
+          V pu[8];
+          ld8(r0v + (size_t)u * VEC, pu);
+          bmv<false>(Wb + ((size_t)v * nd + u) * BLK, pu, wr);
+        }
+      }
+      if (dense) group_reduce7<V, G>(wr, gmG);
+      if (has) {
+        V d7[7];
+#pragma unroll
+        for (int c = 0; c < 7; ++c) d7[c] = rv[c] - y[c];
+        const V* M = c0.s_minv + (size_t)(v - c0.row0) * BLK;
+        const bool live = v != g.fixed;
+        V* out = dense ? z : s0;
+#pragma unroll
+        for (int a2 = 0; a2 < 8; ++a2) {
+          if (a2 % G != sl) continue;
+          if (a2 == 7) {
+            out[base + 7] = V(0);
+            continue;
+          }
+          const V o = live ? xv[a2] + w0 * dmul_row(M, a2, d7) + wr[a2] : V(0);
+          out[base + a2] = o;
+          if (dense) rz_loc += S(o) * S(rv[a2]);
+        }
+      }
+    }
+  };
+  // rows of level l >= 1: f_l = x_l + w_l D_l^-1 (r_l - A_l x_l) (+ W r_l on the dense level)
+  auto level_f = [&](int l, bool dense, V* out) {
+    const AmgLevel& Lv = A.lv[l];
+    const V* Ab = AV<V>::a(Lv);
+    const V* xl = AV<V>::vx(Lv);
+    const V* rl = AV<V>::vr(Lv);
+    const V* Dl = AV<V>::dinv(Lv);
+    const V* Wb = AV<V>::w(A);
+    const V wl = V(1.0 / A.rho[l]);
+    const int nd = Lv.n;
+    int r0, r1;
+    range(Lv.n, r0, r1);
+    for (int v0 = r0; v0 < r1; v0 += ncslots) {
+      const int v = v0 + cslot;
+      const bool has = v < r1;
+      const int k0 = has ? __ldg(Lv.a_ptr + v) : 0, k1 = has ? __ldg(Lv.a_ptr + v + 1) : 0;
+      const int w1 = dense && has ? nd : 0;
+      const size_t base = (size_t)(has ? v : 0) * VEC;
+      // the row's own vectors and D^-1 row, in flight with the products
+      V rv[8], drow[7];
+      ld8(rl + base, rv);
+      const V xo = cl < 7 ? __ldcg(xl + base + cl) : V(0);
+#pragma unroll
+      for (int c = 0; c < 7; ++c) drow[c] = cl < 7 ? Dl[(size_t)(has ? v : 0) * BLK + cl * 7 + c] : V(0);
+      V y[7], wr[7];
+#pragma unroll
+      for (int a2 = 0; a2 < 7; ++a2) y[a2] = wr[a2] = V(0);
+      // the A row and (on the dense level) the W row in lockstep
+      for (int k = k0 + cl, u = cl; k < k1 || u < w1; k += GC, u += GC) {
+        const bool ha = k < k1, hw = u < w1;
+        V pa[8], pw[8];
+        if (ha) ld8(xl + (size_t)__ldg(Lv.a_col + k) * VEC, pa);
+        if (hw) ld8(rl + (size_t)u * VEC, pw);
+        if (ha) bmv<false>(Ab + (size_t)k * BLK, pa, y);
+        if (hw) bmv<false>(Wb + ((size_t)v * nd + u) * BLK, pw, wr);
+      }
+      group_reduce7<V, GC>(y, full);
+      if (dense) group_reduce7<V, GC>(wr, full);
+      if (has && cl < 8) {
+        if (cl == 7) {
+          out[base + 7] = V(0);
+        } else {
+          V acc = V(0);
+#pragma unroll
+          for (int c = 0; c < 7; ++c) acc += drow[c] * (rv[c] - y[c]);
+          out[base + cl] = xo + wl * acc + pick7(wr, cl);
+        }
+      }
+    }
+  };
+  // ---- way down: f_l and r_{l+1} = Q_l^T r_l, x_{l+1} = w D^-1 r_{l+1} ----
+  for (int l = 0; l < d; ++l) {
     const AmgLevel& Lv = A.lv[l];
     const AmgLevel& Ln = A.lv[l + 1];
     if (!grid_sync(counter, abort_flag, target)) return false;
-    // ---- s_l = r_l - A_l x_l ----
-    if (l == 0) {
-      const V* x0 = AV<V>::vx(Lv);
-      for (int v0 = c0.row0; v0 < c0.row1; v0 += nsslots) {
-        const int v = v0 + sslot;
-        const bool has = v < c0.row1;
-        V y[7];
-        row_spmv0<V, G>(g, c0, v, has, sl, gmG, x0, y);
-        if (has) {
-          const size_t base = (size_t)v * VEC;
-#pragma unroll
-          for (int a2 = 0; a2 < 8; ++a2) {
-            if (a2 % G != sl) continue;
-            s0[base + a2] = (a2 == 7 || v == g.fixed) ? V(0) : __ldcg(r0v + base + a2) - y[a2];
-          }
-        }
-      }
-    } else {
-      int r0, r1;
-      range(Lv.n, r0, r1);
-      const V* Ab = AV<V>::a(Lv);
-      const V* xl = AV<V>::vx(Lv);
-      const V* rl = AV<V>::vr(Lv);
-      V* sv = AV<V>::vs(Lv);
-      for (int v0 = r0; v0 < r1; v0 += ncslots) {
-        const int v = v0 + cslot;
-        const bool has = v < r1;
-        const int k0 = has ? __ldg(Lv.a_ptr + v) : 0, k1 = has ? __ldg(Lv.a_ptr + v + 1) : 0;
-        V y[7];
-#pragma unroll
-        for (int a2 = 0; a2 < 7; ++a2) y[a2] = V(0);
-        for (int k = k0 + cl; k < k1; k += GC) {
-          V pu[8];
-          ld8(xl + (size_t)__ldg(Lv.a_col + k) * VEC, pu);
-          bmv<false>(Ab + (size_t)k * BLK, pu, y);
-        }
-        group_reduce7<V, GC>(y, full);
-        if (has && cl < 8) sv[(size_t)v * VEC + cl] = cl == 7 ? V(0) : __ldcg(rl + (size_t)v * VEC + cl) - pick7(y, cl);
-      }
-    }
-    if (!grid_sync(counter, abort_flag, target)) return false;
-    // ---- r_{l+1} = P^T s_l, and the next level's pre-smoothing ----
-    {
-      const V* sv = l == 0 ? s0 : AV<V>::vs(Lv);
-      const V* Pb = AV<V>::p(Lv);
-      V* rn = AV<V>::vr(Ln);
-      V* xn = AV<V>::vx(Ln);
-      const bool smooth = l + 1 < L;
-      const V wn = smooth ? V(1.0 / A.rho[l + 1]) : V(0);
-      const V* Dn = AV<V>::dinv(Ln);
-      int r0, r1;
-      range(Ln.n, r0, r1);
-      for (int ci = r0; ci < r1; ci += ncslots) {
-        const int c = ci + cslot;
-        const bool has = c < r1;
-        const int t0 = has ? __ldg(Lv.pt_ptr + c) : 0, t1 = has ? __ldg(Lv.pt_ptr + c + 1) : 0;
-        V y[7];
-#pragma unroll
-        for (int a2 = 0; a2 < 7; ++a2) y[a2] = V(0);
-        for (int t = t0 + cl; t < t1; t += GC) {
-          V pu[8];
-          ld8(sv + (size_t)__ldg(Lv.pt_row + t) * VEC, pu);
-          bmv<true>(Pb + (size_t)__ldg(Lv.pt_blk + t) * BLK, pu, y);
-        }
-        group_reduce7<V, GC>(y, full);
-        if (has && cl < 8) {
-          const size_t base = (size_t)c * VEC;
-          if (cl == 7) {
-            rn[base + 7] = V(0);
-            if (smooth) xn[base + 7] = V(0);
-          } else {
-            rn[base + cl] = pick7(y, cl);
-            if (smooth) xn[base + cl] = wn * dmul_row(Dn + (size_t)c * BLK, cl, y);
-          }
-        }
-      }
-    }
-  }
-  if (!grid_sync(counter, abort_flag, target)) return false;
-  // ---- coarsest: y_L = C^-1 r_L (dense) ----
-  {
-    const AmgLevel& Lc = A.lv[L];
-    const int nL = Lc.n;
-    const V* Ci = AV<V>::cinv(A);
-    const V* rc = AV<V>::vr(Lc);
-    V* yc = AV<V>::vy(Lc);
+    if (l == 0) level0(false);
+    else level_f(l, false, AV<V>::vs(Lv));
+    const V* rl = l == 0 ? r0v : AV<V>::vr(Lv);
+    const V* Qb = AV<V>::q(Lv);
+    V* rn = AV<V>::vr(Ln);
+    V* xn = AV<V>::vx(Ln);
+    const V wn = V(1.0 / A.rho[l + 1]);
+    const V* Dn = AV<V>::dinv(Ln);
     int r0, r1;
-    range(nL, r0, r1);
+    range(Ln.n, r0, r1);
     for (int ci = r0; ci < r1; ci += ncslots) {
       const int c = ci + cslot;
       const bool has = c < r1;
+      const int t0 = has ? __ldg(Lv.apt_ptr + c) : 0, t1 = has ? __ldg(Lv.apt_ptr + c + 1) : 0;
+      V drow[7];   // D^-1 row of the coarse node, in flight with the products
+#pragma unroll
+      for (int k = 0; k < 7; ++k) drow[k] = cl < 7 ? Dn[(size_t)(has ? c : 0) * BLK + cl * 7 + k] : V(0);
       V y[7];
 #pragma unroll
       for (int a2 = 0; a2 < 7; ++a2) y[a2] = V(0);
-      if (has) {
-        for (int d = cl; d < nL; d += GC) {
-          V pu[8];
-          ld8(rc + (size_t)d * VEC, pu);
-          bmv<false>(Ci + (size_t)(c * nL + d) * BLK, pu, y);
-        }
+      // two entries per lane and step, both loads issued first
+      for (int t = t0 + cl; t < t1; t += 2 * GC) {
+        const int t2 = t + GC;
+        const bool h2 = t2 < t1;
+        V pa[8], pb[8];
+        ld8(rl + (size_t)__ldg(Lv.apt_row + t) * VEC, pa);
+        if (h2) ld8(rl + (size_t)__ldg(Lv.apt_row + t2) * VEC, pb);
+        bmv<true>(Qb + (size_t)__ldg(Lv.apt_blk + t) * BLK, pa, y);
+        if (h2) bmv<true>(Qb + (size_t)__ldg(Lv.apt_blk + t2) * BLK, pb, y);
       }
       group_reduce7<V, GC>(y, full);
-      if (has && cl < 8) yc[(size_t)c * VEC + cl] = cl == 7 ? V(0) : pick7(y, cl);
+      if (has && cl < 8) {
+        const size_t base = (size_t)c * VEC;
+        if (cl == 7) {
+          rn[base + 7] = V(0);
+          xn[base + 7] = V(0);
+        } else {
+          V acc = V(0);
+#pragma unroll
+          for (int k = 0; k < 7; ++k) acc += drow[k] * y[k];
+          rn[base + cl] = pick7(y, cl);
+          xn[base + cl] = wn * acc;
+        }
+      }
     }
   }
-  // ---- way up: x_l + P y + w D^-1 (s_l - (A P) y) ----
-  for (int l = L - 1; l >= 0; --l) {
+  // ---- level d: f_d + W r_d ----
+  if (!grid_sync(counter, abort_flag, target)) return false;
+  if (d == 0) {
+    level0(true);
+    return true;
+  }
+  level_f(d, true, AV<V>::vy(A.lv[d]));
+  // ---- way up: z_l = f_l + Q_l z_{l+1} ----
+  for (int l = d - 1; l >= 0; --l) {
     const AmgLevel& Lv = A.lv[l];
     const AmgLevel& Ln = A.lv[l + 1];
     if (!grid_sync(counter, abort_flag, target)) return false;
     const V* yn = AV<V>::vy(Ln);
-    const V* Pb = AV<V>::p(Lv);
-    const V* APb = AV<V>::ap(Lv);
-    const V* xl = AV<V>::vx(Lv);
-    const V wl = V(1.0 / A.rho[l]);
+    const V* Qb = AV<V>::q(Lv);
     if (l == 0) {
       for (int v0 = c0.row0; v0 < c0.row1; v0 += nsslots) {
         const int v = v0 + sslot;
         const bool has = v < c0.row1;
-        int k0 = 0, k1 = 0, j0 = 0, j1 = 0;
+        int k0 = 0, k1 = 0;
         if (has) {
-          k0 = __ldg(Lv.p_ptr + v);
-          k1 = __ldg(Lv.p_ptr + v + 1);
-          j0 = __ldg(Lv.ap_ptr + v);
-          j1 = __ldg(Lv.ap_ptr + v + 1);
+          k0 = __ldg(Lv.ap_ptr + v);
+          k1 = __ldg(Lv.ap_ptr + v + 1);
         }
-        V px[7], ax[7];
+        // lane sl stores component sl (G >= 8): its f and r, in flight with the products
+        const size_t base = (size_t)(has ? v : c0.row0) * VEC;
+        const V fo = sl < 7 ? __ldcg(s0 + base + sl) : V(0);
+        const V ro = sl < 7 ? __ldcg(r0v + base + sl) : V(0);
+        V qy[7];
 #pragma unroll
-        for (int a2 = 0; a2 < 7; ++a2) px[a2] = ax[a2] = V(0);
+        for (int a2 = 0; a2 < 7; ++a2) qy[a2] = V(0);
         for (int k = k0 + sl; k < k1; k += G) {
           V pu[8];
-          ld8(yn + (size_t)__ldg(Lv.p_col + k) * VEC, pu);
-          bmv<false>(Pb + (size_t)k * BLK, pu, px);
-        }
-        for (int k = j0 + sl; k < j1; k += G) {
-          V pu[8];
           ld8(yn + (size_t)__ldg(Lv.ap_col + k) * VEC, pu);
-          bmv<false>(APb + (size_t)k * BLK, pu, ax);
+          bmv<false>(Qb + (size_t)k * BLK, pu, qy);
         }
-        group_reduce7<V, G>(px, gmG);
-        group_reduce7<V, G>(ax, gmG);
-        if (has) {
-          const size_t base = (size_t)v * VEC;
-          V sx[8], xv[8];
-          ld8(s0 + base, sx);
-          ld8(xl + base, xv);
-          V d7[7];
-#pragma unroll
-          for (int c = 0; c < 7; ++c) d7[c] = sx[c] - ax[c];
-          const V* M = c0.s_minv + (size_t)(v - c0.row0) * BLK;
-          const bool live = v != g.fixed;
-#pragma unroll
-          for (int a2 = 0; a2 < 8; ++a2) {
-            if (a2 % G != sl) continue;
-            if (a2 == 7) {
-              z[base + 7] = V(0);
-              continue;
-            }
-            const V o = live ? xv[a2] + px[a2] + wl * dmul_row(M, a2, d7) : V(0);
-            z[base + a2] = o;
-            rz_loc += S(o) * S(__ldcg(r0v + base + a2));
+        group_reduce7<V, G>(qy, gmG);
+        if (has && sl < 8) {
+          if (sl == 7) {
+            z[base + 7] = V(0);
+          } else {
+            const V o = v != g.fixed ? fo + pick7(qy, sl) : V(0);
+            z[base + sl] = o;
+            rz_loc += S(o) * S(ro);
           }
         }
       }
     } else {
       int r0, r1;
       range(Lv.n, r0, r1);
-      const V* sv = AV<V>::vs(Lv);
+      const V* fl = AV<V>::vs(Lv);
       V* out = AV<V>::vy(Lv);
-      const V* Dl = AV<V>::dinv(Lv);
       for (int v0 = r0; v0 < r1; v0 += ncslots) {
         const int v = v0 + cslot;
         const bool has = v < r1;
-        int k0 = 0, k1 = 0, j0 = 0, j1 = 0;
+        int k0 = 0, k1 = 0;
         if (has) {
-          k0 = __ldg(Lv.p_ptr + v);
-          k1 = __ldg(Lv.p_ptr + v + 1);
-          j0 = __ldg(Lv.ap_ptr + v);
-          j1 = __ldg(Lv.ap_ptr + v + 1);
+          k0 = __ldg(Lv.ap_ptr + v);
+          k1 = __ldg(Lv.ap_ptr + v + 1);
         }
-        V px[7], ax[7];
+        const size_t base = (size_t)(has ? v : 0) * VEC;
+        const V fo = cl < 7 ? __ldcg(fl + base + cl) : V(0);   // in flight with the products
+        V qy[7];
 #pragma unroll
-        for (int a2 = 0; a2 < 7; ++a2) px[a2] = ax[a2] = V(0);
+        for (int a2 = 0; a2 < 7; ++a2) qy[a2] = V(0);
         for (int k = k0 + cl; k < k1; k += GC) {
           V pu[8];
-          ld8(yn + (size_t)__ldg(Lv.p_col + k) * VEC, pu);
-          bmv<false>(Pb + (size_t)k * BLK, pu, px);
-        }
-        for (int k = j0 + cl; k < j1; k += GC) {
-          V pu[8];
           ld8(yn + (size_t)__ldg(Lv.ap_col + k) * VEC, pu);
-          bmv<false>(APb + (size_t)k * BLK, pu, ax);
+          bmv<false>(Qb + (size_t)k * BLK, pu, qy);
         }
-        group_reduce7<V, GC>(px, full);
-        group_reduce7<V, GC>(ax, full);
-        if (has && cl < 8) {
-          const size_t base = (size_t)v * VEC;
-          if (cl == 7) {
-            out[base + 7] = V(0);
-          } else {
-            V sx[8];
-            ld8(sv + base, sx);
-            V d7[7];
-#pragma unroll
-            for (int c = 0; c < 7; ++c) d7[c] = sx[c] - ax[c];
-            out[base + cl] = __ldcg(xl + base + cl) + pick7(px, cl) + wl * dmul_row(Dl + (size_t)v * BLK, cl, d7);
-          }
-        }
+        group_reduce7<V, GC>(qy, full);
+        if (has && cl < 8) out[base + cl] = cl == 7 ? V(0) : fo + pick7(qy, cl);
       }
     }
   }
@@ -624,7 +637,7 @@ __device__ bool vcycle_rest(const DevGraph& g, const AmgDev& A, const L0Ctx<V>& 
 // iteration reads the operator from shared memory; entries beyond the
 // capacity are read from global memory.
 template <class V, class S, int G>
-__global__ void __launch_bounds__(512) k_pcg(DevGraph g, PcgArgs a) {
+__global__ void __launch_bounds__(sizeof(V) == 8 ? 256 : 512) k_pcg(DevGraph g, PcgArgs a) {
   SolverState* st = g.st;
   if (st->done || (a.from_residual && st->ref_done)) return;
   __shared__ PcgShared<S> sh;
@@ -772,76 +785,24 @@ __global__ void __launch_bounds__(512) k_pcg(DevGraph g, PcgArgs a) {
         const int v = v0 + sslot;
         const bool has = v < row1;
         const size_t base = (size_t)(has ? v : row0) * VEC;
-        const int k0 = has ? __ldg(g.inc_ptr + v) : 0, k1 = has ? __ldg(g.inc_ptr + v + 1) : -1;
-        const int ks = has ? __ldg(g.inc_split + v) : 0;
+        // lane sl stores component sl (G >= 8): its z and p_prev, in flight
+        // with the row product
+        const V zo = sl < 7 ? __ldcg(z + base + sl) : V(0);
+        const V po = sl < 7 ? __ldcg(pprev + base + sl) : V(0);
         V y[7];
-#pragma unroll
-        for (int a2 = 0; a2 < 7; ++a2) y[a2] = V(0);
-        // side-0 entries (H_vu stored as the (v, u) block) and the diagonal
-        // block (entry k0 - 1), then side-1 entries (H_uv^T): two loops so
-        // that the lanes of a warp never diverge between the two products
-        for (int k = k0 - 1 + sl; k < ks; k += G) {
-          const bool dg = k < k0;
-          const int l = k - e0;
-          int code = 0, u = v;
-          const V* Bp;
-          if (dg) {
-            Bp = s_diag + (size_t)(v - row0) * BLK;
-          } else if (l < nst) {
-            code = s_code[l];
-            u = s_other[l];
-            Bp = s_off + (size_t)l * BLK;
+        row_prod0<V, G>(g, c0, v, has, sl, gmG,
+                        [&](int u, V (&pu)[8]) { load_p(z, pprev, (size_t)u * VEC, vb, pu); }, y);
+        if (has && sl < 8) {
+          if (sl == 7) {
+            q[base + 7] = V(0);
+            pcur[base + 7] = V(0);
           } else {
-            code = __ldg(g.inc_code + k);
-            u = __ldg(g.inc_other + k);
-            Bp = off + (size_t)(code >> 1) * BLK;
-          }
-          V pu[8];
-          load_p(z, pprev, (size_t)u * VEC, vb, pu);
-          if (dg) {
-#pragma unroll
-            for (int a2 = 0; a2 < 7; ++a2) y[a2] += lam * pu[a2];
-          }
-          bmv<false>(Bp, pu, y);
-        }
-        for (int k = ks + sl; k < k1; k += G) {
-          const int l = k - e0;
-          int code, u;
-          const V* Bp;
-          if (l < nst) {
-            code = s_code[l];
-            u = s_other[l];
-            Bp = s_off + (size_t)l * BLK;
-          } else {
-            code = __ldg(g.inc_code + k);
-            u = __ldg(g.inc_other + k);
-            Bp = off + (size_t)(code >> 1) * BLK;
-          }
-          V pu[8];
-          load_p(z, pprev, (size_t)u * VEC, vb, pu);
-          bmv<true>(Bp, pu, y);
-        }
-        // reduce the row's partial products over its G lanes
-#pragma unroll
-        for (int a2 = 0; a2 < 7; ++a2)
-#pragma unroll
-          for (int o2 = G / 2; o2 > 0; o2 >>= 1) y[a2] += __shfl_xor_sync(gmG, y[a2], o2);
-        if (has) {
-          // every lane holds the row's 7 outputs after the reduction; lane sl
-          // stores components sl, sl + G, ... and the zero pad (index 7)
-          const bool live = v != g.fixed;
-#pragma unroll
-          for (int a2 = 0; a2 < 8; ++a2) {
-            if (a2 % G != sl) continue;
-            if (a2 == 7) {
-              q[base + 7] = V(0);
-              pcur[base + 7] = V(0);
-              continue;
-            }
-            const V pv = __ldcg(z + base + a2) + vb * __ldcg(pprev + base + a2);
-            q[base + a2] = live ? y[a2] : V(0);
-            pcur[base + a2] = pv;
-            if (live) pq += S(pv) * S(y[a2]);
+            const bool live = v != g.fixed;
+            const V pv = zo + vb * po;
+            const V yo = pick7(y, sl);
+            q[base + sl] = live ? yo : V(0);
+            pcur[base + sl] = pv;
+            if (live) pq += S(pv) * S(yo);
           }
         }
       }
@@ -1018,26 +979,40 @@ static int num_sms() {
   return g_num_sms;
 }
 
+static int pcg_rows_per_block(int N) {
+  const int rpb = (N + num_sms() - 1) / num_sms();
+  return rpb < 1 ? 1 : rpb;
+}
+
+int pcg_block_entries(int N, const int* inc_ptr) {
+  const int rpb = pcg_rows_per_block(N);
+  int most = 0;
+  for (int r0 = 0; r0 < N; r0 += rpb) {
+    const int r1 = r0 + rpb < N ? r0 + rpb : N;
+    most = inc_ptr[r1] - inc_ptr[r0] > most ? inc_ptr[r1] - inc_ptr[r0] : most;
+  }
+  return most;
+}
+
 static size_t g_smem_optin = 0;
 
 template <class V, class S, int G>
 static cudaError_t launch_pcg_kernel(const DevGraph& g, PcgArgs a, cudaStream_t s) {
-  const int sms = num_sms();
   if (g_smem_optin == 0) {
     int dev = 0, v = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     g_smem_optin = v > 0 ? (size_t)v : 48 * 1024;
   }
-  // one block per SM, rows split evenly; max(8, G) lanes per row, <= 512 threads
+  // one block per SM, rows split evenly; max(8, G) lanes per row, at most
+  // the kernel's launch bound (FP64: 256 threads, for its registers; FP32: 512)
   const int lanes = G > 8 ? G : 8;
-  int blocks = sms;
-  int rows_per_block = (g.N + blocks - 1) / blocks;
-  if (rows_per_block < 1) rows_per_block = 1;
-  blocks = (g.N + rows_per_block - 1) / rows_per_block;
+  const int rows_per_block = pcg_rows_per_block(g.N);
+  const int blocks = (g.N + rows_per_block - 1) / rows_per_block;
   int threads = rows_per_block * lanes;
   threads = ((threads + 31) / 32) * 32;
-  if (threads > 512) threads = 512;
+  const int tmax = sizeof(V) == 8 ? 256 : 512;
+  if (threads > tmax) threads = tmax;
   if (threads < 32) threads = 32;
   a.rows_per_block = rows_per_block;
   // shared memory: diag + preconditioner blocks of the rows, then as many
@@ -1047,7 +1022,10 @@ static cudaError_t launch_pcg_kernel(const DevGraph& g, PcgArgs a, cudaStream_t 
   const size_t fixed_bytes = 2 * (size_t)rows_per_block * blk_bytes;
   size_t cap = 0;
   if (budget > fixed_bytes) cap = (budget - fixed_bytes) / (blk_bytes + 2 * sizeof(int));
-  const size_t max_entries = (size_t)2 * (size_t)(g.E > 0 ? g.E : 1);
+  // no more than the fullest row block stages: the rest of the SM's 256 KB
+  // stays L1 cache for the multigrid levels' blocks and indices
+  size_t max_entries = (size_t)2 * (size_t)(g.E > 0 ? g.E : 1);
+  if (g.pcg_block_entries > 0 && (size_t)g.pcg_block_entries < max_entries) max_entries = (size_t)g.pcg_block_entries;
   if (cap > max_entries) cap = max_entries;
   a.cap_entries = (int)cap;
   const size_t smem = fixed_bytes + cap * (blk_bytes + 2 * sizeof(int));
