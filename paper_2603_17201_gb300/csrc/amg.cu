@@ -584,8 +584,8 @@ __device__ __forceinline__ void block_partial(double v, double* partial) {
   __syncthreads();
 }
 
-// Barrier of the 64 threads (two warps) of team `slot` of a 256-thread block
-// (named barriers 1..4; barrier 0 is __syncthreads).
+// Barrier of the 64 threads (two warps) of team `slot` (named barriers 1..8
+// for the at most 8 teams of a block; barrier 0 is __syncthreads).
 __device__ __forceinline__ void team_sync(int slot) {
   asm volatile("bar.sync %0, 64;" ::"r"(slot + 1) : "memory");
 }
@@ -671,13 +671,23 @@ __device__ double power_step(const DevGraph& g, const AmgLevel& Lv, int l, V lam
   return nrm;
 }
 
+// Block shape of the set-up: 64-thread teams, one 7x7 output block each.
+// FP32 runs 8 teams per block (more loads in flight per SM); FP64 runs 4,
+// which leaves it the registers of its unrolled products.
+template <class V>
+struct SetupShape {
+  static constexpr int THREADS = sizeof(V) == 4 ? 512 : 256;
+  static constexpr int TEAMS = THREADS / 64;
+};
+
 // lm: the set-up of an LM iteration.  With DevOptions::amg_refresh = k > 1,
 // only every k-th such set-up rebuilds the coarse levels; the others refresh
 // the finest level (its smoothing weight, P and A P) and keep the coarse
 // levels and the coarsest inverse of the last complete set-up, which stay
 // consistent among themselves, so the cycle stays symmetric positive definite.
 template <class V>
-__global__ void __launch_bounds__(256, 1) k_amg_setup(DevGraph g, int lm) {
+__global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGraph g, int lm) {
+  constexpr int TEAMS = SetupShape<V>::TEAMS;
   SolverState* st = g.st;
   if (st->done) return;
   // the hierarchy descriptor, cached in shared memory
@@ -701,8 +711,8 @@ __global__ void __launch_bounds__(256, 1) k_amg_setup(DevGraph g, int lm) {
   const int refresh = g.opt->amg_refresh;
   const bool lagged = lm && warm && refresh > 1 && (st->it % refresh) != 0;
   double* partial = g.partial;
-  __shared__ V sacc[4][49];
-  __shared__ double smat[4][50];   // D^-1 teams
+  __shared__ V sacc[TEAMS][49];
+  __shared__ double smat[TEAMS][50];   // D^-1 teams
   extern __shared__ double dense[];   // coarsest operator (block 0 only)
 
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -783,7 +793,7 @@ __global__ void __launch_bounds__(256, 1) k_amg_setup(DevGraph g, int lm) {
       const bool lane_on = t < 49;
       const V* Tb = AV<V>::t(Lv);
       V* Pb = AV<V>::p(Lv);
-      for (int b0 = blockIdx.x * 4; b0 < Lv.nnz_p; b0 += gridDim.x * 4) {
+      for (int b0 = blockIdx.x * TEAMS; b0 < Lv.nnz_p; b0 += gridDim.x * TEAMS) {
         const int b = b0 + slot;
         const bool has = b < Lv.nnz_p;
         int u = 0, c = 0;
@@ -818,7 +828,7 @@ __global__ void __launch_bounds__(256, 1) k_amg_setup(DevGraph g, int lm) {
       const V* Dl = l == 0 ? AV<V>::minv(g) : AV<V>::dinv(Lv);
       V* Qb = AV<V>::q(Lv);
       const V wl = V(1.0 / rho);
-      for (int b = blockIdx.x * 4 + slot; b < Lv.nnz_ap; b += gridDim.x * 4) {
+      for (int b = blockIdx.x * TEAMS + slot; b < Lv.nnz_ap; b += gridDim.x * TEAMS) {
         V drow[7], pv = V(0);
         if (A.dense && lane_on) {
           const int u = __ldg(Lv.ap_row + b), pb = __ldg(Lv.ap_pblk + b);
@@ -854,7 +864,7 @@ __global__ void __launch_bounds__(256, 1) k_amg_setup(DevGraph g, int lm) {
       const V* Pb = AV<V>::p(Lv);
       const V* APb = AV<V>::ap(Lv);
       V* An = AV<V>::a(Ln);
-      for (int b = blockIdx.x * 4 + slot; b < Lv.nnz_next; b += gridDim.x * 4) {
+      for (int b = blockIdx.x * TEAMS + slot; b < Lv.nnz_next; b += gridDim.x * TEAMS) {
         if (t >= 49) continue;
         const int e0 = __ldg(Lv.r3_ptr + b), e1 = __ldg(Lv.r3_ptr + b + 1);
         if (e0 == e1) continue;   // mirrored block
@@ -878,7 +888,7 @@ __global__ void __launch_bounds__(256, 1) k_amg_setup(DevGraph g, int lm) {
       // the next level's D^-1: one 64-thread team per node
       const V* An = AV<V>::a(Ln);
       const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
-      for (int c0 = blockIdx.x * 4; c0 < Ln.n; c0 += gridDim.x * 4) {
+      for (int c0 = blockIdx.x * TEAMS; c0 < Ln.n; c0 += gridDim.x * TEAMS) {
         const int c = c0 + slot;
         const bool has = c < Ln.n;
         inv7_spd_team<V, true>(An + (size_t)(has ? __ldg(Ln.a_ptr + c) : 0) * BLK,
@@ -954,7 +964,7 @@ __global__ void __launch_bounds__(256, 1) k_amg_setup(DevGraph g, int lm) {
     const bool lane_on = t < 49;
     if (!grid_sync(counter, abort_flag, target)) goto timeout;
     // H[u][c] = sum over the blocks k of row u of Q: Q_k C^-1[col k][c]
-    for (int b = blockIdx.x * 4 + slot; b < nd * nL; b += gridDim.x * 4) {
+    for (int b = blockIdx.x * TEAMS + slot; b < nd * nL; b += gridDim.x * TEAMS) {
       if (!lane_on) continue;
       const int u = b / nL, c = b - nL * u;
       V acc = V(0);
@@ -968,7 +978,7 @@ __global__ void __launch_bounds__(256, 1) k_amg_setup(DevGraph g, int lm) {
     }
     if (!grid_sync(counter, abort_flag, target)) goto timeout;
     // W[u][v] = sum over the blocks k of row v of Q: H[u][col k] Q_k^T
-    for (int b = blockIdx.x * 4 + slot; b < nd * nd; b += gridDim.x * 4) {
+    for (int b = blockIdx.x * TEAMS + slot; b < nd * nd; b += gridDim.x * TEAMS) {
       if (!lane_on) continue;
       const int u = b / nd, v = b - nd * u;
       V acc = V(0);
@@ -1004,7 +1014,7 @@ cudaError_t launch_amg_setup(const DevGraph& g, const AmgDev& amg, int mixed, in
   const size_t smem = (n7 * n7 + n7) * sizeof(double);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
-  cfg.blockDim = dim3(256);
+  cfg.blockDim = dim3(mixed ? SetupShape<float>::THREADS : SetupShape<double>::THREADS);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = s;
   cudaLaunchAttribute attr[1];
