@@ -554,17 +554,33 @@ size_t amg_bytes(const AmgHost* h) { return h ? h->bytes : 0; }
 // Per-block partial (one double per block) and its fixed-order grid sum,
 // double-buffered by `set` so that a fast block's next write cannot race a
 // slow block's read.
-__device__ __forceinline__ double grid_sum_after_sync(const double* partial) {
-  __shared__ double red[32];
-  double acc = 0.0;
+// The square root of the fixed-order grid sum of the per-block partials
+// (0 for a zero or non-finite sum) and its reciprocal (0 for 0), formed once
+// per block: FP64 square roots and divisions by every thread of the block
+// would cost microseconds at the FP64 rate.
+__device__ __forceinline__ double2 grid_norm_after_sync(const double* partial) {
+  __shared__ double2 res;
   if (threadIdx.x < 32) {
-    for (int b = threadIdx.x; b < gridDim.x; b += 32) acc += __ldcg(partial + b);
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int b = threadIdx.x + 32 * q;
+      v[q] = b < (int)gridDim.x ? __ldcg(partial + b) : 0.0;
+    }
+    double acc = 0.0;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc += v[q];
+    for (int b = threadIdx.x + 256; b < (int)gridDim.x; b += 32) acc += __ldcg(partial + b);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (threadIdx.x == 0) red[0] = acc;
+    if (threadIdx.x == 0) {
+      double nx = sqrt(acc);
+      if (!(nx > 0.0) || !isfinite(nx)) nx = 0.0;
+      res = make_double2(nx, nx > 0.0 ? 1.0 / nx : 0.0);
+    }
   }
   __syncthreads();
-  const double r = red[0];
+  const double2 r = res;
   __syncthreads();
   return r;
 }
@@ -671,6 +687,121 @@ __device__ double power_step(const DevGraph& g, const AmgLevel& Lv, int l, V lam
   return nrm;
 }
 
+// Dense copy of the coarsest operator (n7 x n7, row-major) in shared
+// memory, every (block, entry) pair at once.
+template <class V, class W>
+__device__ __forceinline__ void coarsest_dense(const AmgLevel& Lc, W* dense) {
+  constexpr int BLK = AV<V>::BLK;
+  const int nL = Lc.n, n7 = 7 * nL;
+  const V* Ab = AV<V>::a(Lc);
+  for (int t = threadIdx.x; t < n7 * n7; t += blockDim.x) dense[t] = W(0);
+  __syncthreads();
+  const int nnzL = __ldg(Lc.a_ptr + nL);
+  for (int t = threadIdx.x; t < nnzL * 49; t += blockDim.x) {
+    const int k = t / 49, ij = t - 49 * k;
+    int c = 0;
+    while (c + 1 < nL && __ldg(Lc.a_ptr + c + 1) <= k) ++c;
+    const int d = __ldg(Lc.a_col + k);
+    const int i = ij / 7, j = ij - 7 * (ij / 7);
+    dense[(7 * c + i) * n7 + 7 * d + j] = W(__ldcg(Ab + (size_t)k * BLK + ij));
+  }
+  __syncthreads();
+}
+
+// In-place Gauss-Jordan inverse of the SPD n7 x n7 matrix in shared memory
+// (no pivoting), one pass per column: column k and row k saved first, the
+// pivot's reciprocal formed once (thread 0), element (i, j) to thread
+// (i mod rows, j mod 64) of the block seen as rows x 64.  Returns false on a
+// non-positive or non-finite pivot.  colk, rowk: n7 entries each.
+template <class W>
+__device__ bool gauss_jordan_spd(W* dense, int n7, W* colk, W* rowk) {
+  __shared__ int bad;
+  __shared__ W s_ip;
+  const int j0 = threadIdx.x & 63, i0 = threadIdx.x >> 6, istep = blockDim.x >> 6;
+  bool ok = true;
+  for (int k = 0; k < n7; ++k) {
+    if (threadIdx.x == 0) {
+      const W piv = dense[k * n7 + k];
+      const bool okp = piv > W(0) && isfinite(piv);
+      bad = okp ? 0 : 1;
+      s_ip = okp ? W(1) / piv : W(0);
+    }
+    for (int i = threadIdx.x; i < n7; i += blockDim.x) {
+      colk[i] = dense[i * n7 + k];
+      rowk[i] = dense[k * n7 + i];
+    }
+    __syncthreads();
+    if (bad) {   // uniform: every thread reads the same flag
+      ok = false;
+      break;
+    }
+    const W ip = s_ip;
+    for (int i = i0; i < n7; i += istep)
+      for (int j = j0; j < n7; j += 64) {
+        W o;
+        if (i == k) o = (j == k) ? ip : rowk[j] * ip;
+        else o = (j == k) ? -colk[i] * ip : dense[i * n7 + j] - colk[i] * (rowk[j] * ip);
+        dense[i * n7 + j] = o;
+      }
+    __syncthreads();
+  }
+  __syncthreads();
+  return ok;
+}
+
+// C^-1 of the coarsest level into AV<V>::cinv (symmetrised; zero and the
+// failure flag set when a pivot fails).  FP64 elimination for the FP64 set-up.
+__device__ void coarsest_inverse_f64(const AmgDev& A, double* dense) {
+  const AmgLevel& Lc = A.lv[A.L];
+  const int nL = Lc.n, n7 = 7 * nL;
+  coarsest_dense<double, double>(Lc, dense);
+  const bool ok = gauss_jordan_spd<double>(dense, n7, dense + (size_t)n7 * n7, dense + (size_t)n7 * n7 + n7);
+  double* Ci = AV<double>::cinv(A);
+  for (int t = threadIdx.x; t < nL * nL * 49; t += blockDim.x) {
+    const int cd = t / 49, ij = t - 49 * cd;
+    const int c = cd / nL, d = cd - nL * c;
+    const int i = ij / 7, j = ij - 7 * (ij / 7);
+    const int R = 7 * c + i, C = 7 * d + j;
+    Ci[(size_t)cd * BLK64 + ij] = ok ? 0.5 * (dense[R * n7 + C] + dense[C * n7 + R]) : 0.0;
+  }
+  if (threadIdx.x == 0 && !ok) *A.flag = 1;
+}
+
+// The FP32 set-up: the elimination in FP32 on the symmetrically Jacobi-scaled
+// matrix S C S (unit diagonal, S = diag(C)^-1/2), C^-1 = S (S C S)^-1 S.  At
+// GB300's FP64 rate the FP64 elimination of a 56 x 56 matrix takes about
+// 0.2 ms on one SM; the scaling keeps the FP32 elimination's error at the
+// scaled matrix's condition number, and the operator itself comes from FP32
+// products.
+__device__ void coarsest_inverse_f32(const AmgDev& A, float* dense) {
+  const AmgLevel& Lc = A.lv[A.L];
+  const int nL = Lc.n, n7 = 7 * nL;
+  coarsest_dense<float, float>(Lc, dense);
+  float* colk = dense + (size_t)n7 * n7;
+  float* rowk = colk + n7;
+  float* sc = rowk + n7;
+  for (int i = threadIdx.x; i < n7; i += blockDim.x) {
+    const float d = dense[i * n7 + i];
+    sc[i] = d > 0.f && isfinite(d) ? rsqrtf(d) : 1.f;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < n7 * n7; t += blockDim.x) {
+    const int i = t / n7, j = t - n7 * i;
+    dense[t] *= sc[i] * sc[j];
+  }
+  __syncthreads();
+  const bool ok = gauss_jordan_spd<float>(dense, n7, colk, rowk);
+  float* Ci = AV<float>::cinv(A);
+  for (int t = threadIdx.x; t < nL * nL * 49; t += blockDim.x) {
+    const int cd = t / 49, ij = t - 49 * cd;
+    const int c = cd / nL, d = cd - nL * c;
+    const int i = ij / 7, j = ij - 7 * (ij / 7);
+    const int R = 7 * c + i, C = 7 * d + j;
+    Ci[(size_t)cd * BLK32 + ij] = ok ? 0.5f * (dense[R * n7 + C] + dense[C * n7 + R]) * sc[R] * sc[C] : 0.f;
+  }
+  if (threadIdx.x == 0 && !ok) *A.flag = 1;
+}
+
 // Block shape of the set-up: 64-thread teams, one 7x7 output block each.
 // FP32 runs 8 teams per block (more loads in flight per SM); FP64 runs 4,
 // which leaves it the registers of its unrolled products.
@@ -712,7 +843,8 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
   const bool lagged = lm && warm && refresh > 1 && (st->it % refresh) != 0;
   double* partial = g.partial;
   __shared__ V sacc[TEAMS][49];
-  __shared__ double smat[TEAMS][50];   // D^-1 teams
+  __shared__ double smat[TEAMS][52];   // D^-1 teams (51 doubles each)
+  __shared__ double rho_f[2];          // 4 / (3 rho), 1 / rho of the current level
   extern __shared__ double dense[];   // coarsest operator (block 0 only)
 
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -722,7 +854,9 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
     int base = 0;
     for (int l = 0; l < (lagged ? 1 : A.L); ++l) {
       const AmgLevel& Lv = A.lv[l];
-      for (int u = gtid; u < Lv.n; u += gthreads) {
+      // node q * gridDim.x + b to block b: the few hundred FP64 operations of
+      // a node spread over every SM rather than the first few
+      for (int u = threadIdx.x * gridDim.x + blockIdx.x; u < Lv.n; u += gthreads) {
         if (__ldg(Lv.agg + u) < 0) continue;
         const Sim3T<double> Sr = load_pose(g, cur, __ldg(Lv.ref + u));
         const Sim3T<double> Sc = load_pose(g, cur, __ldg(Lv.refc + u));
@@ -764,30 +898,34 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
       }
       block_partial(nrm, partial);
       if (!grid_sync(counter, abort_flag, target)) goto timeout;
-      double nx = sqrt(grid_sum_after_sync(partial));
-      if (!(nx > 0.0) || !isfinite(nx)) nx = 0.0;
+      double2 nn = grid_norm_after_sync(partial);   // (|x|, 1 / |x|)
       const int its = warm ? AMG_POWER_ITS_WARM : AMG_POWER_ITS;
       for (int it = 0; it < its; ++it) {
         const V* xin = AV<V>::pw(A, it & 1);
         V* yout = AV<V>::pw(A, (it + 1) & 1);
-        const V sc = V(nx > 0.0 ? 1.0 / nx : 0.0);
-        double ny2 = power_step<V>(g, Lv, l, lam, xin, sc, yout);
+        double ny2 = power_step<V>(g, Lv, l, lam, xin, V(nn.y), yout);
         double* pset = partial + ((it + 1) & 1) * gridDim.x;
         block_partial(ny2, pset);
         if (!grid_sync(counter, abort_flag, target)) goto timeout;
-        nx = sqrt(grid_sum_after_sync(pset));
+        nn = grid_norm_after_sync(pset);
       }
-      rho = nx > 1e-30 ? nx : 1.0;
+      rho = nn.x > 1e-30 ? nn.x : 1.0;
       // a few warm iterations approach rho from below; never go under the
       // previous estimate (an underestimate weakens the smoother's damping)
       if (warm && rho_prev > rho && isfinite(rho_prev)) rho = rho_prev;
       if (gtid == 0) A.rho[l] = rho;
+      // the smoother's factors, divided once per block
+      if (threadIdx.x == 0) {
+        rho_f[0] = 4.0 / (3.0 * rho);
+        rho_f[1] = 1.0 / rho;
+      }
+      __syncthreads();
       const V* yl = AV<V>::pw(A, its & 1);
       for (int t = gtid; t < Lv.n * VEC; t += gthreads) pv[t] = __ldcg(yl + t);
     }
     // ---- P = T_agg - 4/(3 rho) D^-1 (A T) ----
     {
-      const double f = 4.0 / (3.0 * rho);
+      const double f = rho_f[0];
       const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
       const int i = t / 7, j = t - 7 * (t / 7);
       const bool lane_on = t < 49;
@@ -827,7 +965,7 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
       V* APb = AV<V>::ap(Lv);
       const V* Dl = l == 0 ? AV<V>::minv(g) : AV<V>::dinv(Lv);
       V* Qb = AV<V>::q(Lv);
-      const V wl = V(1.0 / rho);
+      const V wl = V(rho_f[1]);
       for (int b = blockIdx.x * TEAMS + slot; b < Lv.nnz_ap; b += gridDim.x * TEAMS) {
         V drow[7], pv = V(0);
         if (A.dense && lane_on) {
@@ -899,55 +1037,8 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
   }
   // ---- coarsest level: dense inverse (block 0, Gauss-Jordan on the SPD matrix) ----
   if (blockIdx.x == 0 && !lagged) {
-    const AmgLevel& Lc = A.lv[A.L];
-    const int nL = Lc.n, n7 = 7 * nL;
-    const V* Ab = AV<V>::a(Lc);
-    for (int t = threadIdx.x; t < n7 * n7; t += blockDim.x) dense[t] = 0.0;
-    __syncthreads();
-    for (int c = 0; c < nL; ++c)
-      for (int k = Lc.a_ptr[c]; k < Lc.a_ptr[c + 1]; ++k) {
-        const int d = Lc.a_col[k];
-        for (int ij = threadIdx.x; ij < 49; ij += blockDim.x) {
-          const int i = ij / 7, j = ij - 7 * (ij / 7);
-          dense[(7 * c + i) * n7 + 7 * d + j] = (double)__ldcg(Ab + (size_t)k * BLK + ij);
-        }
-      }
-    __syncthreads();
-    __shared__ int bad;
-    if (threadIdx.x == 0) bad = 0;
-    __syncthreads();
-    double* colk = dense + (size_t)n7 * n7;   // column k, saved before the pass
-    for (int k = 0; k < n7; ++k) {
-      const double piv = dense[k * n7 + k];
-      if (!(piv > 0.0) || !isfinite(piv)) {   // uniform: every thread reads the same pivot
-        if (threadIdx.x == 0) bad = 1;
-        break;
-      }
-      const double ip = 1.0 / piv;
-      for (int i = threadIdx.x; i < n7; i += blockDim.x) colk[i] = dense[i * n7 + k];
-      __syncthreads();
-      for (int j = threadIdx.x; j < n7; j += blockDim.x) dense[k * n7 + j] = (j == k) ? ip : dense[k * n7 + j] * ip;
-      __syncthreads();
-      for (int t = threadIdx.x; t < n7 * n7; t += blockDim.x) {
-        const int i = t / n7, j = t - n7 * i;
-        if (i == k) continue;
-        const double fik = colk[i];
-        dense[t] = (j == k) ? -fik * ip : dense[t] - fik * dense[k * n7 + j];
-      }
-      __syncthreads();
-    }
-    __syncthreads();
-    V* Ci = AV<V>::cinv(A);
-    const bool ok = bad == 0;
-    for (int t = threadIdx.x; t < nL * nL * 49; t += blockDim.x) {
-      const int cd = t / 49, ij = t - 49 * cd;
-      const int c = cd / nL, d = cd - nL * c;
-      const int i = ij / 7, j = ij - 7 * (ij / 7);
-      const int R = 7 * c + i, C = 7 * d + j;
-      const double v = ok ? 0.5 * (dense[R * n7 + C] + dense[C * n7 + R]) : 0.0;
-      Ci[(size_t)cd * BLK + ij] = V(v);
-    }
-    if (threadIdx.x == 0 && !ok) *A.flag = 1;
+    if (sizeof(V) == 4) coarsest_inverse_f32(A, reinterpret_cast<float*>(dense));
+    else coarsest_inverse_f64(A, dense);
     if (threadIdx.x == 0) A.warm[warm_slot] = 1;
   }
   // ---- level L - 1: W = Q C^-1 Q^T, the coarse correction as one dense product ----
@@ -1011,7 +1102,7 @@ static int amg_sms() {
 cudaError_t launch_amg_setup(const DevGraph& g, const AmgDev& amg, int mixed, int lm, cudaStream_t s) {
   const int blocks = amg_sms();
   const size_t n7 = (size_t)7 * amg.nL;
-  const size_t smem = (n7 * n7 + n7) * sizeof(double);
+  const size_t smem = (n7 * n7 + 2 * n7) * sizeof(double);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(mixed ? SetupShape<float>::THREADS : SetupShape<double>::THREADS);

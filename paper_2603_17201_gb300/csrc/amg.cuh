@@ -187,22 +187,28 @@ __device__ __forceinline__ void adj7(const Sim3T<double>& S, double (&A)[7][7]) 
 // A non-positive pivot falls back to the inverse of the diagonal.
 template <class V, bool CG>
 __device__ __forceinline__ void inv7_spd_team(const V* src, V* dst, bool has, double* M, int t) {
+  // M: 51 doubles of shared scratch (the block, a bad-pivot flag, the reciprocal)
   const int i = t / 7, j = t - 7 * (t / 7);
   const bool on = has && t < 49;
   if (on) M[t] = (double)(CG ? __ldcg(src + t) : src[t]);
   if (t == 0) M[49] = 0.0;
   __syncthreads();
   for (int k = 0; k < 7; ++k) {
-    double p = 1.0, mkj = 0.0, fik = 0.0;
+    double mkj = 0.0, fik = 0.0;
     if (on) {
-      p = M[k * 7 + k];
       mkj = M[k * 7 + j];
       fik = M[i * 7 + k];
     }
+    // the pivot's reciprocal once per team (an FP64 division per lane would
+    // cost more than the whole elimination at the FP64 rate)
+    if (has && t == 0) {
+      const double p = M[k * 7 + k];
+      if (!(p > 0.0)) M[49] = 1.0;
+      M[50] = 1.0 / p;
+    }
     __syncthreads();
     if (on) {
-      if (!(p > 0.0)) M[49] = 1.0;   // benign race: every writer stores 1
-      const double ip = 1.0 / p;
+      const double ip = M[50];
       if (i == k) M[t] = (j == k) ? ip : mkj * ip;
       else M[t] = (j == k) ? -fik * ip : M[t] - fik * mkj * ip;
     }

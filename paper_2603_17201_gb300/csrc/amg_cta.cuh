@@ -168,7 +168,7 @@ __device__ void cta_amg_setup(const DevGraph& g, const AmgDev& A, int sg, int fi
                               double* dense) {
   constexpr int BLK = AV<V>::BLK;
   __shared__ V sacc[8][49];
-  __shared__ double smat[8][50];   // D^-1 teams
+  __shared__ double smat[8][52];   // D^-1 teams (51 doubles each)
   const V lam = V(lam_d);
   const int tid = threadIdx.x, nt = blockDim.x;
   const int L = A.L;
