@@ -607,7 +607,8 @@ __device__ __forceinline__ void team_sync(int slot) {
 }
 
 // y = D^-1 A (sc x) for the rows of level l, one warp per row: the lanes
-// take whole blocks of the row (the diagonal block first), the warp sums
+// take whole blocks of the row (the diagonal block first, each block in
+// 16-byte vector loads), the warp sums
 // the partial products, lanes 0..6 apply D^-1.  Returns the thread's part of
 // |y|^2.
 template <class V>
@@ -637,15 +638,16 @@ __device__ double power_step(const DevGraph& g, const AmgLevel& Lv, int l, V lam
             w = __ldg(g.inc_other + k);
             B = AV<V>::off(g) + (size_t)(code >> 1) * BLK;
           }
-          V xv[7];
+          V xv[7], Bv[49];
 #pragma unroll
           for (int c = 0; c < 7; ++c) xv[c] = sc * __ldcg(x + (size_t)w * VEC + c);
+          ld_block<true>(B, Bv);
           const bool tr = k >= ks;
 #pragma unroll
           for (int a = 0; a < 7; ++a) {
             V t = (k < k0) ? lam * xv[a] : V(0);
 #pragma unroll
-            for (int c = 0; c < 7; ++c) t += __ldg(B + (tr ? c * 7 + a : a * 7 + c)) * xv[c];
+            for (int c = 0; c < 7; ++c) t += (tr ? Bv[c * 7 + a] : Bv[a * 7 + c]) * xv[c];
             acc[a] += t;
           }
         }
@@ -654,15 +656,15 @@ __device__ double power_step(const DevGraph& g, const AmgLevel& Lv, int l, V lam
         const int k1 = __ldg(Lv.a_ptr + u + 1);
         for (int k = __ldg(Lv.a_ptr + u) + lane; k < k1; k += 32) {
           const int w = __ldg(Lv.a_col + k);
-          V xv[7];
+          V xv[7], Bv[49];
 #pragma unroll
           for (int c = 0; c < 7; ++c) xv[c] = sc * __ldcg(x + (size_t)w * VEC + c);
-          const V* B = Ab + (size_t)k * BLK;
+          ld_block<false>(Ab + (size_t)k * BLK, Bv);
 #pragma unroll
           for (int a = 0; a < 7; ++a) {
             V t = V(0);
 #pragma unroll
-            for (int c = 0; c < 7; ++c) t += __ldcg(B + a * 7 + c) * xv[c];
+            for (int c = 0; c < 7; ++c) t += Bv[a * 7 + c] * xv[c];
             acc[a] += t;
           }
         }

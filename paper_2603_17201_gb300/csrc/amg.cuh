@@ -52,6 +52,34 @@ struct AV<float> {
   static __device__ __forceinline__ float* pv(const AmgLevel& L) { return L.pv32; }
 };
 
+// A padded 7x7 block (16-byte aligned) into registers with vector loads:
+// through the non-coherent cache (NC, data of an earlier launch) or from L2
+// (data written by this launch).
+template <bool NC>
+__device__ __forceinline__ void ld_block(const float* src, float (&B)[49]) {
+  const float4* s4 = reinterpret_cast<const float4*>(src);
+#pragma unroll
+  for (int k = 0; k < 12; ++k) {
+    const float4 v = NC ? __ldg(s4 + k) : __ldcg(s4 + k);
+    B[4 * k] = v.x;
+    B[4 * k + 1] = v.y;
+    B[4 * k + 2] = v.z;
+    B[4 * k + 3] = v.w;
+  }
+  B[48] = NC ? __ldg(src + 48) : __ldcg(src + 48);
+}
+template <bool NC>
+__device__ __forceinline__ void ld_block(const double* src, double (&B)[49]) {
+  const double2* s2 = reinterpret_cast<const double2*>(src);
+#pragma unroll
+  for (int k = 0; k < 24; ++k) {
+    const double2 v = NC ? __ldg(s2 + k) : __ldcg(s2 + k);
+    B[2 * k] = v.x;
+    B[2 * k + 1] = v.y;
+  }
+  B[48] = NC ? __ldg(src + 48) : __ldcg(src + 48);
+}
+
 // sum over the recipe entries e of (A_e X_e)[i][j].  A_e: level-0 block
 // reference (L0: diagonal + lambda, or an off-diagonal block, maybe
 // transposed) or a block of this level's operator; X_e = X + rec[e].y * BLK.
