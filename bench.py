@@ -37,7 +37,7 @@ UNIT = "edges/s"
 # DRAM bytes (read + write) of one PCG iteration of the roofline kernel from an
 # ncu capture of `bench.py --roofline-only`; None whenever the kernel has
 # changed since the counters were taken.
-TRAFFIC_PER_ITERATION = None
+TRAFFIC_PER_ITERATION = 21.2567e6 / 9   # DRAM bytes of the 9-iteration roofline launch, per iteration
 
 
 def parse():

@@ -112,7 +112,8 @@ struct AmgLevel {
   const int* r3_ptr;      // per next-level block (upper half): (P block, AP block)
   const int2* r3;
   // V-cycle vectors (n x VEC): restricted residual, pre-smoothed iterate,
-  // residual after pre-smoothing, result
+  // vs: the smoothing part f = x + w D^-1 (r - A x) of the single-graph cycle,
+  // or the residual after pre-smoothing of the batch cycle; the result
   double *vr64, *vx64, *vs64, *vy64;
   float *vr32, *vx32, *vs32, *vy32;
   // power-iteration vector kept from the previous set-up (warm start)
