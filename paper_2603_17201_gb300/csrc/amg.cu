@@ -852,27 +852,31 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
   const int gtid = blockIdx.x * blockDim.x + threadIdx.x;
   const int gthreads = gridDim.x * blockDim.x;
   // ---- tentative prolongation blocks T = Adj(S_ref S_refc^-1), all levels ----
+  // one node per thread over the levels' nodes in sequence, node
+  // q * gridDim.x + b to block b: each node is a chain of a few hundred
+  // dependent FP64 operations, so no thread takes two and every SM takes some
   {
-    int base = 0;
-    for (int l = 0; l < (lagged ? 1 : A.L); ++l) {
-      const AmgLevel& Lv = A.lv[l];
-      // node q * gridDim.x + b to block b: the few hundred FP64 operations of
-      // a node spread over every SM rather than the first few
-      for (int u = threadIdx.x * gridDim.x + blockIdx.x; u < Lv.n; u += gthreads) {
-        if (__ldg(Lv.agg + u) < 0) continue;
-        const Sim3T<double> Sr = load_pose(g, cur, __ldg(Lv.ref + u));
-        const Sim3T<double> Sc = load_pose(g, cur, __ldg(Lv.refc + u));
-        double T[7][7];
-        adj7(compose(Sr, inverse(Sc)), T);
-        V* out = AV<V>::t(Lv) + (size_t)u * BLK;
-#pragma unroll
-        for (int i = 0; i < 7; ++i)
-#pragma unroll
-          for (int j = 0; j < 7; ++j) out[i * 7 + j] = V(T[i][j]);
+    const int nlev = lagged ? 1 : A.L;
+    int total = 0;
+    for (int l = 0; l < nlev; ++l) total += A.lv[l].n;
+    for (int q = threadIdx.x * gridDim.x + blockIdx.x; q < total; q += gthreads) {
+      int l = 0, u = q;
+      while (u >= A.lv[l].n) {
+        u -= A.lv[l].n;
+        ++l;
       }
-      base += Lv.n;
+      const AmgLevel& Lv = A.lv[l];
+      if (__ldg(Lv.agg + u) < 0) continue;
+      const Sim3T<double> Sr = load_pose(g, cur, __ldg(Lv.ref + u));
+      const Sim3T<double> Sc = load_pose(g, cur, __ldg(Lv.refc + u));
+      double T[7][7];
+      adj7(compose(Sr, inverse(Sc)), T);
+      V* out = AV<V>::t(Lv) + (size_t)u * BLK;
+#pragma unroll
+      for (int i = 0; i < 7; ++i)
+#pragma unroll
+        for (int j = 0; j < 7; ++j) out[i * 7 + j] = V(T[i][j]);
     }
-    (void)base;
     if (gtid == 0) *A.flag = 0;
   }
   if (!grid_sync(counter, abort_flag, target)) goto timeout;
@@ -1012,7 +1016,9 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
       }
     }
     if (!grid_sync(counter, abort_flag, target)) goto timeout;
-    // ---- mirror the lower blocks; then the next level's D^-1 ----
+    // ---- mirror the lower blocks, and the next level's D^-1 in the same
+    // phase (it reads only diagonal blocks, which the products wrote; the
+    // mirror writes only lower blocks) ----
     {
       V* An = AV<V>::a(Ln);
       for (int t = gtid; t < Lv.nnz_next * 49; t += gthreads) {
@@ -1023,9 +1029,8 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
         An[(size_t)b * BLK + i * 7 + j] = __ldcg(An + (size_t)src * BLK + j * 7 + i);
       }
     }
-    if (!grid_sync(counter, abort_flag, target)) goto timeout;
     if (l + 1 < A.L) {
-      // the next level's D^-1: one 64-thread team per node
+      // one 64-thread team per node
       const V* An = AV<V>::a(Ln);
       const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
       for (int c0 = blockIdx.x * TEAMS; c0 < Ln.n; c0 += gridDim.x * TEAMS) {
@@ -1034,8 +1039,8 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
         inv7_spd_team<V, true>(An + (size_t)(has ? __ldg(Ln.a_ptr + c) : 0) * BLK,
                                AV<V>::dinv(Ln) + (size_t)(has ? c : 0) * BLK, has, smat[slot], t);
       }
-      if (!grid_sync(counter, abort_flag, target)) goto timeout;
     }
+    if (!grid_sync(counter, abort_flag, target)) goto timeout;
   }
   // ---- coarsest level: dense inverse (block 0, Gauss-Jordan on the SPD matrix) ----
   if (blockIdx.x == 0 && !lagged) {
