@@ -1,6 +1,7 @@
 """Host logic of bench.py without a GPU: the job time as the maximum over
 ranks with two gloo processes on the CPU (the N > 1 replicas path), the
-whole-job aggregation of replicas and the kernel-launch count of a solve."""
+whole-job aggregation of replicas, the kernel-launch count of a solve and
+the algorithmic bytes of one multigrid PCG iteration."""
 import os
 import socket
 import sys
@@ -51,3 +52,27 @@ def test_aggregate_replicas_and_launch_count():
     assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
     assert bench.launches_per_solve("fp64", 11) == 3 + 11 * 7
     assert bench.launches_per_solve("mixed", 11) == 3 + 11 * 12
+
+
+def test_vcycle_bytes_per_iteration_counts_each_operator_read():
+    """The roofline's algorithmic bytes of one multigrid PCG iteration, on a
+    hand-sized hierarchy (FP32 blocks of 49 x 4 B, vectors of 7 x 4 B):
+    level 0 reads its operator twice, D^-1 twice and Q twice; a further
+    sparse level its operator once, Q twice and D^-1 twice; the level next to
+    the coarsest its operator once, D^-1 twice and the dense W once."""
+    import bench
+    blk, vec = 196, 28
+    N, E = 10, 20
+    lv0 = {"nodes": N, "a_blocks": 0, "p_blocks": 5, "ap_blocks": 12}
+    lv1 = {"nodes": 5, "a_blocks": 13, "p_blocks": 5, "ap_blocks": 8}
+    lv2 = {"nodes": 3, "a_blocks": 7, "p_blocks": 3, "ap_blocks": 3}
+    crs = {"nodes": 1, "a_blocks": 1, "p_blocks": 0, "ap_blocks": 0}
+    # three levels above the coarsest: level 1 sparse, level 2 dense (W: 3 x 3 blocks)
+    want = ((2 * (E + N) + 2 * N + 2 * 12) * blk + 18 * N * vec
+            + (13 + 2 * 8 + 2 * 5) * blk + 8 * 5 * vec
+            + (7 + 2 * 3 + 3 * 3) * blk + 6 * 3 * vec)
+    assert bench.vcycle_pcg_bytes_per_iter([lv0, lv1, lv2, crs], N, E, 4) == want
+    # one level above the coarsest: level 0 itself is the dense level (W: N x N blocks)
+    assert bench.vcycle_pcg_bytes_per_iter([lv0, crs], N, E, 4) == (2 * (E + N) + 2 * N + N * N) * blk + 18 * N * vec
+    # FP64 doubles every byte
+    assert bench.vcycle_pcg_bytes_per_iter([lv0, lv1, lv2, crs], N, E, 8) == 2 * want
