@@ -37,7 +37,7 @@ UNIT = "edges/s"
 # DRAM bytes (read + write) of one PCG iteration of the roofline kernel from an
 # ncu capture of `bench.py --roofline-only`; None whenever the kernel has
 # changed since the counters were taken.
-TRAFFIC_PER_ITERATION = 21.2567e6 / 9   # DRAM bytes of the 9-iteration roofline launch, per iteration
+TRAFFIC_PER_ITERATION = None
 
 
 def parse():
@@ -231,7 +231,7 @@ def roofline_leg(pg, N, E, stream, flush, torch, reps=5):
     peak = peaks.get("hbm_gbs", 6800.0)
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": TRAFFIC_PER_ITERATION,
-            "kernel": "k_pcg<float,float,16> (mixed inner PCG with the V(1,1) multigrid cycle), per iteration",
+            "kernel": "k_pcg<float,float,32> (mixed inner PCG with the V(1,1) multigrid cycle, a warp per block row), per iteration",
             "peak_kind": peak_kind, "us_per_pcg_iteration": 1e3 * it_ms,
             "algorithmic_bytes_per_iteration": bytes_it, "multigrid_levels": [lv["nodes"] for lv in info],
             "iterations_timed": [i_lo, i_hi]}

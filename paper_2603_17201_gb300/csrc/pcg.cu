@@ -321,6 +321,30 @@ __device__ __forceinline__ void row_prod0(const DevGraph& g, const L0Ctx<V>& c, 
     }
   };
   const V* Bd = c.s_diag + (size_t)(has ? v - c.row0 : 0) * BLK;
+  if (G >= 32) {
+    // a warp per row: one pass over all of the row's entries, each lane one
+    // entry, the transposed side by a register select (one round trip to L2
+    // for a row of up to 32 entries)
+    for (int k = k0 - 1 + sl; k < k1; k += G) {
+      int u = v;
+      const V* Bp = Bd;
+      if (k >= k0) entry(k, u, Bp);
+      V xa[8];
+      ld(u, xa);
+      V B[49];
+      load_block_any(Bp, B);
+      const bool tr = k >= ks;
+#pragma unroll
+      for (int a2 = 0; a2 < 7; ++a2) {
+        V acc = k < k0 ? c.lam * xa[a2] : V(0);
+#pragma unroll
+        for (int c2 = 0; c2 < 7; ++c2) acc += (tr ? B[c2 * 7 + a2] : B[a2 * 7 + c2]) * xa[c2];
+        y[a2] += acc;
+      }
+    }
+    group_reduce7<V, G>(y, gmG);
+    return;
+  }
   for (int k = k0 - 1 + sl; k < ks; k += G) {
     int u = v;
     const V* Bp = Bd;
@@ -1060,6 +1084,9 @@ cudaError_t launch_pcg(const DevGraph& g, int mixed, int from_residual, const Am
   a.rows_per_block = 1;
   a.cap_entries = 0;
   a.amg = amg != nullptr && g.amg != nullptr;
+  // FP32: a warp per row (one pass over a row's entries) while a block's rows
+  // fit in 512 threads, else 16 lanes per row
+  if (mixed && pcg_rows_per_block(g.N) * 32 <= 512) return launch_pcg_kernel<float, float, 32>(g, a, s);
   if (mixed) return launch_pcg_kernel<float, float, PCG_G32>(g, a, s);
   return launch_pcg_kernel<double, double, 8>(g, a, s);
 }
