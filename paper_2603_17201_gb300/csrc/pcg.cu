@@ -296,12 +296,14 @@ __device__ __forceinline__ void group_reduce7(V (&y)[7], unsigned gmG) {
 }
 
 // y = (H + lambda I) x for level-0 row v over the row's G lanes; ld(u, xu)
-// loads the 8-vector of vertex u.  The lanes take the row's side-0 entries
-// (the diagonal first), then its side-1 entries (stored transposed): two
-// loops, so that the lanes of a warp never diverge between the two products
-// (walking both sides in lockstep measured slower: its register pressure
-// spills).  An absent row (has == false) has no entries.  After the call
-// every lane of the group holds the row's 7 outputs.
+// loads the 8-vector of vertex u.  With a warp per row (G = 32) each lane
+// takes one entry of the whole row in one pass, the transposed side by a
+// register select.  With fewer lanes the lanes take the row's side-0
+// entries (the diagonal first), then its side-1 entries (stored transposed):
+// two loops, so that the lanes of a warp never diverge between the two
+// products (walking both sides in lockstep measured slower: its register
+// pressure spills).  An absent row (has == false) has no entries.  After the
+// call every lane of the group holds the row's 7 outputs.
 template <class V, int G, class LD>
 __device__ __forceinline__ void row_prod0(const DevGraph& g, const L0Ctx<V>& c, int v, bool has, int sl,
                                           unsigned gmG, LD ld, V (&y)[7]) {
@@ -988,6 +990,8 @@ __global__ void __launch_bounds__(256) k_refine_accumulate(DevGraph g) {
 }
 
 // ---- launch configuration ---------------------------------------------------
+// FP32 lanes per block row when a block's rows do not fit in 512 threads
+// with a warp each.
 #ifndef PCG_G32
 #define PCG_G32 16
 #endif
