@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the extra workloads of the default run (8k corridor, 4k adjoint, 256-graph batch)")
     ap.add_argument("--roofline-only", action="store_true",
                     help="only the roofline leg: linearise once, then the capped FP32 PCG re-solves "
                          "(an ncu capture of k_pcg should skip 2 launches: the third runs 9 iterations)")
@@ -185,6 +187,22 @@ def vcycle_pcg_bytes_per_iter(info, n_vertices, n_edges, value_bytes):
     return b
 
 
+def workload_config(name, g, world=1):
+    """The `config` object of the bench line, identical in both arms."""
+    return {"workload": name, "n_vertices": g.n_vertices, "n_edges": g.n_edges, "max_lm_iters": MAX_ITERS,
+            "graph": "figure-8 3-D trajectory, 2 laps, covisibility window 15, 5 loop edges"
+            if name == WORKLOAD else name,
+            "l2": "flushed before every timed step (256 MB write)",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
 def oracle_reference(g, max_iters):
     import oracle
     og = oracle.OracleGraph.from_synthetic(g)
@@ -229,12 +247,84 @@ def roofline_leg(pg, N, E, stream, flush, torch, reps=5):
     bytes_it = vcycle_pcg_bytes_per_iter(info, N, E, 4)
     achieved = bytes_it / (it_ms * 1e-3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
+    bj = block_jacobi_pcg_bytes_per_iter(N, E, 4)
+    kernel = ("k_pcg<float,float,32> (mixed inner PCG with the V(1,1) multigrid cycle, a warp per block row)"
+              if pcg_rows_per_block(N, torch.cuda.get_device_properties(0).multi_processor_count) * 32 <= 512 else
+              "k_pcg<float,float,16> (mixed inner PCG with the V(1,1) multigrid cycle, 16 lanes per block row)")
     return {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
             "traffic": TRAFFIC_PER_ITERATION,
-            "kernel": "k_pcg<float,float,32> (mixed inner PCG with the V(1,1) multigrid cycle, a warp per block row), per iteration",
+            "kernel": kernel + ", per iteration",
+            "achieved_kind": "algorithmic bytes (V-cycle operators and vectors) / CUDA-event time per iteration",
+            "limiter": "latency: 9 dependent phases behind grid barriers per iteration; the marginal iteration "
+                       "runs from L2 and shared memory",
+            "frac_block_jacobi_bytes": bj / (it_ms * 1e-3) / 1e9 / peak,
+            "block_jacobi_bytes_per_iteration": bj,
             "peak_kind": peak_kind, "us_per_pcg_iteration": 1e3 * it_ms,
             "algorithmic_bytes_per_iteration": bytes_it, "multigrid_levels": [lv["nodes"] for lv in info],
             "iterations_timed": [i_lo, i_hi]}
+
+
+def pcg_rows_per_block(N, sms):
+    """Rows per thread block of the persistent PCG (one block per SM)."""
+    return max(1, -(-N // sms))
+
+
+def block_jacobi_pcg_bytes_per_iter(n_vertices, n_edges, value_bytes):
+    """The plain block-Jacobi PCG iteration's algorithmic bytes: every
+    off-diagonal block read once (used for both directions), the diagonal and
+    preconditioner blocks once, and six passes over the 7-vectors."""
+    blk, vec = 49 * value_bytes, 7 * value_bytes
+    return n_edges * blk + n_vertices * (2 * blk + 6 * vec)
+
+
+def setup_bytes(info, n_vertices, n_edges, value_bytes):
+    """Compulsory bytes of one multigrid set-up: read each level's operator
+    once (level 0: one block per edge plus the diagonal blocks) and the poses,
+    write each product once -- tentative prolongations (one block per node),
+    P, A P and Q = (I - w D^-1 A) P (both in the pattern of A P), the next
+    level's operator and D^-1 -- and, on the level next to the coarsest, the
+    dense W = Q C^-1 Q^T and H = Q C^-1."""
+    blk = 49 * value_bytes
+    L = len(info) - 1
+    b = n_vertices * 64
+    for l in range(L):
+        a = n_edges + n_vertices if l == 0 else info[l]["a_blocks"]
+        b += (a + info[l]["nodes"] + info[l]["p_blocks"] + 2 * info[l]["ap_blocks"]) * blk
+        b += (info[l + 1]["a_blocks"] + info[l + 1]["nodes"]) * blk
+    if L >= 1:
+        b += (info[L - 1]["nodes"] ** 2 + info[L - 1]["nodes"] * info[L]["nodes"]) * blk
+    return b
+
+
+def setup_leg(pg, N, E, stream, flush, torch, reps=7):
+    """Duration of the FP32 multigrid set-up of the mixed solve at the
+    current linearisation (pgo_graph_precondition: block-Jacobi blocks plus
+    the numeric hierarchy), CUDA events on the graph's stream, L2 flushed
+    before each repetition; achieved = compulsory bytes / duration."""
+    peaks, peak_kind = measured_peaks()
+    info = pg.multigrid_info()
+    lam = 1e-3
+    pg.precondition_async(lam, precision="mixed")
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(reps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pg.precondition_async(lam, precision="mixed")
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    t = statistics.median(ms)
+    b = setup_bytes(info, N, E, 4)
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return {"bound": "hbm", "achieved": b / (t * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+            "frac": b / (t * 1e-3) / 1e9 / peak, "traffic": None,
+            "kernel": "k_precond<float> + k_amg_setup<float> (FP32 multigrid set-up, once per LM linearisation)",
+            "achieved_kind": "compulsory bytes of the set-up / CUDA-event time",
+            "limiter": "latency and instruction issue: grid-barrier phases of 7x7 block products",
+            "ms_per_setup": t, "algorithmic_bytes_per_setup": b, "peak_kind": peak_kind}
 
 
 def run_roofline_only(args):
@@ -270,9 +360,8 @@ def run_reference(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": args.workload, "n_vertices": g.n_vertices,
-                                        "n_edges": g.n_edges, "max_lm_iters": MAX_ITERS},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "data": "synthetic", "config": workload_config(args.workload, g, world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "host_cores": host_cores(), "kind": "oracle",
                          "sample": f"{args.steps} full LM solves of {args.workload}, single thread"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -284,7 +373,7 @@ BATCH_SCHEDULES = [(4, 256, 1), (8, 256, 1), (16, 256, 1), (8, 512, 1), (16, 512
                    (4, 256, 2), (8, 256, 2), (16, 256, 2)]
 
 
-def run_batch(args):
+def batch_leg(steps, sample=32):
     """256 graphs with N ~ U[100, 5000] (window 15, one loop per 400 keyframes):
     each step solves all of them (20 LM iterations at most) in one persistent
     launch from their initial estimates, timed by the library's CUDA events
@@ -294,45 +383,133 @@ def run_batch(args):
     import torch
     from paper_2603_17201_gb300 import PoseGraph, PoseGraphBatch
     from paper_2603_17201_gb300 import synthetic as syn
-    torch.cuda.set_device(0)
     gs = syn.make_batch()
     V = sum(g.n_vertices for g in gs)
     E = sum(g.n_edges for g in gs)
     out = {}
     for precision in ("fp64", "mixed"):
+        t0 = time.perf_counter()
         b = PoseGraphBatch(gs)
+        t_create = time.perf_counter() - t0
         b.solve(poses=False, max_iters=MAX_ITERS, precision=precision)   # warm-up + autotune
         lanes, threads, bps, _ = b.schedule()
         sched = BATCH_SCHEDULES.index((lanes, threads, bps)) + (len(BATCH_SCHEDULES) if precision == "mixed" else 0)
         ms, its = [], []
-        for _ in range(max(1, args.steps)):
+        for _ in range(max(1, steps)):
+            b.close()
             b = PoseGraphBatch(gs)
             reps, _ = b.solve(poses=False, max_iters=MAX_ITERS, precision=precision, schedule=sched)
             assert max(r["status"] for r in reps) == 0
             ms.append(reps[0]["ms_total"])
             its.append(sum(r["iterations"] for r in reps))
-        sample = 32
+        b.close()
         seq = 0.0
         for g in gs[:sample]:
             pg = PoseGraph.from_synthetic(g)
             pg.solve(max_iters=MAX_ITERS, precision=precision)
             pg.set_poses(g.poses_init)
             seq += pg.solve(max_iters=MAX_ITERS, precision=precision)["ms_total"]
+            pg.close()
         t = statistics.median(ms)
         out[precision] = {"ms_per_batch": t, "ms_per_graph": t / len(gs), "lm_iterations": statistics.median(its),
                           "graph_edges_per_s": E / (t * 1e-3),
                           "schedule": {"lanes": lanes, "threads": threads, "blocks_per_sm": bps},
+                          "create_ms": 1e3 * t_create,
                           "sequential_single_ms_scaled": seq * len(gs) / sample,
                           "sequential_sample": f"first {sample} graphs, single-graph multigrid solves"}
-    line = {"metric": "batched Sim(3) PGO: ms per batch of 256 graphs (one persistent launch)", "unit": "ms",
-            "value": out["mixed"]["ms_per_batch"], "higher_is_better": False, "dtype": "f32+f64",
-            "data": "synthetic", "steps": args.steps,
-            "config": {"workload": "c4_batch256", "graphs": len(gs), "vertices": V, "edges": E,
-                       "max_lm_iters": MAX_ITERS},
+    torch.cuda.synchronize()
+    return {"workload": "c4_batch256", "graphs": len(gs), "vertices": V, "edges": E,
             "mixed": out["mixed"], "fp64": out["fp64"],
             "speedup_batched_mixed_vs_sequential_fp64": out["fp64"]["sequential_single_ms_scaled"] /
-            out["mixed"]["ms_per_batch"]}
+            out["mixed"]["ms_per_batch"],
+            "speedup_batched_mixed_vs_batched_fp64": out["fp64"]["ms_per_batch"] / out["mixed"]["ms_per_batch"]}
+
+
+def run_batch(args):
+    import torch
+    torch.cuda.set_device(0)
+    r = batch_leg(args.steps)
+    line = {"metric": "batched Sim(3) PGO: ms per batch of 256 graphs (one persistent launch)", "unit": "ms",
+            "value": r["mixed"]["ms_per_batch"], "higher_is_better": False, "dtype": "f32+f64",
+            "data": "synthetic", "steps": args.steps,
+            "config": {"workload": "c4_batch256", "graphs": r["graphs"], "vertices": r["vertices"],
+                       "edges": r["edges"], "max_lm_iters": MAX_ITERS}}
+    line.update({k: v for k, v in r.items() if k not in ("graphs", "vertices", "edges", "workload")})
     print(json.dumps(line), flush=True)
+
+
+def single_leg(name, steps, flush, torch, max_iters=MAX_ITERS):
+    """One named single-graph workload: `steps` timed LM solves per precision
+    (one warm-up each) from the drifted estimate, device-resident inputs, L2
+    flushed before each, CUDA events on the graph's stream."""
+    from paper_2603_17201_gb300 import PoseGraph
+    from paper_2603_17201_gb300 import synthetic as syn
+    g = syn.make_config(name)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t = lambda a, dt=torch.float64: torch.as_tensor(a, dtype=dt, device=dev)  # noqa: E731
+    init = t(g.poses_init)
+    pg = PoseGraph(g.n_vertices, t(g.edge_i, torch.int32), t(g.edge_j, torch.int32), t(g.meas), None, None, init, 0)
+    stream = torch.cuda.current_stream(dev)
+    out = {"workload": name, "n_vertices": g.n_vertices, "n_edges": g.n_edges, "max_lm_iters": max_iters}
+    for precision in ("fp64", "mixed"):
+        ms, rep = [], None
+        for k in range(steps + 1):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            pg.set_poses(init)
+            pg.solve_async(max_iters=max_iters, precision=precision)
+            e1.record(stream)
+            e1.synchronize()
+            rep = pg.solve_report()
+            if k > 0:
+                ms.append(e0.elapsed_time(e1))
+        m = statistics.median(ms)
+        out[precision] = {"ms_per_solve": m, "edges_per_s": g.n_edges * rep["iterations"] / (m * 1e-3),
+                          "lm_iterations": rep["iterations"], "pcg_iterations": rep["pcg_iterations"],
+                          "final_cost": rep["final_cost"], "stop_reason": rep["stop_reason"]}
+    out["speedup_mixed_vs_fp64"] = out["fp64"]["ms_per_solve"] / out["mixed"]["ms_per_solve"]
+    out["rel_cost_mixed_vs_fp64"] = abs(out["mixed"]["final_cost"] - out["fp64"]["final_cost"]) / out["fp64"]["final_cost"]
+    pg.close()
+    return out
+
+
+def adjoint_leg(steps, torch):
+    """The differentiation workload (4,000-keyframe noisy figure-8, 67,857
+    edges, weights 1): FP64 forward solve to a stationary point (LM plus
+    Newton polish), then pgo_backward for a seeded loss gradient dL/dx (N x 7
+    on the device): gradients w.r.t. every measurement and weight.  Wall time
+    of each call (both synchronise), median over `steps`."""
+    import numpy as np
+    from paper_2603_17201_gb300 import PoseGraph
+    from paper_2603_17201_gb300 import synthetic as syn
+    g = syn.make_config("c5_figure8_4k_noisy")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    t = lambda a, dt=torch.float64: torch.as_tensor(a, dtype=dt, device=dev)  # noqa: E731
+    init = t(g.poses_init)
+    pg = PoseGraph(g.n_vertices, t(g.edge_i, torch.int32), t(g.edge_j, torch.int32), t(g.meas),
+                   t(np.ones(g.n_edges)), None, init, 0)
+    dl = t(np.random.default_rng(5).normal(size=(g.n_vertices, 7)))
+    opts = dict(max_iters=60, polish_iters=10, gtol=1e-15, pcg_tol=1e-12, pcg_max_iters=20000)
+    fwd, bwd, rep = [], [], None
+    for k in range(steps + 1):
+        pg.set_poses(init)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rep = pg.solve(**opts)
+        t1 = time.perf_counter()
+        pg.backward(dl, layout="tangent", pcg_tol=1e-12, pcg_max_iters=20000)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        if k > 0:
+            fwd.append(1e3 * (t1 - t0))
+            bwd.append(1e3 * (t2 - t1))
+    pg.close()
+    return {"workload": "c5_figure8_4k_noisy", "n_vertices": g.n_vertices, "n_edges": g.n_edges,
+            "forward_ms": statistics.median(fwd), "backward_ms": statistics.median(bwd),
+            "forward_lm_iterations": rep["iterations"], "grad_inf_norm": rep["grad_inf_norm"],
+            "precision": "fp64"}
 
 
 # --------------------------------------------------------------------- our arm
@@ -402,6 +579,12 @@ def run_ours(args):
             launches = sum(launches_per_solve(precision, k) for k in its)
 
     roofline = roofline_leg(pg, N, E, stream, flush, torch)
+    roofline_setup = setup_leg(pg, N, E, stream, flush, torch)
+    extra = {}
+    if not args.no_extra and world == 1:
+        extra["c3"] = single_leg("c3_corridor_8k", 3, flush, torch)
+        extra["c5_adjoint"] = adjoint_leg(2, torch)
+        extra["c4_batch"] = batch_leg(1, sample=16)
 
     # ---- correctness gate: final cost vs the FP64 oracle ----
     cpu = None
@@ -410,7 +593,8 @@ def run_ours(args):
         for precision in ("fp64", "mixed"):
             rel = abs(results[precision]["final_cost"] - orep["final_cost"]) / orep["final_cost"]
             results[precision]["rel_cost_err_vs_oracle"] = rel
-        cpu = {"value": E * orep["iterations"] / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+        cpu = {"value": E * orep["iterations"] / dt, "unit": UNIT, "cores": 1, "host_cores": host_cores(),
+               "kind": "oracle",
                "sample": f"one full LM solve of {args.workload} ({orep['iterations']} iterations, "
                          f"{dt:.1f} s, single thread)"}
 
@@ -444,15 +628,14 @@ def run_ours(args):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed["ms_per_solve"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64",
             "data": "synthetic",
-            "config": {"workload": args.workload, "n_vertices": N, "n_edges": E, "max_lm_iters": MAX_ITERS,
-                       "graph": "figure-8 3-D trajectory, 2 laps, covisibility window 15, 5 loop edges",
-                       "l2": "flushed before every timed step (256 MB write)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": workload_config(args.workload, g, world),
             "mixed": mixed, "fp64": results["fp64"],
             "speedup_mixed_vs_fp64": results["fp64"]["ms_per_solve"] / mixed["ms_per_solve"],
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
+            "roofline": roofline, "roofline_setup": roofline_setup,
+            "cpu_baseline": cpu, "e2e": e2e, "clocks": clocks,
             "gpu_launches": launches,
         }
+        line.update(extra)
         print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -93,8 +93,10 @@ typedef struct {
  * (recursively), block-Jacobi smoothing, dense coarsest solve; its sparsity
  * is analysed once per graph on the host at the first solve that uses it.
  * Both are symmetric positive definite, so either gives the same solution
- * to the PCG tolerance; they differ in iteration count.  The batched solve
- * always uses block-Jacobi. */
+ * to the PCG tolerance; they differ in iteration count.  Every solve entry
+ * point honours this choice: pgo_solve, pgo_graph_damped_step,
+ * pgo_graph_resolve, pgo_backward and the batched pgo_batch_solve (where the
+ * hierarchy has one independent segment per graph). */
 typedef enum { PGO_PRECOND_BLOCK_JACOBI = 0, PGO_PRECOND_MULTIGRID = 1 } pgo_preconditioner;
 
 /* Solve options.  pgo_default_options() fills the documented defaults. */
@@ -195,8 +197,10 @@ pgo_status pgo_graph_linearize(pgo_graph* g, int32_t precision, double* jac, dou
                                double* h_off, double* b, int32_t mem_space);
 
 /* One damped linear solve at the current estimate (Sec. IV-F linear solver):
- * (H + lambda I) delta = -b with the block-Jacobi preconditioned conjugate
- * gradient method, the fixed vertex's rows and columns removed.
+ * (H + lambda I) delta = -b by the preconditioned conjugate gradient method
+ * with the preconditioner opt->preconditioner names (block-Jacobi or
+ * multigrid; opt NULL = defaults), in opt->precision (mixed: FP32 PCG inside
+ * FP64 refinement), the fixed vertex's rows and columns removed.
  * delta: double[n_vertices * 7] in mem_space (fixed row = 0).  *pcg_iters
  * (host, nullable) receives the iteration count.  Returns
  * PGO_ERR_NOT_CONVERGED when opt->pcg_max_iters is reached (delta is still
@@ -213,6 +217,17 @@ pgo_status pgo_graph_damped_step(pgo_graph* g, const pgo_solve_options* opt, dou
  * work on the graph's stream and returns. */
 pgo_status pgo_graph_resolve(pgo_graph* g, const pgo_solve_options* opt, double lambda, double* delta,
                              int32_t* pcg_iters, int32_t mem_space);
+
+/* The preconditioner set-up of one linear solve at the last linearisation
+ * (the one made by pgo_graph_linearize, pgo_graph_damped_step or pgo_solve,
+ * in the precision opt->precision names), without the solve (Sec. IV-F
+ * linear solver; a piece of pgo_graph_resolve for timing and composition):
+ * the inverse damped diagonal blocks (H_vv + lambda I)^-1 and, for
+ * PGO_PRECOND_MULTIGRID, the numeric multigrid hierarchy (smoothed
+ * prolongations, Galerkin coarse operators, coarsest inverse).  Enqueued on
+ * the graph's stream; no synchronisation.  PGO_ERR_STATE without a
+ * linearisation. */
+pgo_status pgo_graph_precondition(pgo_graph* g, const pgo_solve_options* opt, double lambda);
 
 /* Fill *report from the device state of the last pgo_solve (synchronises the
  * graph's stream); use after a pgo_solve called with report == NULL. */
@@ -287,13 +302,17 @@ pgo_status pgo_batch_schedule(const pgo_batch* b, int32_t* lanes, int32_t* threa
 /* Stateless cost evaluation (the Sec. IV-F objective) over caller-owned
  * device arrays: n_vertices poses (pose8), n_edges edges (edge_i, edge_j,
  * meas pose8, weight nullable).  *cost_out is a device double written on
- * `stream`.  Uses a temporary device workspace of one double per thread
- * block, allocated and freed on the stream (stream-ordered allocator).
- * No validation of indices beyond a device-side bounds check that skips and
- * counts bad edges; returns PGO_ERR_INVALID_ARG for negative sizes. */
+ * `stream`.  An edge with an endpoint outside [0, n_vertices) or with
+ * i == j is skipped; *bad_edges_out (device int32, nullable) receives the
+ * number of skipped edges on the same stream, so a caller that passes it can
+ * tell a complete cost from a partial one.  Uses a temporary device
+ * workspace of one double per thread block, allocated and freed on the
+ * stream (stream-ordered allocator).  Returns PGO_ERR_INVALID_ARG for
+ * negative sizes or NULL arrays. */
 pgo_status pgo_evaluate_cost(int32_t n_vertices, int32_t n_edges, const int32_t* edge_i,
                              const int32_t* edge_j, const double* meas, const double* weight,
-                             const double* poses, double* cost_out, void* stream);
+                             const double* poses, double* cost_out, int32_t* bad_edges_out,
+                             void* stream);
 
 /* pgo_evaluate_cost without any device allocation (no counterpart in the
  * paper: an addition for callers that cannot allocate device memory at call
@@ -304,16 +323,19 @@ pgo_status pgo_evaluate_cost(int32_t n_vertices, int32_t n_edges, const int32_t*
  * library's device image, held by every GPU that loads the library until the
  * process exits.  Limits and rules:
  *   - n_edges <= 1,048,576, else PGO_ERR_INVALID_ARG (use pgo_evaluate_cost);
- *   - the first call on each device, with that device current, looks up the
- *     workspace address (cudaGetSymbolAddress) and caches it: make that first
- *     call before any stream capture;
+ *   - the first call in each CUDA context, with that context's device
+ *     current, looks up the workspace address (cudaGetSymbolAddress) and
+ *     caches it with the context's unique id (a new context, e.g. after
+ *     cudaDeviceReset, triggers a new look-up): make that first call before
+ *     any stream capture;
  *   - every call shares the one workspace and it keeps the last call's
  *     contents (each call clears its counters first); calls that overlap on
  *     the GPU, from several streams or threads, race and must be avoided;
  *   - it calls no cudaMalloc, cudaFree or allocating library routine. */
 pgo_status pgo_evaluate_cost_noalloc(int32_t n_vertices, int32_t n_edges, const int32_t* edge_i,
                                      const int32_t* edge_j, const double* meas, const double* weight,
-                                     const double* poses, double* cost_out, void* stream);
+                                     const double* poses, double* cost_out, int32_t* bad_edges_out,
+                                     void* stream);
 
 #ifdef __cplusplus
 }

@@ -246,6 +246,12 @@ class PoseGraph:
         o = L.default_options(**opts)
         L.check(self._lib.pgo_graph_resolve(self._h, ctypes.byref(o), float(lam), None, None, L.PGO_MEM_HOST))
 
+    def precondition_async(self, lam, **opts):
+        """Enqueue the preconditioner set-up at the last linearisation for
+        ``lam`` on the graph's stream (no synchronisation)."""
+        o = L.default_options(**opts)
+        L.check(self._lib.pgo_graph_precondition(self._h, ctypes.byref(o), float(lam)))
+
     def multigrid_info(self):
         """Shape of the multigrid hierarchy: list of dicts (nodes, blocks of
         the operator, of P and of A P) per level, the coarsest last."""
@@ -397,13 +403,16 @@ def solve_pose_graph(graph, meas, weight, poses0, **opts):
     return _SolveFunction.get().apply(meas, weight, graph, poses0, opts)
 
 
-def evaluate_cost(n_vertices, edge_i, edge_j, meas, weight, poses):
+def evaluate_cost(n_vertices, edge_i, edge_j, meas, weight, poses, return_bad=False):
     """Stateless F over CUDA tensors (int32 edges, float64 pose8 arrays);
-    returns a 0-d CUDA tensor written on the current stream."""
+    returns a 0-d CUDA tensor written on the current stream (and, with
+    ``return_bad``, a 0-d int32 CUDA tensor counting the skipped edges whose
+    endpoints are out of range or equal)."""
     torch = _torch()
     lib = L.load()
     out = torch.empty((), dtype=torch.float64, device="cuda")
+    bad = torch.zeros((), dtype=torch.int32, device="cuda")
     ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
     L.check(lib.pgo_evaluate_cost(int(n_vertices), int(edge_i.numel()), ptr(edge_i), ptr(edge_j), ptr(meas),
-                                  ptr(weight), ptr(poses), ptr(out), _current_stream_handle()))
-    return out
+                                  ptr(weight), ptr(poses), ptr(out), ptr(bad), _current_stream_handle()))
+    return (out, bad) if return_bad else out

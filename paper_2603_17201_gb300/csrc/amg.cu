@@ -835,7 +835,7 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
   const AmgDev& A = sA;
   unsigned* counter = &st->ticket[T_AMG];
   int* abort_flag = reinterpret_cast<int*>(&st->ticket[T_AMG_ABORT]);
-  unsigned target = 0;
+  GridTarget target(g.opt->barrier_limit_ns);
   constexpr int BLK = AV<V>::BLK;
   const V lam = V(st->lambda);
   const int cur = st->cur;
@@ -1092,7 +1092,13 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
   grid_sync_release(&st->ticket[T_AMG_DONE], counter, nullptr);
   return;
 timeout:
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->status = PGO_ERR_CUDA;
+  // a barrier wait ran out: stop the solve and report a device failure
+  // (every block that gave up writes the same values: block 0 may be the absent one)
+  if (threadIdx.x == 0) {
+    st->status = PGO_ERR_CUDA;
+    st->stop_reason = 4;
+    st->done = 1;
+  }
 }
 
 static int amg_sms() {

@@ -85,11 +85,13 @@ __global__ void k_scatter(int n, int width, const int* perm, const double* src, 
 }
 
 // Stateless cost over caller arrays (pose8 poses and measurements).  Edges
-// with an endpoint out of range, or i == j, are skipped and counted in *bad.
+// with an endpoint out of range, or i == j, are skipped and counted in *bad
+// (zeroed by the caller); the last block copies the count to *bad_out.
 __global__ void __launch_bounds__(256) k_eval_cost_raw(int N, int E, const int* ei, const int* ej,
                                                        const double* meas, const double* w,
                                                        const double* poses, double* partial,
-                                                       unsigned* ticket, int* bad, double* cost_out) {
+                                                       unsigned* ticket, int* bad, double* cost_out,
+                                                       int* bad_out) {
   __shared__ double sh[32];
   double c[1] = {0.0};
   int nbad = 0;
@@ -132,7 +134,11 @@ __global__ void __launch_bounds__(256) k_eval_cost_raw(int N, int E, const int* 
   if (!publish_partials<1>(c, partial, ticket)) return;
   double tot[1];
   gather_partials_sum<1>(partial, tot, sh);
-  if (threadIdx.x == 0) *cost_out = tot[0];
+  if (threadIdx.x == 0) {
+    *cost_out = tot[0];
+    // every block added its count before publishing its partial
+    if (bad_out) *bad_out = atomicAdd(bad, 0);
+  }
 }
 
 // Exact Jacobians A_i, A_j per edge (caller order, E x 2 x 49) at `buf`.
@@ -199,15 +205,15 @@ int eval_cost_blocks(int E) {
 }
 void launch_eval_cost_raw(int N, int E, const int* ei, const int* ej, const double* meas, const double* w,
                           const double* poses, double* partial, unsigned* ticket, int* bad,
-                          double* cost_out, cudaStream_t s) {
+                          double* cost_out, int* bad_out, cudaStream_t s) {
   k_eval_cost_raw<<<eval_cost_blocks(E), 256, 0, s>>>(N, E, ei, ej, meas, w, poses, partial, ticket, bad,
-                                                      cost_out);
+                                                      cost_out, bad_out);
 }
 
 void launch_eval_cost_raw_blocks(int N, int E, const int* ei, const int* ej, const double* meas, const double* w,
                                  const double* poses, double* partial, unsigned* ticket, int* bad,
-                                 double* cost_out, int blocks, cudaStream_t s) {
-  k_eval_cost_raw<<<blocks, 256, 0, s>>>(N, E, ei, ej, meas, w, poses, partial, ticket, bad, cost_out);
+                                 double* cost_out, int* bad_out, int blocks, cudaStream_t s) {
+  k_eval_cost_raw<<<blocks, 256, 0, s>>>(N, E, ei, ej, meas, w, poses, partial, ticket, bad, cost_out, bad_out);
 }
 
 }  // namespace pgo

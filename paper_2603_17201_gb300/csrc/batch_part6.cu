@@ -1,0 +1,12 @@
+// Persistent batch kernel, compiled for two of its launch schedules (the
+// schedules are split over eight translation units that compile in parallel).
+#include "batch_impl.cuh"
+
+namespace pgo {
+
+template cudaError_t launch_batch_instance<1, 16, 512, 1>(const DevGraph&, const BatchArgs&, int, size_t,
+                                                            cudaStream_t);
+template cudaError_t launch_batch_instance<1, 4, 256, 2>(const DevGraph&, const BatchArgs&, int, size_t,
+                                                            cudaStream_t);
+
+}  // namespace pgo

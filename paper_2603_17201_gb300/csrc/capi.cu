@@ -50,6 +50,10 @@ pgo_status fail(pgo_status st, const char* fmt, ...) {
 
 // Test hook: fail device allocations above this many bytes (0 = off).
 size_t g_alloc_limit = 0;
+// Test hooks of the bounded grid barrier: a PCG block that never arrives
+// (-1 = off) and the wait limit in ns (0 = the 2 s default).
+int g_test_absent_block = -1;
+unsigned long long g_barrier_limit_ns = 0;
 
 // One device arena per graph, sub-allocated with 256-byte alignment.
 struct Arena {
@@ -176,6 +180,8 @@ void fill_dev_options(const pgo_solve_options& o, DevOptions* d) {
   d->refine_tol = o.refine_tol;
   d->lambda_fixed = 0.0;
   d->amg_refresh = o.multigrid_refresh;
+  d->test_absent_block = g_test_absent_block;
+  d->barrier_limit_ns = g_barrier_limit_ns;
 }
 
 pgo_status check_options(const pgo_solve_options& o) {
@@ -425,6 +431,16 @@ const char* pgo_version(void) { return "pgo-gb300 0.1 (sm_103a)"; }
 
 // Test hook (not in the public header): cap device allocations in bytes.
 void pgo_test_set_alloc_limit(size_t bytes) { g_alloc_limit = bytes; }
+
+// Test hook (not in the public header): the grid-barrier wait limit of later
+// solves (seconds, <= 0 restores the 2 s default) and a block of the PCG
+// launch that never arrives at its barriers (-1 = none).  With a block absent
+// the other blocks wait out the limit, the solve stops and reports
+// PGO_ERR_CUDA: this exercises the bounded wait without any device fault.
+void pgo_test_set_barrier(double limit_s, int absent_block) {
+  g_barrier_limit_ns = limit_s > 0.0 ? (unsigned long long)(limit_s * 1e9) : 0ull;
+  g_test_absent_block = absent_block;
+}
 
 pgo_status pgo_default_options(pgo_solve_options* opt) {
   if (!opt) return fail(PGO_ERR_INVALID_ARG, "opt is NULL");
@@ -766,6 +782,7 @@ pgo_status pgo_graph_linearize(pgo_graph* G, int32_t precision, double* jac, dou
   launch_linearize(g, precision == PGO_MIXED, s);
   launch_assemble(g, precision == PGO_MIXED, s);
   CUDA_TRY(cudaGetLastError());
+  G->lin_valid = true;
   const int E = G->E, N = G->N;
   double* tmp = G->d_scratch;
   if (jac) {
@@ -814,6 +831,7 @@ pgo_status pgo_graph_damped_step(pgo_graph* G, const pgo_solve_options* opt, dou
   if (st != PGO_OK) return st;
   cudaStream_t s = G->stream;
   CUDA_TRY(cudaGraphLaunch(ex, s));
+  G->lin_valid = true;
   launch_scatter(G->N, 7, nullptr, mixed ? G->g.dx64 : G->g.x64, VEC, G->d_scratch, 7, s);
   CUDA_TRY(cudaGetLastError());
   CUDA_TRY(cudaMemcpyAsync(G->h_state, G->g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
@@ -917,6 +935,28 @@ pgo_status pgo_graph_resolve(pgo_graph* G, const pgo_solve_options* opt, double 
   if (pcg_iters) *pcg_iters = G->h_state->pcg_total;
   if (G->h_state->status) return fail((pgo_status)G->h_state->status, "re-solve failed on the device");
   if (G->h_state->pcg_hit_cap) return fail(PGO_ERR_NOT_CONVERGED, "PCG reached pcg_max_iters (%d)", o.pcg_max_iters);
+  return PGO_OK;
+}
+
+pgo_status pgo_graph_precondition(pgo_graph* G, const pgo_solve_options* opt, double lambda) {
+  if (!G) return fail(PGO_ERR_INVALID_ARG, "graph is NULL");
+  if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(PGO_ERR_INVALID_ARG, "lambda must be finite and >= 0");
+  if (!G->lin_valid) return fail(PGO_ERR_STATE, "no linearisation to precondition (linearise or solve first)");
+  pgo_solve_options o;
+  if (opt) o = *opt; else pgo_default_options(&o);
+  pgo_status st = check_options(o);
+  if (st != PGO_OK) return st;
+  st = ensure_amg(G, o.preconditioner);
+  if (st != PGO_OK) return st;
+  cudaStream_t s = G->stream;
+  fill_dev_options(o, G->h_opt);
+  G->h_opt->lambda_fixed = lambda;
+  CUDA_TRY(cudaMemcpyAsync(G->g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
+  launch_resolve_reset(G->g, s);
+  cudaError_t le = cudaSuccess;
+  enqueue_precond(G->g, o.precision == PGO_MIXED, amg_for(G, o.preconditioner), s, &le);
+  CUDA_TRY(le);
+  CUDA_TRY(cudaGetLastError());
   return PGO_OK;
 }
 
@@ -1442,7 +1482,7 @@ pgo_status pgo_batch_schedule(const pgo_batch* B, int32_t* lanes, int32_t* threa
 
 pgo_status pgo_evaluate_cost(int32_t n_vertices, int32_t n_edges, const int32_t* edge_i, const int32_t* edge_j,
                              const double* meas, const double* weight, const double* poses, double* cost_out,
-                             void* stream) {
+                             int32_t* bad_edges_out, void* stream) {
   if (n_vertices < 0 || n_edges < 0) return fail(PGO_ERR_INVALID_ARG, "negative size");
   if (!cost_out) return fail(PGO_ERR_INVALID_ARG, "cost_out is NULL");
   if (n_edges > 0 && (!edge_i || !edge_j || !meas || !poses)) return fail(PGO_ERR_INVALID_ARG, "NULL input array");
@@ -1457,7 +1497,8 @@ pgo_status pgo_evaluate_cost(int32_t n_vertices, int32_t n_edges, const int32_t*
   int* bad = reinterpret_cast<int*>(ticket + 4);
   cudaError_t e = cudaMemsetAsync(ticket, 0, 64, s);
   if (e == cudaSuccess) {
-    launch_eval_cost_raw(n_vertices, n_edges, edge_i, edge_j, meas, weight, poses, partial, ticket, bad, cost_out, s);
+    launch_eval_cost_raw(n_vertices, n_edges, edge_i, edge_j, meas, weight, poses, partial, ticket, bad, cost_out,
+                         bad_edges_out, s);
     e = cudaGetLastError();
   }
   cudaError_t e2 = cudaFreeAsync(ws, s);

@@ -50,6 +50,8 @@ struct DevOptions {
   double tau, lambda_init, ftol, gtol, pcg_tol, refine_tol;
   double lambda_fixed;   // lambda of a standalone re-solve
   int amg_refresh;       // rebuild the coarse multigrid levels every k-th LM linearisation
+  int test_absent_block; // test hook: this block of the PCG launch never arrives (-1: none)
+  unsigned long long barrier_limit_ns;   // grid-barrier wait limit (0: the 2 s default)
 };
 
 // ---- smoothed-aggregation multigrid preconditioner ----
@@ -268,10 +270,10 @@ void launch_jacobians_out(const DevGraph& g, int buf, const int* perm, double* o
 int eval_cost_blocks(int E);
 void launch_eval_cost_raw(int N, int E, const int* ei, const int* ej, const double* meas, const double* w,
                           const double* poses, double* partial, unsigned* ticket, int* bad,
-                          double* cost_out, cudaStream_t s);
+                          double* cost_out, int* bad_out, cudaStream_t s);
 void launch_eval_cost_raw_blocks(int N, int E, const int* ei, const int* ej, const double* meas, const double* w,
                                  const double* poses, double* partial, unsigned* ticket, int* bad,
-                                 double* cost_out, int blocks, cudaStream_t s);
+                                 double* cost_out, int* bad_out, int blocks, cudaStream_t s);
 void set_last_error(const char* msg);   // message returned by pgo_last_error()
 
 }  // namespace pgo

@@ -10,15 +10,18 @@
 // workspace that lives in the library's own device image instead.
 //
 // The workspace is a file-scope device array.  Host code cannot use the
-// array's name as a device address, so the first call on each device, with
-// that device current, looks its address up with cudaGetSymbolAddress and
-// keeps it; later calls on that device reuse the cached address.  That first
-// call should therefore come before any stream capture.
+// array's name as a device address, so the first call in each CUDA context
+// (with that context's device current) looks its address up with
+// cudaGetSymbolAddress and keeps it with the context's unique id; later calls
+// in the same context reuse the cached address, and a call in a new context
+// (after cudaDeviceReset, say) looks it up again.  That first call should
+// therefore come before any stream capture.
 //
 // Every call shares the one workspace and it keeps the previous call's
 // contents, so each call clears the counters it needs before launching.  Calls
 // that overlap on the GPU (on different streams, or from several threads)
 // race on the workspace and must not be issued.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdio>
@@ -40,12 +43,44 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 constexpr int kMaxDevices = 64;
 std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
+unsigned long long g_scratch_ctx[kMaxDevices] = {};   // unique id of the context of the cached address
+
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
+// Unique id of the calling thread's current CUDA context (0: none, or the
+// driver entry points are unavailable, which forces a fresh look-up).
+unsigned long long current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static bool resolved = false;
+  if (!resolved) {
+    cudaDriverEntryPointQueryResult q;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    cudaGetLastError();
+    resolved = true;
+  }
+  if (!get_current || !get_id) return 0;
+  CUcontext ctx = nullptr;
+  unsigned long long id = 0;
+  if (get_current(&ctx) != CUDA_SUCCESS || !ctx) return 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return id;
+}
 
 }  // namespace
 
 extern "C" pgo_status pgo_evaluate_cost_noalloc(int32_t n_vertices, int32_t n_edges, const int32_t* edge_i,
                                                 const int32_t* edge_j, const double* meas, const double* weight,
-                                                const double* poses, double* cost_out, void* stream) {
+                                                const double* poses, double* cost_out, int32_t* bad_edges_out,
+                                                void* stream) {
   auto fail = [](pgo_status st, const char* msg) {
     pgo::set_last_error(msg);
     return st;
@@ -70,7 +105,8 @@ extern "C" pgo_status pgo_evaluate_cost_noalloc(int32_t n_vertices, int32_t n_ed
   void* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_setup_mutex);
-    if (!g_scratch_addr[dev]) {
+    const unsigned long long ctx = current_context_id();
+    if (!g_scratch_addr[dev] || ctx == 0 || ctx != g_scratch_ctx[dev]) {
       void* p = nullptr;
       const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
       if (e != cudaSuccess || !p) {
@@ -78,6 +114,7 @@ extern "C" pgo_status pgo_evaluate_cost_noalloc(int32_t n_vertices, int32_t n_ed
         return fail(PGO_ERR_CUDA, "pgo_evaluate_cost_noalloc: cudaGetSymbolAddress of the workspace failed");
       }
       g_scratch_addr[dev] = p;
+      g_scratch_ctx[dev] = current_context_id();   // the look-up made the device's context current
     }
     base = g_scratch_addr[dev];
   }
@@ -92,7 +129,7 @@ extern "C" pgo_status pgo_evaluate_cost_noalloc(int32_t n_vertices, int32_t n_ed
   }
   const int blocks = n_edges > 0 ? (n_edges + 255) / 256 : 1;
   pgo::launch_eval_cost_raw_blocks(n_vertices, n_edges, edge_i, edge_j, meas, weight, poses, partial, ticket, bad,
-                                   cost_out, blocks, s);
+                                   cost_out, bad_edges_out, blocks, s);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(PGO_ERR_CUDA, cudaGetErrorString(e));
   return PGO_OK;

@@ -410,7 +410,7 @@ constexpr int GC = 32;
 // false on a barrier timeout.
 template <class V, class S, int G>
 __device__ bool vcycle_rest(const DevGraph& g, const AmgDev& A, const L0Ctx<V>& c0, const V* r0v, V* s0, V* z,
-                            S& rz_loc, unsigned* counter, int* abort_flag, unsigned& target) {
+                            S& rz_loc, unsigned* counter, int* abort_flag, GridTarget& target) {
   constexpr int BLK = AV<V>::BLK;
   const int sl = threadIdx.x & (G - 1);
   const int sslot = threadIdx.x / G;
@@ -673,7 +673,9 @@ __global__ void __launch_bounds__(sizeof(V) == 8 ? 256 : 512) k_pcg(DevGraph g, 
   unsigned* counter = &st->ticket[T_PCG_SPMV];
   int* abort_flag = reinterpret_cast<int*>(&st->ticket[T_PCG_UPDATE]);
   S* partial = reinterpret_cast<S*>(g.partial);
-  unsigned target = 0;
+  GridTarget target(o->barrier_limit_ns);
+  // test hook: this block never arrives, so the others reach the wait limit
+  if ((int)blockIdx.x == o->test_absent_block) return;
 
   const int sl = threadIdx.x & (G - 1);        // SpMV: lane within the row's group of G
   const int sslot = threadIdx.x / G;
@@ -914,7 +916,14 @@ __global__ void __launch_bounds__(sizeof(V) == 8 ? 256 : 512) k_pcg(DevGraph g, 
   }
   return;
 timeout:
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->status = PGO_ERR_CUDA;
+  // a barrier wait ran out: stop the solve (later kernels of this LM
+  // iteration see done and return) and report a device failure
+  // (every block that gave up writes the same values: block 0 may be the absent one)
+  if (threadIdx.x == 0) {
+    st->status = PGO_ERR_CUDA;
+    st->stop_reason = 4;
+    st->done = 1;
+  }
   return;
 }
 

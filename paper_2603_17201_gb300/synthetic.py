@@ -36,7 +36,7 @@ import dataclasses
 import numpy as np
 
 __all__ = [
-    "PoseGraph", "make_graph", "make_config", "make_batch", "CONFIGS",
+    "PoseGraph", "make_graph", "make_config", "make_batch", "batch_sizes", "CONFIGS",
     "compose", "inverse", "quat_mul", "quat_rotate",
 ]
 
@@ -368,16 +368,24 @@ def make_config(name, **overrides):
     return make_graph(name=name, **kw)
 
 
+def batch_sizes(n_graphs=256, seed0=1000, n_min=100, n_max=5000):
+    """Keyframe counts of the batched workload's graphs (graph k draws its
+    size from seed ``seed0 + k``)."""
+    return [int(np.random.Generator(np.random.PCG64(seed0 + k)).integers(n_min, n_max + 1))
+            for k in range(n_graphs)]
+
+
 def make_batch(n_graphs=256, seed0=1000, n_min=100, n_max=5000, window=15,
-               kf_per_loop=400, noise=(0.01, 0.02, 0.01)):
+               kf_per_loop=400, noise=(0.01, 0.02, 0.01), only=None):
     """The batched workload: ``n_graphs`` independent figure-8 graphs with
     keyframe counts drawn uniformly from [n_min, n_max], covisibility window
     ``window`` and one loop edge per ``kf_per_loop`` keyframes.  Graph k uses
-    seed ``seed0 + k`` for both its size and its noise."""
+    seed ``seed0 + k`` for both its size and its noise.  ``only``: build just
+    these graph indices (same graphs as in the full batch)."""
+    sizes = batch_sizes(n_graphs, seed0, n_min, n_max)
     out = []
-    for k in range(n_graphs):
-        rng = np.random.Generator(np.random.PCG64(seed0 + k))
-        n = int(rng.integers(n_min, n_max + 1))
+    for k in (range(n_graphs) if only is None else only):
+        n = sizes[k]
         loops = max(1, n // kf_per_loop)
         out.append(make_graph("figure8", n, seed=seed0 + k, window=window,
                               n_loops=loops, noise=noise, name=f"batch{k}"))

@@ -96,5 +96,24 @@ def test_null_arguments(lib):
     assert lib.pgo_graph_create(None, ctypes.byref(h)) == L.PGO_ERR_INVALID_ARG
     assert lib.pgo_default_options(None) == L.PGO_ERR_INVALID_ARG
     assert lib.pgo_solve(None, None, None, None, 0) == L.PGO_ERR_INVALID_ARG
-    assert lib.pgo_evaluate_cost(-1, 0, None, None, None, None, None, None, None) == L.PGO_ERR_INVALID_ARG
+    assert lib.pgo_evaluate_cost(-1, 0, None, None, None, None, None, None, None, None) == L.PGO_ERR_INVALID_ARG
     lib.pgo_graph_destroy(None)
+
+
+def test_allocation_limit_gives_oom_and_no_handle(lib):
+    """The device-allocation test hook: graph creation needs more than the
+    limit, so it fails with PGO_ERR_OOM before touching the device, and the
+    handle stays NULL (no GPU needed: the check precedes every CUDA call)."""
+    g = syn.make_graph("circle", 40, seed=2)
+    d, keep = _desc(g.n_vertices, g.edge_i, g.edge_j, g.meas)
+    lib.pgo_test_set_alloc_limit.argtypes = [ctypes.c_size_t]
+    lib.pgo_test_set_alloc_limit.restype = None
+    lib.pgo_test_set_alloc_limit(4096)
+    try:
+        h = ctypes.c_void_p()
+        st = lib.pgo_graph_create(ctypes.byref(d), ctypes.byref(h))
+        assert st == L.PGO_ERR_OOM
+        assert h.value is None
+        assert b"exceeds the test limit" in lib.pgo_last_error()
+    finally:
+        lib.pgo_test_set_alloc_limit(0)
