@@ -89,6 +89,8 @@ def load():
     lib.og_adjoint.argtypes = [ctypes.c_void_p, _dp, _dp, ctypes.c_double, _dp, _dp, _dp]
     lib.og_pose_loss.restype = ctypes.c_double
     lib.og_pose_loss.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
+    lib.og_propagate_correction.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int, _ip, _dp]
+    lib.og_correct_points.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _ip, _dp]
     _lib = lib
     return lib
 
@@ -278,3 +280,37 @@ def pose_error(a, b):
 
 
 __all__ += ["pose_error"]
+
+
+# ---------------------------------------------------------------- loop correction
+def propagate_correction(poses, current, corrected, connected):
+    """Loop correction before the pose graph optimisation (Sec. III-B): the
+    keyframes in ``connected`` take S_k' = (S_k S_c^-1) S_c' with S_c' =
+    ``corrected`` the new pose of keyframe ``current``; others are copied.
+    Returns the (N, 8) pose array."""
+    poses = _f64(poses)
+    n = poses.shape[0]
+    conn = np.ascontiguousarray(connected, dtype=np.int32)
+    corr = _f64(corrected, (8,))
+    out = np.empty((n, 8))
+    load().og_propagate_correction(n, _d(poses), int(current), _d(corr), int(conn.shape[0]),
+                                   conn.ctypes.data_as(_ip), _d(out))
+    return out
+
+
+def correct_points(before, after, points, ref):
+    """Map-point correction (Sec. III-B): x' = S_after[r]^-1 (S_before[r] x)
+    through each point's reference keyframe r (r < 0: unchanged).  Returns
+    the (P, 3) array."""
+    before = _f64(before)
+    after = _f64(after, before.shape)
+    X = _f64(points)
+    P = X.shape[0]
+    X = X.reshape(P, 3)
+    r = np.ascontiguousarray(ref, dtype=np.int32)
+    out = np.empty((P, 3))
+    load().og_correct_points(before.shape[0], _d(before), _d(after), P, _d(X), r.ctypes.data_as(_ip), _d(out))
+    return out
+
+
+__all__ += ["propagate_correction", "correct_points"]

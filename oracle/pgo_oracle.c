@@ -33,11 +33,19 @@
  *   else lambda *= nu, nu *= 2;  lambda_0 = tau * max diag(H);
  *   one fixed gauge vertex; quaternions renormalised after each update.
  *
+ * Around the optimisation, the loop-correction steps of Sec. III-B: the
+ * connected keyframes take the loop's Sim(3) correction before it
+ * (og_propagate_correction) and map points follow their reference keyframe
+ * (og_correct_points), both written as the compositions they are.
+ *
  * Parity pins (tests): exp/log round trips and the closed-form limits of the
  * V matrix, central finite differences of the Jacobians, zero cost on
  * noise-free graphs, gauge invariance of the final cost, the closed-form
  * translation-only ring, dense and scipy cross-checks of the linear solve,
- * and brute-force finite differences of the whole solve for the adjoint.
+ * and brute-force finite differences of the whole solve for the adjoint;
+ * for the loop correction a hand-worked example, the identity correction,
+ * the closed form of a change of world frame and the invariance of a point
+ * in its reference camera.
  */
 #include <math.h>
 #include <stdint.h>
@@ -1035,4 +1043,60 @@ EXPORT double og_pose_loss(void *hg, const double *poses, const double *gt, doub
     }
   }
   return L;
+}
+
+/* ------------------------------------------------------------------ */
+/* Loop correction around the pose graph optimisation (Sec. III-B,     */
+/* "Loop Correction")                                                  */
+/* ------------------------------------------------------------------ */
+
+/* x -> s R x + t */
+static void sim3_apply(const sim3 *S, const double *x, double *y) {
+  double Rx[3];
+  mm(S->R, x, Rx, 3, 3, 1);
+  for (int k = 0; k < 3; ++k) y[k] = S->s * Rx[k] + S->t[k];
+}
+
+/* Before the pose graph optimisation the keyframes connected to the current
+ * keyframe c take the loop's Sim(3) correction: with S_c' the corrected pose
+ * of c (estimated by the loop detection), every listed keyframe k keeps its
+ * pose relative to c,
+ *     S_k' = (S_k S_c^-1) S_c',
+ * and every keyframe not listed keeps its pose (copied).  out: n x 8. */
+EXPORT void og_propagate_correction(int n, const double *poses, int current, const double *corrected8,
+                                    int n_conn, const int32_t *conn, double *out) {
+  memcpy(out, poses, sizeof(double) * 8 * (size_t)n);
+  const sim3 Sc = sim3_from8(poses + 8 * (size_t)current);
+  const sim3 Scinv = sim3_inv(&Sc);
+  const sim3 Sc_new = sim3_from8(corrected8);
+  for (int a = 0; a < n_conn; ++a) {
+    const int k = conn[a];
+    const sim3 Sk = sim3_from8(poses + 8 * (size_t)k);
+    const sim3 rel = sim3_mul(&Sk, &Scinv);          /* S_k S_c^-1: camera c -> camera k */
+    const sim3 Sk_new = sim3_mul(&rel, &Sc_new);
+    sim3_to8(&Sk_new, out + 8 * (size_t)k);
+  }
+}
+
+/* Map-point correction: a point keeps its position in the camera frame of
+ * its reference keyframe r while that keyframe's pose changes from
+ * S_before[r] to S_after[r]:
+ *     x' = S_after[r]^-1 (S_before[r] x).
+ * Points with r < 0 are copied.  X, out: P x 3 (world coordinates). */
+EXPORT void og_correct_points(int n, const double *before, const double *after, int P, const double *X,
+                              const int32_t *ref, double *out) {
+  (void)n;
+  for (int p = 0; p < P; ++p) {
+    const int r = ref[p];
+    if (r < 0) {
+      memcpy(out + 3 * (size_t)p, X + 3 * (size_t)p, sizeof(double) * 3);
+      continue;
+    }
+    const sim3 Sb = sim3_from8(before + 8 * (size_t)r);
+    const sim3 Sa = sim3_from8(after + 8 * (size_t)r);
+    const sim3 Sa_inv = sim3_inv(&Sa);
+    double y[3];
+    sim3_apply(&Sb, X + 3 * (size_t)p, y);       /* into the reference camera */
+    sim3_apply(&Sa_inv, y, out + 3 * (size_t)p); /* back to the corrected world */
+  }
 }

@@ -37,7 +37,7 @@ import numpy as np
 
 __all__ = [
     "PoseGraph", "make_graph", "make_config", "make_batch", "batch_sizes", "CONFIGS",
-    "compose", "inverse", "quat_mul", "quat_rotate",
+    "compose", "inverse", "quat_mul", "quat_rotate", "LoopCorrection", "make_loop_correction",
 ]
 
 
@@ -390,3 +390,52 @@ def make_batch(n_graphs=256, seed0=1000, n_min=100, n_max=5000, window=15,
         out.append(make_graph("figure8", n, seed=seed0 + k, window=window,
                               n_loops=loops, noise=noise, name=f"batch{k}"))
     return out
+
+
+class LoopCorrection:
+    """Inputs of the loop-correction steps around the pose graph optimisation
+    of one graph (see make_loop_correction)."""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+def make_loop_correction(g, points_per_kf=150, seed=0, depth=(1.0, 8.0), half_angle=0.6):
+    """Synthetic inputs of the loop-correction steps for graph ``g``:
+
+    current    the keyframe that closed the loop: the later end of the graph's
+               last loop edge (the last keyframe if it has none);
+    matched    the loop edge's other end (keyframe 0 if none);
+    corrected  the Sim(3) pose of ``current`` that the loop detection would
+               estimate, consistent with the matched keyframe:
+               S_c' = (S_c^gt (S_m^gt)^-1) S_m (exact relative pose);
+    connected  ``current`` and every keyframe sharing an edge with it;
+    points     ``points_per_kf`` map points per keyframe, (P, 3) world
+               coordinates, created in the keyframe's camera frame at its
+               drifted estimate (depth uniform in ``depth``, direction within
+               ``half_angle`` rad of the optical axis z);
+    ref        (P,) int32 reference keyframe of each point.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    n = g.n_vertices
+    if g.n_loop_edges > 0:
+        a, b = int(g.edge_i[-1]), int(g.edge_j[-1])
+        current, matched = max(a, b), min(a, b)
+    else:
+        current, matched = n - 1, 0
+    rel = compose(g.poses_gt[current], inverse(g.poses_gt[matched]))
+    corrected = compose(rel, g.poses_init[matched])
+    corrected[0:4] /= np.linalg.norm(corrected[0:4])
+    nb = np.concatenate([g.edge_j[g.edge_i == current], g.edge_i[g.edge_j == current]])
+    connected = np.unique(np.concatenate([[current], nb])).astype(np.int32)
+    P = n * points_per_kf
+    ref = np.repeat(np.arange(n, dtype=np.int32), points_per_kf)
+    d = rng.uniform(depth[0], depth[1], P)
+    ang = rng.uniform(0.0, half_angle, P)
+    az = rng.uniform(0.0, 2.0 * np.pi, P)
+    pc = np.stack([d * np.sin(ang) * np.cos(az), d * np.sin(ang) * np.sin(az), d * np.cos(ang)], axis=1)
+    S = g.poses_init[ref]
+    Sinv = inverse(S)
+    X = Sinv[:, 7:8] * quat_rotate(Sinv[:, 0:4], pc) + Sinv[:, 4:7]
+    return LoopCorrection(current=current, matched=matched, corrected=np.ascontiguousarray(corrected),
+                          connected=connected, points=np.ascontiguousarray(X), ref=ref)
