@@ -475,6 +475,62 @@ def single_leg(name, steps, flush, torch, max_iters=MAX_ITERS):
     return out
 
 
+def correction_leg(torch, flush, name="c3_corridor_8k", points_per_kf=150, reps=10):
+    """Loop-correction steps on a graph's keyframes and map points
+    (`points_per_kf` per keyframe): pgo_propagate_correction of the connected
+    keyframes and pgo_correct_points of every map point (the post-optimisation
+    pass), device-resident arrays, L2 flushed before each timed call, CUDA
+    events on the current stream, median of `reps`.  Roofline of the point
+    pass: 52 bytes (point read and write, reference index) and 9 FP64 fused
+    multiply-adds (18 flops) per point; the FP64 rate bounds it."""
+    import numpy as np
+    from paper_2603_17201_gb300 import correct_points, propagate_correction
+    from paper_2603_17201_gb300 import synthetic as syn
+    g = syn.make_config(name)
+    lc = syn.make_loop_correction(g, points_per_kf=points_per_kf, seed=1)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+    poses, corr, conn = t(g.poses_init), t(lc.corrected), t(lc.connected, torch.int32)
+    X, ref = t(lc.points), t(lc.ref, torch.int32)
+    out_p = propagate_correction(poses, lc.current, corr, conn)
+    out_x = correct_points(poses, out_p, X, ref)
+
+    def timed(fn):
+        ms = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    ms_prop = timed(lambda: propagate_correction(poses, lc.current, corr, conn))
+    ms_pts = timed(lambda: correct_points(poses, out_p, X, ref, out=out_x))
+    P, N = X.shape[0], g.n_vertices
+    bytes_ = 52 * P + N * (2 * 64 + 2 * 128)
+    flops = 18 * P
+    peaks, peak_kind = measured_peaks()
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    fp64_tflops = 1.25   # nominal GB300 FP64 rate (no FP64 figure is measured)
+    f_hbm = bytes_ / (ms_pts * 1e-3) / 1e9 / hbm
+    f_alu = flops / (ms_pts * 1e-3) / 1e12 / fp64_tflops
+    return {"workload": f"{name} keyframes, {points_per_kf} map points each", "n_vertices": N, "n_points": P,
+            "n_connected": int(len(lc.connected)),
+            "propagate_us": 1e3 * ms_prop, "correct_points_us": 1e3 * ms_pts,
+            "points_per_s": P / (ms_pts * 1e-3),
+            "roofline": {"bound": "alu" if f_alu > f_hbm else "hbm",
+                         "achieved": flops / (ms_pts * 1e-3) / 1e12, "peak": fp64_tflops, "unit": "TFLOP/s (FP64)",
+                         "frac": f_alu, "peak_kind": "nominal FP64 rate",
+                         "achieved_hbm_gbs": bytes_ / (ms_pts * 1e-3) / 1e9, "frac_hbm": f_hbm,
+                         "hbm_peak_kind": peak_kind, "traffic": None,
+                         "kernel": "k_point_table + k_apply_points (pgo_correct_points, one call)"}}
+
+
 def adjoint_leg(steps, torch):
     """The differentiation workload (4,000-keyframe noisy figure-8, 67,857
     edges, weights 1): FP64 forward solve to a stationary point (LM plus
@@ -585,6 +641,8 @@ def run_ours(args):
         extra["c3"] = single_leg("c3_corridor_8k", 3, flush, torch)
         extra["c5_adjoint"] = adjoint_leg(2, torch)
         extra["c4_batch"] = batch_leg(1, sample=16)
+    if not args.no_extra:
+        extra["loop_correction"] = correction_leg(torch, flush)
 
     # ---- correctness gate: final cost vs the FP64 oracle ----
     cpu = None

@@ -314,6 +314,52 @@ pgo_status pgo_evaluate_cost(int32_t n_vertices, int32_t n_edges, const int32_t*
                              const double* poses, double* cost_out, int32_t* bad_edges_out,
                              void* stream);
 
+/* Loop correction before the pose graph optimisation (Sec. III-B, "Loop
+ * Correction": the keyframes connected to the keyframe that closed the loop
+ * have their poses corrected with the Sim(3) the loop detection estimated,
+ * before the optimisation propagates the correction to the whole map).
+ * With S_c the pose of keyframe `current` in `poses` and S_c' = *corrected,
+ * every keyframe k listed in `connected` keeps its pose relative to c:
+ *     S_k' = (S_k S_c^-1) S_c'
+ * (list `current` itself to move it to S_c'); every other keyframe is copied.
+ * Arguments (device memory of the current device, caller-owned, ordered on
+ * `stream`, no synchronisation):
+ *   poses      double[n_vertices * 8] pose8, 16-byte aligned;
+ *   corrected  double[8] pose8 of S_c', 16-byte aligned;
+ *   connected  int32[n_connected] keyframe indices (an index outside
+ *              [0, n_vertices) is skipped and counted);
+ *   poses_out  double[n_vertices * 8], 16-byte aligned, must not overlap
+ *              poses; quaternions written normalised with w >= 0;
+ *   bad_out    int32 (nullable): number of skipped indices.
+ * PGO_ERR_INVALID_ARG for bad sizes, a current index out of range, NULL or
+ * misaligned arrays, or overlapping poses_out. */
+pgo_status pgo_propagate_correction(int32_t n_vertices, const double* poses, int32_t current,
+                                    const double* corrected, int32_t n_connected, const int32_t* connected,
+                                    double* poses_out, int32_t* bad_out, void* stream);
+
+/* Map-point correction (Sec. III-B: the loop correction carried from the
+ * keyframes to the map).  A point keeps its position in the camera frame of
+ * its reference keyframe r while that keyframe's pose changes from
+ * S_before[r] to S_after[r]:
+ *     x' = S_after[r]^-1 (S_before[r] x),   S x = s R x + t.
+ * Used after pgo_propagate_correction (before = the poses it read, after =
+ * its output, the connected keyframes' points listed) and after pgo_solve
+ * (before = the initial estimate, after = the optimised poses, every point).
+ * Arguments (device memory, caller-owned, ordered on `stream`):
+ *   poses_before, poses_after  double[n_vertices * 8] pose8, 16-byte aligned;
+ *   points      double[n_points * 3] world coordinates (x, y, z);
+ *   ref_kf      int32[n_points]: reference keyframe of each point; r < 0
+ *               leaves the point unchanged, r >= n_vertices also leaves it
+ *               unchanged and is counted;
+ *   points_out  double[n_points * 3]; may be `points` itself (in place);
+ *   bad_out     int32 (nullable): number of points with r >= n_vertices.
+ * Uses a temporary device table of 128 bytes per keyframe from the
+ * stream-ordered allocator.  PGO_ERR_INVALID_ARG for bad sizes or NULL or
+ * misaligned pose arrays. */
+pgo_status pgo_correct_points(int32_t n_vertices, const double* poses_before, const double* poses_after,
+                              int32_t n_points, const double* points, const int32_t* ref_kf,
+                              double* points_out, int32_t* bad_out, void* stream);
+
 /* pgo_evaluate_cost without any device allocation (no counterpart in the
  * paper: an addition for callers that cannot allocate device memory at call
  * time, such as a real-time loop-closing thread that must not stall on the

@@ -39,7 +39,7 @@ EXPORTED = [
     "pgo_graph_set_poses", "pgo_graph_set_measurements", "pgo_graph_get_poses", "pgo_graph_cost", "pgo_graph_linearize",
     "pgo_graph_damped_step", "pgo_graph_resolve", "pgo_graph_report", "pgo_solve", "pgo_backward", "pgo_batch_create", "pgo_batch_destroy",
     "pgo_batch_solve", "pgo_batch_schedule", "pgo_evaluate_cost", "pgo_evaluate_cost_noalloc",
-    "pgo_graph_multigrid_info", "pgo_graph_precondition",
+    "pgo_graph_multigrid_info", "pgo_graph_precondition", "pgo_propagate_correction", "pgo_correct_points",
 ]
 
 
@@ -107,6 +107,8 @@ def load(build_if_missing: bool = True):
         lib.pgo_graph_resolve.argtypes = [vp, ctypes.POINTER(SolveOptions), c_double, vp,
                                           ctypes.POINTER(c_int32), c_int32]
         lib.pgo_graph_report.argtypes = [vp, ctypes.POINTER(Report)]
+        lib.pgo_propagate_correction.argtypes = [c_int32, vp, c_int32, vp, c_int32, vp, vp, vp, vp]
+        lib.pgo_correct_points.argtypes = [c_int32, vp, vp, c_int32, vp, vp, vp, vp, vp]
         lib.pgo_graph_precondition.argtypes = [vp, ctypes.POINTER(SolveOptions), c_double]
         lib.pgo_graph_multigrid_info.argtypes = [vp, ctypes.POINTER(c_int32), vp, vp, vp, vp]
         lib.pgo_solve.argtypes = [vp, ctypes.POINTER(SolveOptions), ctypes.POINTER(Report), vp, c_int32]

@@ -15,7 +15,8 @@ import numpy as np
 
 from . import _lib as L
 
-__all__ = ["PoseGraph", "PoseGraphBatch", "evaluate_cost", "default_options", "PGOError", "solve_pose_graph"]
+__all__ = ["PoseGraph", "PoseGraphBatch", "evaluate_cost", "default_options", "PGOError", "solve_pose_graph",
+           "propagate_correction", "correct_points"]
 
 PGOError = L.PGOError
 default_options = L.default_options
@@ -415,4 +416,56 @@ def evaluate_cost(n_vertices, edge_i, edge_j, meas, weight, poses, return_bad=Fa
     ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
     L.check(lib.pgo_evaluate_cost(int(n_vertices), int(edge_i.numel()), ptr(edge_i), ptr(edge_j), ptr(meas),
                                   ptr(weight), ptr(poses), ptr(out), ptr(bad), _current_stream_handle()))
+    return (out, bad) if return_bad else out
+
+
+def _dev_f64(x, shape):
+    torch = _torch()
+    t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64))
+    return t.to(device="cuda", dtype=torch.float64).reshape(shape).contiguous()
+
+
+def _dev_i32(x):
+    torch = _torch()
+    t = x if isinstance(x, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(x, dtype=np.int32))
+    return t.to(device="cuda", dtype=torch.int32).reshape(-1).contiguous()
+
+
+def propagate_correction(poses, current, corrected, connected, return_bad=False):
+    """Loop correction before the optimisation (pgo_propagate_correction):
+    S_k' = (S_k S_c^-1) S_c' for the keyframes in ``connected``, the others
+    copied.  Inputs are host arrays or CUDA tensors; returns an (N, 8) CUDA
+    tensor written on the current stream (and the count of skipped indices
+    as a 0-d int32 CUDA tensor with ``return_bad``)."""
+    torch = _torch()
+    lib = L.load()
+    p = _dev_f64(poses, (-1, 8))
+    n = p.shape[0]
+    c = _dev_f64(corrected, (8,))
+    k = _dev_i32(connected)
+    out = torch.empty((n, 8), dtype=torch.float64, device="cuda")
+    bad = torch.zeros((), dtype=torch.int32, device="cuda")
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    L.check(lib.pgo_propagate_correction(n, ptr(p), int(current), ptr(c), int(k.numel()), ptr(k), ptr(out), ptr(bad),
+                                         _current_stream_handle()))
+    return (out, bad) if return_bad else out
+
+
+def correct_points(poses_before, poses_after, points, ref, out=None, return_bad=False):
+    """Map-point correction (pgo_correct_points): x' = S_after[r]^-1
+    (S_before[r] x) through each point's reference keyframe r (r < 0:
+    unchanged).  Returns a (P, 3) CUDA tensor (``out`` if given, which may be
+    ``points`` itself) written on the current stream."""
+    torch = _torch()
+    lib = L.load()
+    b = _dev_f64(poses_before, (-1, 8))
+    a = _dev_f64(poses_after, (-1, 8))
+    X = _dev_f64(points, (-1, 3))
+    r = _dev_i32(ref)
+    if out is None:
+        out = torch.empty_like(X)
+    bad = torch.zeros((), dtype=torch.int32, device="cuda")
+    ptr = lambda t: ctypes.c_void_p(t.data_ptr())  # noqa: E731
+    L.check(lib.pgo_correct_points(b.shape[0], ptr(b), ptr(a), X.shape[0], ptr(X), ptr(r), ptr(out), ptr(bad),
+                                   _current_stream_handle()))
     return (out, bad) if return_bad else out

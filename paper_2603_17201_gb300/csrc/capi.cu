@@ -1480,6 +1480,47 @@ pgo_status pgo_batch_schedule(const pgo_batch* B, int32_t* lanes, int32_t* threa
   return PGO_OK;
 }
 
+static bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+pgo_status pgo_propagate_correction(int32_t n_vertices, const double* poses, int32_t current, const double* corrected,
+                                    int32_t n_connected, const int32_t* connected, double* poses_out,
+                                    int32_t* bad_out, void* stream) {
+  if (n_vertices < 1 || n_connected < 0) return fail(PGO_ERR_INVALID_ARG, "need n_vertices >= 1 and n_connected >= 0");
+  if (current < 0 || current >= n_vertices)
+    return fail(PGO_ERR_INVALID_ARG, "current keyframe %d out of range [0, %d)", current, n_vertices);
+  if (!poses || !corrected || !poses_out || (n_connected > 0 && !connected))
+    return fail(PGO_ERR_INVALID_ARG, "NULL array");
+  if (!aligned16(poses) || !aligned16(corrected) || !aligned16(poses_out))
+    return fail(PGO_ERR_INVALID_ARG, "poses, corrected and poses_out must be 16-byte aligned");
+  const char* lo = reinterpret_cast<const char*>(poses);
+  const char* hi = lo + sizeof(double) * 8 * (size_t)n_vertices;
+  const char* o = reinterpret_cast<const char*>(poses_out);
+  if (o < hi && o + sizeof(double) * 8 * (size_t)n_vertices > lo)
+    return fail(PGO_ERR_INVALID_ARG, "poses_out must not overlap poses");
+  CUDA_TRY(launch_propagate_correction(n_vertices, poses, current, corrected, n_connected, connected, poses_out, bad_out,
+                                       (cudaStream_t)stream));
+  return PGO_OK;
+}
+
+pgo_status pgo_correct_points(int32_t n_vertices, const double* poses_before, const double* poses_after,
+                              int32_t n_points, const double* points, const int32_t* ref_kf, double* points_out,
+                              int32_t* bad_out, void* stream) {
+  if (n_vertices < 1 || n_points < 0) return fail(PGO_ERR_INVALID_ARG, "need n_vertices >= 1 and n_points >= 0");
+  if (!poses_before || !poses_after || (n_points > 0 && (!points || !ref_kf || !points_out)))
+    return fail(PGO_ERR_INVALID_ARG, "NULL array");
+  if (!aligned16(poses_before) || !aligned16(poses_after))
+    return fail(PGO_ERR_INVALID_ARG, "poses_before and poses_after must be 16-byte aligned");
+  cudaStream_t s = (cudaStream_t)stream;
+  void* table = nullptr;
+  CUDA_TRY(cudaMallocAsync(&table, point_table_bytes(n_vertices), s));
+  cudaError_t e = launch_correct_points(n_vertices, poses_before, poses_after, n_points, points, ref_kf,
+                                        reinterpret_cast<double*>(table), points_out, bad_out, s);
+  cudaError_t e2 = cudaFreeAsync(table, s);
+  if (e != cudaSuccess) return fail(PGO_ERR_CUDA, "pgo_correct_points: %s", cudaGetErrorString(e));
+  if (e2 != cudaSuccess) return fail(PGO_ERR_CUDA, "pgo_correct_points free: %s", cudaGetErrorString(e2));
+  return PGO_OK;
+}
+
 pgo_status pgo_evaluate_cost(int32_t n_vertices, int32_t n_edges, const int32_t* edge_i, const int32_t* edge_j,
                              const double* meas, const double* weight, const double* poses, double* cost_out,
                              int32_t* bad_edges_out, void* stream) {

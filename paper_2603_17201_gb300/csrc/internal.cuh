@@ -274,6 +274,12 @@ void launch_eval_cost_raw(int N, int E, const int* ei, const int* ej, const doub
 void launch_eval_cost_raw_blocks(int N, int E, const int* ei, const int* ej, const double* meas, const double* w,
                                  const double* poses, double* partial, unsigned* ticket, int* bad,
                                  double* cost_out, int* bad_out, int blocks, cudaStream_t s);
+// Loop-correction steps around the optimisation (correction.cu).
+cudaError_t launch_propagate_correction(int n, const double* poses, int current, const double* corrected, int n_conn,
+                                        const int* conn, double* out, int* bad, cudaStream_t s);
+size_t point_table_bytes(int n);
+cudaError_t launch_correct_points(int n, const double* before, const double* after, int P, const double* X,
+                                  const int* ref, double* table, double* out, int* bad, cudaStream_t s);
 void set_last_error(const char* msg);   // message returned by pgo_last_error()
 
 }  // namespace pgo
