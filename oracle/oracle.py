@@ -48,6 +48,13 @@ class LMReport(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class ProjParams(ctypes.Structure):
+    _fields_ = [("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
+                ("min_x", ctypes.c_double), ("max_x", ctypes.c_double), ("min_y", ctypes.c_double),
+                ("max_y", ctypes.c_double), ("scale_factor", ctypes.c_double), ("th", ctypes.c_double),
+                ("cos_min", ctypes.c_double), ("n_levels", ctypes.c_int), ("th_low", ctypes.c_int)]
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (strict IEEE: -O2, no fast-math)."""
     with _lock:
@@ -91,6 +98,9 @@ def load():
     lib.og_pose_loss.argtypes = [ctypes.c_void_p, _dp, _dp, _dp]
     lib.og_propagate_correction.argtypes = [ctypes.c_int, _dp, ctypes.c_int, _dp, ctypes.c_int, _ip, _dp]
     lib.og_correct_points.argtypes = [ctypes.c_int, _dp, _dp, ctypes.c_int, _dp, _ip, _dp]
+    vp = ctypes.c_void_p
+    lib.og_project_match.argtypes = [ctypes.POINTER(ProjParams), ctypes.c_int, ctypes.c_int, vp, vp, vp, vp, vp,
+                                     vp, vp, vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp, vp, vp]
     _lib = lib
     return lib
 
@@ -314,3 +324,44 @@ def correct_points(before, after, points, ref):
 
 
 __all__ += ["propagate_correction", "correct_points"]
+
+
+# ---------------------------------------------------------------- projection search / loop fusion
+def proj_params(camera, n_levels=8, scale_factor=1.2, th=10.0, cos_min=0.5, th_low=50):
+    p = ProjParams()
+    for k in ("fx", "fy", "cx", "cy", "min_x", "max_x", "min_y", "max_y"):
+        setattr(p, k, float(camera[k]))
+    p.scale_factor = float(scale_factor)
+    p.th = float(th)
+    p.cos_min = float(cos_min)
+    p.n_levels = int(n_levels)
+    p.th_low = int(th_low)
+    return p
+
+
+def project_match(w, mode, th=10.0, th_low=50, cos_min=0.5, poses=None):
+    """Projection search (mode 'search') or loop fusion ('fusion') of the map
+    points of workload ``w`` against its keyframes (Sec. IV-D): returns
+    (match, dist, fuse) as (K, P) int32 arrays (fuse None for the search)."""
+    pp = proj_params(w.camera, w.n_levels, w.scale_factor, th, cos_min, th_low)
+    K = len(w.feat_ptr) - 1
+    P = w.points.shape[0]
+    m = 0 if mode == "search" else 1
+    poses = _f64(w.poses if poses is None else poses, (K, 8))
+    arrs = dict(ptr=np.ascontiguousarray(w.feat_ptr, np.int32), fu=np.ascontiguousarray(w.fu, np.float32),
+                fv=np.ascontiguousarray(w.fv, np.float32), fo=np.ascontiguousarray(w.foct, np.int32),
+                fd=np.ascontiguousarray(w.fdesc, np.uint32), fs=np.ascontiguousarray(w.fskip, np.uint8),
+                fm=np.ascontiguousarray(w.fmp, np.int32), X=_f64(w.points, (P, 3)),
+                pd=np.ascontiguousarray(w.pdesc, np.uint32), mn=_f64(w.min_dist), mx=_f64(w.max_dist),
+                nr=_f64(w.normal, (P, 3)), pid=np.ascontiguousarray(w.pid, np.int32))
+    match = np.empty((K, P), np.int32)
+    dist = np.empty((K, P), np.int32)
+    fuse = np.empty((K, P), np.int32) if m == 1 else None
+    a = {k: v.ctypes.data for k, v in arrs.items()}
+    load().og_project_match(ctypes.byref(pp), m, K, poses.ctypes.data, a["ptr"], a["fu"], a["fv"], a["fo"], a["fd"],
+                            a["fs"] if m == 0 else None, a["fm"], P, a["X"], a["pd"], a["mn"], a["mx"], a["nr"],
+                            a["pid"], match.ctypes.data, dist.ctypes.data, fuse.ctypes.data if m == 1 else None)
+    return match, dist, fuse
+
+
+__all__ += ["ProjParams", "proj_params", "project_match"]

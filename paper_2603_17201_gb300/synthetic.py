@@ -439,3 +439,148 @@ def make_loop_correction(g, points_per_kf=150, seed=0, depth=(1.0, 8.0), half_an
     X = Sinv[:, 7:8] * quat_rotate(Sinv[:, 0:4], pc) + Sinv[:, 4:7]
     return LoopCorrection(current=current, matched=matched, corrected=np.ascontiguousarray(corrected),
                           connected=connected, points=np.ascontiguousarray(X), ref=ref)
+
+
+# --------------------------------------------------------------------------
+# Projection search and loop fusion workloads (keyframe features, map points)
+# --------------------------------------------------------------------------
+class MatchWorkload:
+    """Keyframes with ORB-like features and map points to match against them
+    (see make_match_workload); arrays in the layout of pgo_frames_create and
+    pgo_project_match."""
+
+    def __init__(self, **kw):
+        self.__dict__.update(kw)
+
+
+CAMERA = dict(fx=460.0, fy=460.0, cx=376.0, cy=240.0, min_x=0.0, max_x=752.0, min_y=0.0, max_y=480.0)
+
+
+def _rand_desc(rng, n):
+    return rng.integers(0, 2 ** 32, size=(n, 8), dtype=np.uint64).astype(np.uint32)
+
+
+def _flip_bits(rng, desc, nflip):
+    out = desc.copy()
+    for i in range(desc.shape[0]):
+        bits = rng.choice(256, int(nflip[i]), replace=False)
+        for b in bits:
+            out[i, b // 32] ^= np.uint32(1) << np.uint32(b % 32)
+    return out
+
+
+def _camera_centre(S):
+    Si = inverse(S)
+    return Si[..., 4:7]
+
+
+def _project(S, X, cam):
+    pc = S[..., 7:8] * quat_rotate(S[..., 0:4], X) + S[..., 4:7]
+    u = cam["fx"] * pc[..., 0] / pc[..., 2] + cam["cx"]
+    v = cam["fy"] * pc[..., 1] / pc[..., 2] + cam["cy"]
+    return u, v, pc[..., 2]
+
+
+def make_match_workload(mode="search", n_kf=3, n_points=4000, features_per_kf=1200, seed=0,
+                        n_levels=8, scale_factor=1.2, detect=0.7, pixel_noise=1.0, max_flips=30,
+                        matched_frac=0.1, duplicate_frac=0.5, observed_frac=0.02):
+    """Synthetic keyframes on the figure-8 trajectory (752 x 480 camera,
+    ~``features_per_kf`` features each over ``n_levels`` octaves) and
+    ``n_points`` map points around them.
+
+    Every map point has a random 256-bit descriptor, a creation distance d0
+    and level l0 (max_dist = d0 scale^l0 times a factor in [1.02, 1.15], off
+    the level boundaries; min_dist = max_dist / scale^(n_levels-1)) and a
+    viewing direction.  A keyframe detects a fraction ``detect`` of the
+    points in its view as features at the projection plus Gaussian pixel
+    noise, with the point's descriptor after up to ``max_flips`` random bit
+    flips and the octave its distance predicts; random clutter features fill
+    the rest.  mode 'search' (projection search, PS1 with n_kf = 1, PS3a-c
+    with n_kf = 3): keyframe poses are Sim(3) with a random scale, and a
+    fraction ``matched_frac`` of each keyframe's features is marked as matched
+    before the search.  mode 'fusion': the points are the loop side's map
+    points; a fraction ``duplicate_frac`` of the detected ones are already in
+    the keyframe's map under another id (the duplicates loop fusion finds),
+    and a fraction ``observed_frac`` is observed by the keyframe itself.
+    """
+    rng = np.random.Generator(np.random.PCG64(seed))
+    cam = CAMERA
+    c, f = _figure8(400)
+    gt = _poses_from_path(c, f)
+    k0 = int(rng.integers(0, 400 - n_kf * 3))
+    kf_idx = k0 + 2 * np.arange(n_kf)
+    S = gt[kf_idx].copy()
+    # points in front of the keyframes: created from the first keyframe's view and its neighbours
+    creators = kf_idx[rng.integers(0, n_kf, n_points)]
+    Sc = gt[creators]
+    d0 = rng.uniform(2.0, 12.0, n_points)
+    ang = rng.uniform(0.0, 0.55, n_points)
+    az = rng.uniform(0.0, 2.0 * np.pi, n_points)
+    pc = np.stack([d0 * np.sin(ang) * np.cos(az), d0 * np.sin(ang) * np.sin(az), d0 * np.cos(ang)], axis=1)
+    Sci = inverse(Sc)
+    X = Sci[:, 7:8] * quat_rotate(Sci[:, 0:4], pc) + Sci[:, 4:7]
+    Oc = _camera_centre(Sc)
+    nrm = X - Oc
+    dist0 = np.linalg.norm(nrm, axis=1)
+    nrm /= dist0[:, None]
+    l0 = rng.integers(0, 3, n_points)
+    # a margin keeps the creating keyframe's own distance off a level boundary
+    max_dist = dist0 * scale_factor ** l0 * rng.uniform(1.02, 1.15, n_points)
+    min_dist = max_dist / scale_factor ** (n_levels - 1)
+    pdesc = _rand_desc(rng, n_points)
+    pid = np.arange(n_points, dtype=np.int32) + 100000
+    feat_ptr = [0]
+    fu, fv, foct, fdesc, fskip, fmp = [], [], [], [], [], []
+    truth = []
+    for k in range(n_kf):
+        u, v, z = _project(S[k][None], X, cam)
+        O = _camera_centre(S[k])
+        d = np.linalg.norm(X - O, axis=1)
+        inview = (z > 0) & (u >= 0) & (u < cam["max_x"]) & (v >= 0) & (v < cam["max_y"])
+        inview &= (d >= min_dist) & (d <= max_dist)
+        inview &= np.einsum("ij,ij->i", X - O, nrm) >= 0.5 * d     # viewing angle within 60 degrees
+        det = np.nonzero(inview & (rng.random(n_points) < detect))[0][: int(features_per_kf * 0.8)]
+        lev = np.zeros(len(det), dtype=np.int32)
+        for i, p in enumerate(det):
+            L = 0
+            while L < n_levels - 1 and max_dist[p] > d[p] * scale_factor ** L:
+                L += 1
+            lev[i] = L
+        lev = np.maximum(lev - rng.integers(0, 2, len(det)), 0).astype(np.int32)
+        nu = (u[det] + rng.normal(0.0, pixel_noise, len(det))).clip(0.0, cam["max_x"] - 1e-3)
+        nv = (v[det] + rng.normal(0.0, pixel_noise, len(det))).clip(0.0, cam["max_y"] - 1e-3)
+        dd = _flip_bits(rng, pdesc[det], rng.integers(0, max_flips + 1, len(det)))
+        ncl = max(0, features_per_kf - len(det))
+        cu = rng.uniform(0.0, cam["max_x"], ncl)
+        cv = rng.uniform(0.0, cam["max_y"], ncl)
+        co = rng.integers(0, n_levels, ncl).astype(np.int32)
+        cd = _rand_desc(rng, ncl)
+        mp = np.full(len(det) + ncl, -1, dtype=np.int32)
+        if mode == "fusion":
+            dup = rng.random(len(det)) < duplicate_frac
+            mp[: len(det)][dup] = det[dup].astype(np.int32) + 500000      # the other side's id of the same point
+            own = rng.random(len(det)) < observed_frac
+            mp[: len(det)][own] = pid[det[own]]
+        uu = np.concatenate([nu, cu]).astype(np.float32)
+        vv = np.concatenate([nv, cv]).astype(np.float32)
+        oo = np.concatenate([lev, co]).astype(np.int32)
+        de = np.concatenate([dd, cd]).astype(np.uint32)
+        perm = rng.permutation(len(uu))
+        fu.append(uu[perm]); fv.append(vv[perm]); foct.append(oo[perm]); fdesc.append(de[perm]); fmp.append(mp[perm])
+        sk = (rng.random(len(uu)) < matched_frac).astype(np.uint8) if mode == "search" else np.zeros(len(uu), np.uint8)
+        fskip.append(sk)
+        inv = np.empty(len(uu), dtype=np.int64)
+        inv[perm] = np.arange(len(uu))
+        truth.append(dict(points=det, features=inv[: len(det)]))
+        feat_ptr.append(feat_ptr[-1] + len(uu))
+    if mode == "search":   # Sim(3) poses: same projections, scaled camera frame
+        s = rng.uniform(0.8, 1.25, n_kf)
+        S[:, 4:7] *= s[:, None]
+        S[:, 7] = s
+    return MatchWorkload(
+        mode=mode, camera=dict(cam), n_levels=n_levels, scale_factor=scale_factor,
+        poses=np.ascontiguousarray(S), feat_ptr=np.array(feat_ptr, dtype=np.int32),
+        fu=np.concatenate(fu), fv=np.concatenate(fv), foct=np.concatenate(foct),
+        fdesc=np.ascontiguousarray(np.concatenate(fdesc)), fskip=np.concatenate(fskip), fmp=np.concatenate(fmp),
+        points=np.ascontiguousarray(X), pdesc=pdesc, min_dist=min_dist, max_dist=max_dist,
+        normal=np.ascontiguousarray(nrm), pid=pid, truth=truth)
