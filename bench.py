@@ -531,6 +531,49 @@ def correction_leg(torch, flush, name="c3_corridor_8k", points_per_kf=150, reps=
                          "kernel": "k_point_table + k_apply_points (pgo_correct_points, one call)"}}
 
 
+def matching_leg(torch, flush, reps=20):
+    """Projection search PS3a-c (3 keyframes, 4,000 map points) and loop
+    fusion (30 connected keyframes, 4,000 loop map points): one
+    pgo_project_match call each on device-resident features (a frames
+    object) and points, L2 flushed before each timed call, CUDA events on
+    the current stream, median of `reps`.  Throughput in (keyframe, point)
+    pairs per second; the compulsory traffic (points, features and outputs
+    once) is a few MB, so the call is bound by latency and the integer
+    popcount work of the candidate comparisons, not by HBM."""
+    import numpy as np
+    from paper_2603_17201_gb300 import Frames, match_params
+    from paper_2603_17201_gb300 import synthetic as syn
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    out = {}
+    for name, mode, K, th in (("ps3_search", "search", 3, 10.0), ("loop_fusion", "fusion", 30, 4.0)):
+        w = syn.make_match_workload(mode, n_kf=K, n_points=4000, seed=7)
+        fr = Frames.from_workload(w)
+        prm = match_params(w.camera, w.n_levels, w.scale_factor, th)
+        t = lambda a, dt: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device=dev)  # noqa: E731
+        args = (t(w.poses, torch.float64), t(w.points, torch.float32), t(w.pdesc.view(np.int32), torch.int32),
+                t(w.min_dist, torch.float32), t(w.max_dist, torch.float32), t(w.normal, torch.float32),
+                t(w.pid, torch.int32), t(w.fskip, torch.uint8) if mode == "search" else None)
+        call = lambda: fr.project_match(prm, mode, *args[:7], matched=args[7])  # noqa: E731
+        m, _, _ = call()
+        ms = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            call()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        tm = statistics.median(ms)
+        P = w.points.shape[0]
+        out[name] = {"keyframes": K, "points": P, "features": int(w.feat_ptr[-1]), "us_per_call": 1e3 * tm,
+                     "pairs_per_s": K * P / (tm * 1e-3), "matches": int((m >= 0).sum().item())}
+        fr.close()
+    return out
+
+
 def adjoint_leg(steps, torch):
     """The differentiation workload (4,000-keyframe noisy figure-8, 67,857
     edges, weights 1): FP64 forward solve to a stationary point (LM plus
@@ -643,6 +686,7 @@ def run_ours(args):
         extra["c4_batch"] = batch_leg(1, sample=16)
     if not args.no_extra:
         extra["loop_correction"] = correction_leg(torch, flush)
+        extra["matching"] = matching_leg(torch, flush)
 
     # ---- correctness gate: final cost vs the FP64 oracle ----
     cpu = None

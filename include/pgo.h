@@ -360,6 +360,99 @@ pgo_status pgo_correct_points(int32_t n_vertices, const double* poses_before, co
                               int32_t n_points, const double* points, const int32_t* ref_kf,
                               double* points_out, int32_t* bad_out, void* stream);
 
+/* ---- projection search and loop fusion (Sec. IV-D) ----
+ * Map points are projected into keyframes with a Sim(3) pose and matched to
+ * the keyframes' features by 256-bit (ORB) descriptor distance within a
+ * window around the projection: the projection searches PS1 and PS3a-c
+ * (correspondences between map points and one or three keyframes) and the
+ * loop fusion (duplicate map points between the loop's map points and each
+ * connected keyframe's).  Per (keyframe, point) pair, in single precision:
+ *   p = s R x + t (pose (q, t, s) taken to float, R = R(q / |q|)), rejected
+ *   if p_z <= 0; u = fx p_x / p_z + cx, v = fy p_y / p_z + cy, rejected
+ *   outside [min_x, max_x) x [min_y, max_y); d = |x - O| with O = -(R^T t)/s
+ *   the camera centre, rejected unless min_dist <= d <= max_dist, and if
+ *   (x - O) . n < cos_min d; level = smallest L >= 0 with
+ *   max_dist <= d scale^L (at most n_levels - 1); candidates: features with
+ *   |u_f - u| < r, |v_f - v| < r (r = th scale^level) and octave in
+ *   [level - 1, level] (search: not matched before); the best candidate has
+ *   the smallest Hamming distance (ties: lower feature index) and is a match
+ *   if its distance is <= th_low.
+ * Conflicts: search -- a feature chosen by several points goes to the one
+ * with the smallest (distance, point index), the others get no match;
+ * fusion -- a feature that holds a map point makes every loop point choosing
+ * it fuse with that point; otherwise the smallest (distance, point index)
+ * adds its observation and the other points choosing it fuse with that one.
+ * The paper names the operations only; these rules follow the ORB-SLAM
+ * system it builds on. */
+typedef struct pgo_frames pgo_frames;
+
+typedef enum { PGO_MATCH_SEARCH = 0, PGO_MATCH_FUSE = 1 } pgo_match_mode;
+
+/* Keyframe features (Sec. IV-E: kept resident on the device).  feat_ptr:
+ * host int32[n_keyframes + 1], keyframe k owns features
+ * [feat_ptr[k], feat_ptr[k + 1]) of the arrays below (in mem_space):
+ * uv float[F * 2] keypoint (u, v); octave int32[F]; desc uint32[F * 8];
+ * map_point int32[F] map point id at each feature, -1 = none (nullable: all
+ * -1).  The image bounds define the 64 x 48 feature grid and must equal the
+ * match parameters' bounds.  stream: every call on the object is ordered on
+ * it. */
+typedef struct {
+  int32_t n_keyframes;
+  int32_t mem_space;
+  const int32_t* feat_ptr;
+  const float* uv;
+  const int32_t* octave;
+  const uint32_t* desc;
+  const int32_t* map_point;
+  float min_x, max_x, min_y, max_y;
+  void* stream;
+} pgo_frames_desc;
+
+/* Camera and search parameters (pixels; th: search radius at octave 0;
+ * th_low: largest accepted Hamming distance; cos_min: smallest cosine of the
+ * viewing angle). */
+typedef struct {
+  float fx, fy, cx, cy;
+  float min_x, max_x, min_y, max_y;
+  float scale_factor, th, cos_min;
+  int32_t n_levels, th_low;
+} pgo_match_params;
+
+/* Map points (device memory): xyz float[n * 3] world position; desc
+ * uint32[n * 8] (16-byte aligned); min_dist, max_dist float[n] scale
+ * invariance range; normal float[n * 3] mean viewing direction (unit);
+ * id int32[n] map point ids (fusion; nullable for the search). */
+typedef struct {
+  int32_t n_points;
+  const float* xyz;
+  const uint32_t* desc;
+  const float* min_dist;
+  const float* max_dist;
+  const float* normal;
+  const int32_t* id;
+} pgo_points_desc;
+
+/* Copy keyframe features to the device, bucketed by grid cell.  *out is NULL
+ * on error; free with pgo_frames_destroy. */
+pgo_status pgo_frames_create(const pgo_frames_desc* desc, pgo_frames** out);
+void pgo_frames_destroy(pgo_frames* f);
+
+/* Every (keyframe, point) pair (Sec. IV-D: one thread per map point and
+ * keyframe).  poses: device double[n_keyframes * 8] pose8 (16-byte aligned),
+ * the pose each keyframe is projected with (the Sim(3) estimate for the
+ * search, the corrected pose for fusion).  matched: device uint8[F] in the
+ * caller's feature order, nonzero = matched before this search (search only,
+ * nullable).  Outputs (device, n_keyframes * n_points, keyframe-major):
+ * match int32 feature index within the keyframe or -1; dist int32 Hamming
+ * distance of the pair's best candidate (256: none; search losers 256);
+ * fuse int32 (fusion only): the map point id the point fuses with, -1 = it
+ * adds a new observation or has no match.  A fusion pair whose keyframe
+ * already observes the point (a feature holds its id) has no match.  Ordered
+ * on the frames' stream; no synchronisation. */
+pgo_status pgo_project_match(pgo_frames* f, const pgo_match_params* params, int32_t mode, const double* poses,
+                             const uint8_t* matched, const pgo_points_desc* points, int32_t* match,
+                             int32_t* dist, int32_t* fuse);
+
 /* pgo_evaluate_cost without any device allocation (no counterpart in the
  * paper: an addition for callers that cannot allocate device memory at call
  * time, such as a real-time loop-closing thread that must not stall on the

@@ -49,10 +49,10 @@ class LMReport(ctypes.Structure):
 
 
 class ProjParams(ctypes.Structure):
-    _fields_ = [("fx", ctypes.c_double), ("fy", ctypes.c_double), ("cx", ctypes.c_double), ("cy", ctypes.c_double),
-                ("min_x", ctypes.c_double), ("max_x", ctypes.c_double), ("min_y", ctypes.c_double),
-                ("max_y", ctypes.c_double), ("scale_factor", ctypes.c_double), ("th", ctypes.c_double),
-                ("cos_min", ctypes.c_double), ("n_levels", ctypes.c_int), ("th_low", ctypes.c_int)]
+    _fields_ = [("fx", ctypes.c_float), ("fy", ctypes.c_float), ("cx", ctypes.c_float), ("cy", ctypes.c_float),
+                ("min_x", ctypes.c_float), ("max_x", ctypes.c_float), ("min_y", ctypes.c_float),
+                ("max_y", ctypes.c_float), ("scale_factor", ctypes.c_float), ("th", ctypes.c_float),
+                ("cos_min", ctypes.c_float), ("n_levels", ctypes.c_int), ("th_low", ctypes.c_int)]
 
 
 def build(force: bool = False) -> str:
@@ -341,8 +341,9 @@ def proj_params(camera, n_levels=8, scale_factor=1.2, th=10.0, cos_min=0.5, th_l
 
 def project_match(w, mode, th=10.0, th_low=50, cos_min=0.5, poses=None):
     """Projection search (mode 'search') or loop fusion ('fusion') of the map
-    points of workload ``w`` against its keyframes (Sec. IV-D): returns
-    (match, dist, fuse) as (K, P) int32 arrays (fuse None for the search)."""
+    points of workload ``w`` against its keyframes (Sec. IV-D), in single
+    precision: returns (match, dist, fuse) as (K, P) int32 arrays (fuse None
+    for the search)."""
     pp = proj_params(w.camera, w.n_levels, w.scale_factor, th, cos_min, th_low)
     K = len(w.feat_ptr) - 1
     P = w.points.shape[0]
@@ -351,9 +352,10 @@ def project_match(w, mode, th=10.0, th_low=50, cos_min=0.5, poses=None):
     arrs = dict(ptr=np.ascontiguousarray(w.feat_ptr, np.int32), fu=np.ascontiguousarray(w.fu, np.float32),
                 fv=np.ascontiguousarray(w.fv, np.float32), fo=np.ascontiguousarray(w.foct, np.int32),
                 fd=np.ascontiguousarray(w.fdesc, np.uint32), fs=np.ascontiguousarray(w.fskip, np.uint8),
-                fm=np.ascontiguousarray(w.fmp, np.int32), X=_f64(w.points, (P, 3)),
-                pd=np.ascontiguousarray(w.pdesc, np.uint32), mn=_f64(w.min_dist), mx=_f64(w.max_dist),
-                nr=_f64(w.normal, (P, 3)), pid=np.ascontiguousarray(w.pid, np.int32))
+                fm=np.ascontiguousarray(w.fmp, np.int32), X=np.ascontiguousarray(w.points, np.float32).reshape(P, 3),
+                pd=np.ascontiguousarray(w.pdesc, np.uint32), mn=np.ascontiguousarray(w.min_dist, np.float32),
+                mx=np.ascontiguousarray(w.max_dist, np.float32),
+                nr=np.ascontiguousarray(w.normal, np.float32).reshape(P, 3), pid=np.ascontiguousarray(w.pid, np.int32))
     match = np.empty((K, P), np.int32)
     dist = np.empty((K, P), np.int32)
     fuse = np.empty((K, P), np.int32) if m == 1 else None

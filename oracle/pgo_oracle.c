@@ -1112,11 +1112,12 @@ EXPORT void og_correct_points(int n, const double *before, const double *after, 
  *   the loop map points that duplicate one of its points (descriptor
  *   similarity and spatial proximity) or that it should observe.
  * The per-pair rule (ORB-SLAM lineage; the paper names the operations
- * only):
- *   p = S_k x (s R x + t); reject if p_z <= 0;
+ * only), in single precision like the system the paper builds on:
+ *   pose (q, t, s) taken to float, R = R(q / |q|);
+ *   p = s R x + t; reject if p_z <= 0;
  *   u = fx p_x / p_z + cx, v = fy p_y / p_z + cy; reject outside
  *   [min_x, max_x) x [min_y, max_y);
- *   O = S_k^-1 (0) (camera centre), d = |x - O|; reject unless
+ *   O = -(R^T t) / s (camera centre), d = |x - O|; reject unless
  *   min_dist <= d <= max_dist, and if (x - O) . n < cos_min d (n the
  *   point's mean viewing direction);
  *   level = smallest L >= 0 with max_dist <= d scale^L (scale^L by
@@ -1125,9 +1126,9 @@ EXPORT void og_correct_points(int n, const double *before, const double *after, 
  *   |v_f - v| < radius and level - 1 <= octave <= level (search: and not
  *   matched before); best = smallest Hamming distance of the 256-bit
  *   descriptors, ties to the lower feature index; a match if best <= th_low.
- * Every floating-point step is written out in one fixed order without
- * contraction (-std=c99), so a GPU that performs the same IEEE operations
- * in the same order takes the same decisions.
+ * Every floating-point step is one IEEE single operation in a fixed order
+ * (no contraction under -std=c99), so a GPU performing the same operations in
+ * the same order takes the same decisions.
  * Conflicts (reading; the paper resolves them on the CPU after the kernel):
  *   search: a feature chosen by several points goes to the one with the
  *   smallest (distance, point index); the others get no match;
@@ -1136,11 +1137,11 @@ EXPORT void og_correct_points(int n, const double *before, const double *after, 
  *   its observation and the others fuse with that point; a feature that has
  *   a map point makes every loop point choosing it fuse with that point. */
 typedef struct {
-  double fx, fy, cx, cy;
-  double min_x, max_x, min_y, max_y;
-  double scale_factor;
-  double th;          /* search radius at level 0, pixels */
-  double cos_min;     /* minimum cosine of the viewing angle */
+  float fx, fy, cx, cy;
+  float min_x, max_x, min_y, max_y;
+  float scale_factor;
+  float th;           /* search radius at level 0, pixels */
+  float cos_min;      /* minimum cosine of the viewing angle */
   int n_levels;
   int th_low;         /* largest accepted Hamming distance */
 } og_proj_params;
@@ -1157,55 +1158,48 @@ static int hamming256(const uint32_t *a, const uint32_t *b) {
   return d;
 }
 
-/* R(q) of a quaternion (x, y, z, w) after normalisation, in a fixed order of
- * single operations: n = sqrt(x x + y y + z z + w w), then x/n, ... */
-static void proj_rotation(const double *q, double *R) {
-  double n = sqrt(((q[0] * q[0] + q[1] * q[1]) + q[2] * q[2]) + q[3] * q[3]);
-  double x = q[0] / n, y = q[1] / n, z = q[2] / n, w = q[3] / n;
-  R[0] = 1.0 - 2.0 * (y * y + z * z); R[1] = 2.0 * (x * y - w * z);       R[2] = 2.0 * (x * z + w * y);
-  R[3] = 2.0 * (x * y + w * z);       R[4] = 1.0 - 2.0 * (x * x + z * z); R[5] = 2.0 * (y * z - w * x);
-  R[6] = 2.0 * (x * z - w * y);       R[7] = 2.0 * (y * z + w * x);       R[8] = 1.0 - 2.0 * (x * x + y * y);
-}
-
-/* One (keyframe, point) pair: the predicted feature index (-1: none) and its
- * Hamming distance.  Features of the keyframe: f in [0, nf). */
+/* One (keyframe, point) pair: the predicted feature index (-1: none) and the
+ * Hamming distance of its best candidate (256 if none).  Features of the
+ * keyframe: f in [0, nf). */
 static int proj_pair(const og_proj_params *pp, const double *pose8, int nf, const float *fu, const float *fv,
                      const int32_t *foct, const uint32_t *fdesc, const uint8_t *fskip,
-                     const double *X, const uint32_t *pdesc, double min_dist, double max_dist, const double *nrm,
+                     const float *X, const uint32_t *pdesc, float min_dist, float max_dist, const float *nrm,
                      int *best_dist) {
-  double R[9];
-  proj_rotation(pose8, R);
-  const double s = pose8[7], t0 = pose8[4], t1 = pose8[5], t2 = pose8[6];
-  const double px = s * ((R[0] * X[0] + R[1] * X[1]) + R[2] * X[2]) + t0;
-  const double py = s * ((R[3] * X[0] + R[4] * X[1]) + R[5] * X[2]) + t1;
-  const double pz = s * ((R[6] * X[0] + R[7] * X[1]) + R[8] * X[2]) + t2;
+  const float qx = (float)pose8[0], qy = (float)pose8[1], qz = (float)pose8[2], qw = (float)pose8[3];
+  const float t0 = (float)pose8[4], t1 = (float)pose8[5], t2 = (float)pose8[6], s = (float)pose8[7];
+  const float n = sqrtf(((qx * qx + qy * qy) + qz * qz) + qw * qw);
+  const float x = qx / n, y = qy / n, z = qz / n, w = qw / n;
+  float R[9];
+  R[0] = 1.0f - 2.0f * (y * y + z * z); R[1] = 2.0f * (x * y - w * z);        R[2] = 2.0f * (x * z + w * y);
+  R[3] = 2.0f * (x * y + w * z);        R[4] = 1.0f - 2.0f * (x * x + z * z); R[5] = 2.0f * (y * z - w * x);
+  R[6] = 2.0f * (x * z - w * y);        R[7] = 2.0f * (y * z + w * x);        R[8] = 1.0f - 2.0f * (x * x + y * y);
+  const float px = s * ((R[0] * X[0] + R[1] * X[1]) + R[2] * X[2]) + t0;
+  const float py = s * ((R[3] * X[0] + R[4] * X[1]) + R[5] * X[2]) + t1;
+  const float pz = s * ((R[6] * X[0] + R[7] * X[1]) + R[8] * X[2]) + t2;
   *best_dist = 256;
-  if (!(pz > 0.0)) return -1;
-  const double u = pp->fx * px / pz + pp->cx;
-  const double v = pp->fy * py / pz + pp->cy;
+  if (!(pz > 0.0f)) return -1;
+  const float u = pp->fx * px / pz + pp->cx;
+  const float v = pp->fy * py / pz + pp->cy;
   if (u < pp->min_x || u >= pp->max_x || v < pp->min_y || v >= pp->max_y) return -1;
-  /* camera centre O = -R^T t / s */
-  const double ox = -((R[0] * t0 + R[3] * t1) + R[6] * t2) / s;
-  const double oy = -((R[1] * t0 + R[4] * t1) + R[7] * t2) / s;
-  const double oz = -((R[2] * t0 + R[5] * t1) + R[8] * t2) / s;
-  const double dx = X[0] - ox, dy = X[1] - oy, dz = X[2] - oz;
-  const double dist = sqrt((dx * dx + dy * dy) + dz * dz);
+  const float ox = -((R[0] * t0 + R[3] * t1) + R[6] * t2) / s;
+  const float oy = -((R[1] * t0 + R[4] * t1) + R[7] * t2) / s;
+  const float oz = -((R[2] * t0 + R[5] * t1) + R[8] * t2) / s;
+  const float dx = X[0] - ox, dy = X[1] - oy, dz = X[2] - oz;
+  const float dist = sqrtf((dx * dx + dy * dy) + dz * dz);
   if (dist < min_dist || dist > max_dist) return -1;
   if ((dx * nrm[0] + dy * nrm[1]) + dz * nrm[2] < pp->cos_min * dist) return -1;
   int level = 0;
-  double sc = 1.0;
+  float sc = 1.0f;
   while (level < pp->n_levels - 1 && max_dist > dist * sc) {
     sc = sc * pp->scale_factor;
     ++level;
   }
-  double scale_l = 1.0;
-  for (int l = 0; l < level; ++l) scale_l = scale_l * pp->scale_factor;
-  const double r = pp->th * scale_l;
+  const float r = pp->th * sc;   /* sc = scale^level */
   int best = -1, bd = 256;
   for (int f = 0; f < nf; ++f) {
     if (fskip && fskip[f]) continue;
     if (foct[f] < level - 1 || foct[f] > level) continue;
-    if (!(fabs((double)fu[f] - u) < r) || !(fabs((double)fv[f] - v) < r)) continue;
+    if (!(fabsf(fu[f] - u) < r) || !(fabsf(fv[f] - v) < r)) continue;
     const int d = hamming256(fdesc + 8 * (size_t)f, pdesc);
     if (d < bd) { bd = d; best = f; }
   }
@@ -1214,19 +1208,20 @@ static int proj_pair(const og_proj_params *pp, const double *pose8, int nf, cons
 }
 
 /* mode 0: projection search, mode 1: loop fusion.  K keyframes with poses
- * (K x 8) and features in CSR (feat_ptr[K + 1]; fu, fv float, foct int32,
- * fdesc 8 uint32 per feature; fskip: search, nonzero = matched before
- * (nullable); fmp: fusion, the map point id at each feature or -1).  P points:
- * X (P x 3), pdesc (P x 8), min/max distance, normal (P x 3), pid (fusion:
- * the point's map point id; a keyframe with a feature holding that id already
- * observes the point and is skipped).  Outputs K x P: match (feature index
- * within the keyframe or -1), dist (Hamming distance of the best candidate,
- * 256 if none), fuse (fusion: the map point id the point fuses with, -1 = it
- * adds a new observation; search: unused, may be NULL). */
+ * (K x 8, double, taken to float) and features in CSR (feat_ptr[K + 1]; fu,
+ * fv float, foct int32, fdesc 8 uint32 per feature; fskip: search, nonzero =
+ * matched before (nullable); fmp: fusion, the map point id at each feature
+ * or -1).  P points (float): X (P x 3), pdesc (P x 8 uint32), min/max
+ * distance, normal (P x 3), pid (fusion: the point's map point id; a
+ * keyframe with a feature holding that id already observes the point and is
+ * skipped).  Outputs K x P: match (feature index within the keyframe or -1),
+ * dist (Hamming distance of the best candidate, 256 if none), fuse (fusion:
+ * the map point id the point fuses with, -1 = it adds a new observation;
+ * search: may be NULL). */
 EXPORT void og_project_match(const og_proj_params *pp, int mode, int K, const double *poses, const int32_t *feat_ptr,
                              const float *fu, const float *fv, const int32_t *foct, const uint32_t *fdesc,
-                             const uint8_t *fskip, const int32_t *fmp, int P, const double *X, const uint32_t *pdesc,
-                             const double *min_dist, const double *max_dist, const double *nrm, const int32_t *pid,
+                             const uint8_t *fskip, const int32_t *fmp, int P, const float *X, const uint32_t *pdesc,
+                             const float *min_dist, const float *max_dist, const float *nrm, const int32_t *pid,
                              int32_t *match, int32_t *dist, int32_t *fuse) {
   for (int k = 0; k < K; ++k) {
     const int f0 = feat_ptr[k], nf = feat_ptr[k + 1] - feat_ptr[k];

@@ -10,7 +10,7 @@ __version__ = "0.1.0"
 
 def __getattr__(name):
     if name in ("PoseGraph", "evaluate_cost", "default_options", "PGOError", "solve_pose_graph", "PoseGraphBatch",
-                "propagate_correction", "correct_points"):
+                "propagate_correction", "correct_points", "Frames", "match_params"):
         from . import api
         return getattr(api, name)
     raise AttributeError(name)

@@ -40,6 +40,7 @@ EXPORTED = [
     "pgo_graph_damped_step", "pgo_graph_resolve", "pgo_graph_report", "pgo_solve", "pgo_backward", "pgo_batch_create", "pgo_batch_destroy",
     "pgo_batch_solve", "pgo_batch_schedule", "pgo_evaluate_cost", "pgo_evaluate_cost_noalloc",
     "pgo_graph_multigrid_info", "pgo_graph_precondition", "pgo_propagate_correction", "pgo_correct_points",
+    "pgo_frames_create", "pgo_frames_destroy", "pgo_project_match",
 ]
 
 
@@ -56,6 +57,29 @@ class SolveOptions(ctypes.Structure):
                 ("pcg_tol", c_double), ("pcg_max_iters", c_int32), ("refine_steps", c_int32),
                 ("refine_tol", c_double), ("polish_iters", c_int32), ("schedule", c_int32),
                 ("preconditioner", c_int32), ("multigrid_refresh", c_int32)]
+
+
+class FramesDesc(ctypes.Structure):
+    _fields_ = [("n_keyframes", c_int32), ("mem_space", c_int32), ("feat_ptr", ctypes.c_void_p),
+                ("uv", ctypes.c_void_p), ("octave", ctypes.c_void_p), ("desc", ctypes.c_void_p),
+                ("map_point", ctypes.c_void_p), ("min_x", ctypes.c_float), ("max_x", ctypes.c_float),
+                ("min_y", ctypes.c_float), ("max_y", ctypes.c_float), ("stream", ctypes.c_void_p)]
+
+
+class MatchParams(ctypes.Structure):
+    _fields_ = [(k, ctypes.c_float) for k in ("fx", "fy", "cx", "cy", "min_x", "max_x", "min_y", "max_y",
+                                                "scale_factor", "th", "cos_min")] + [("n_levels", c_int32),
+                                                                                     ("th_low", c_int32)]
+
+
+class PointsDesc(ctypes.Structure):
+    _fields_ = [("n_points", c_int32), ("xyz", ctypes.c_void_p), ("desc", ctypes.c_void_p),
+                ("min_dist", ctypes.c_void_p), ("max_dist", ctypes.c_void_p), ("normal", ctypes.c_void_p),
+                ("id", ctypes.c_void_p)]
+
+
+PGO_MATCH_SEARCH = 0
+PGO_MATCH_FUSE = 1
 
 
 class Report(ctypes.Structure):
@@ -109,6 +133,11 @@ def load(build_if_missing: bool = True):
         lib.pgo_graph_report.argtypes = [vp, ctypes.POINTER(Report)]
         lib.pgo_propagate_correction.argtypes = [c_int32, vp, c_int32, vp, c_int32, vp, vp, vp, vp]
         lib.pgo_correct_points.argtypes = [c_int32, vp, vp, c_int32, vp, vp, vp, vp, vp]
+        lib.pgo_frames_create.argtypes = [ctypes.POINTER(FramesDesc), ctypes.POINTER(vp)]
+        lib.pgo_frames_destroy.argtypes = [vp]
+        lib.pgo_frames_destroy.restype = None
+        lib.pgo_project_match.argtypes = [vp, ctypes.POINTER(MatchParams), c_int32, vp, vp, ctypes.POINTER(PointsDesc),
+                                          vp, vp, vp]
         lib.pgo_graph_precondition.argtypes = [vp, ctypes.POINTER(SolveOptions), c_double]
         lib.pgo_graph_multigrid_info.argtypes = [vp, ctypes.POINTER(c_int32), vp, vp, vp, vp]
         lib.pgo_solve.argtypes = [vp, ctypes.POINTER(SolveOptions), ctypes.POINTER(Report), vp, c_int32]
@@ -123,7 +152,8 @@ def load(build_if_missing: bool = True):
         lib.pgo_evaluate_cost_noalloc.argtypes = [c_int32, c_int32, vp, vp, vp, vp, vp, vp, vp, vp]
         for name in EXPORTED:
             fn = getattr(lib, name)
-            if name not in ("pgo_last_error", "pgo_version", "pgo_graph_destroy", "pgo_batch_destroy"):
+            if name not in ("pgo_last_error", "pgo_version", "pgo_graph_destroy", "pgo_batch_destroy",
+                            "pgo_frames_destroy"):
                 fn.restype = ctypes.c_int
         _lib = lib
         return lib

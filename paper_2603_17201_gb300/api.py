@@ -16,7 +16,7 @@ import numpy as np
 from . import _lib as L
 
 __all__ = ["PoseGraph", "PoseGraphBatch", "evaluate_cost", "default_options", "PGOError", "solve_pose_graph",
-           "propagate_correction", "correct_points"]
+           "propagate_correction", "correct_points", "Frames", "match_params"]
 
 PGOError = L.PGOError
 default_options = L.default_options
@@ -469,3 +469,110 @@ def correct_points(poses_before, poses_after, points, ref, out=None, return_bad=
     L.check(lib.pgo_correct_points(b.shape[0], ptr(b), ptr(a), X.shape[0], ptr(X), ptr(r), ptr(out), ptr(bad),
                                    _current_stream_handle()))
     return (out, bad) if return_bad else out
+
+
+def _dev(x, dtype):
+    torch = _torch()
+    tdt = {np.float32: torch.float32, np.float64: torch.float64, np.int32: torch.int32, np.uint8: torch.uint8,
+           np.uint32: torch.int32}[dtype]
+    if isinstance(x, torch.Tensor):
+        return x.to(device="cuda").contiguous()
+    a = np.ascontiguousarray(x, dtype=dtype)
+    if dtype == np.uint32:
+        a = a.view(np.int32)
+    return torch.from_numpy(a).to(device="cuda").contiguous()
+
+
+def match_params(camera, n_levels=8, scale_factor=1.2, th=10.0, cos_min=0.5, th_low=50):
+    """pgo_match_params from a camera dict (fx, fy, cx, cy, min_x, max_x,
+    min_y, max_y) and the search settings."""
+    p = L.MatchParams()
+    for k in ("fx", "fy", "cx", "cy", "min_x", "max_x", "min_y", "max_y"):
+        setattr(p, k, float(camera[k]))
+    p.scale_factor, p.th, p.cos_min = float(scale_factor), float(th), float(cos_min)
+    p.n_levels, p.th_low = int(n_levels), int(th_low)
+    return p
+
+
+class Frames:
+    """Keyframe features resident on the device (pgo_frames_create):
+    feat_ptr (K + 1,), uv (F, 2) float32, octave (F,), desc (F, 8) uint32,
+    map_point (F,) or None, image bounds (min_x, max_x, min_y, max_y)."""
+
+    def __init__(self, feat_ptr, uv, octave, desc, map_point=None, bounds=(0.0, 752.0, 0.0, 480.0), stream=None):
+        self._lib = L.load()
+        self._h = ctypes.c_void_p()
+        ptr = np.ascontiguousarray(feat_ptr, dtype=np.int32)
+        self.K = int(ptr.shape[0] - 1)
+        self.n_features = int(ptr[-1])
+        m = _Marshal(False)
+        d = L.FramesDesc()
+        d.n_keyframes = self.K
+        d.mem_space = L.PGO_MEM_HOST
+        d.feat_ptr = m.put(ptr, np.int32)
+        d.uv = self._put_f32(m, uv)
+        d.octave = m.put(octave, np.int32)
+        dd = np.ascontiguousarray(desc, dtype=np.uint32).reshape(-1)
+        m.keep.append(dd)
+        d.desc = ctypes.c_void_p(dd.ctypes.data)
+        d.map_point = m.put(map_point, np.int32)
+        d.min_x, d.max_x, d.min_y, d.max_y = (float(b) for b in bounds)
+        d.stream = stream if stream is not None else _current_stream_handle()
+        L.check(self._lib.pgo_frames_create(ctypes.byref(d), ctypes.byref(self._h)))
+        self.bounds = tuple(float(b) for b in bounds)
+
+    @staticmethod
+    def _put_f32(m, x):
+        a = np.ascontiguousarray(x, dtype=np.float32).reshape(-1)
+        m.keep.append(a)
+        return ctypes.c_void_p(a.ctypes.data)
+
+    @classmethod
+    def from_workload(cls, w):
+        cam = w.camera
+        return cls(w.feat_ptr, np.stack([w.fu, w.fv], axis=1), w.foct, w.fdesc, w.fmp,
+                   (cam["min_x"], cam["max_x"], cam["min_y"], cam["max_y"]))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            self._lib.pgo_frames_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def project_match(self, params, mode, poses, xyz, desc, min_dist, max_dist, normal, ids=None, matched=None):
+        """pgo_project_match over every (keyframe, point) pair; returns CUDA
+        tensors (match, dist, fuse) of shape (K, P) (fuse None for the
+        search).  Inputs are host arrays or CUDA tensors."""
+        torch = _torch()
+        mode_i = L.PGO_MATCH_SEARCH if mode == "search" else L.PGO_MATCH_FUSE
+        X = _dev(xyz, np.float32).reshape(-1)
+        P = X.numel() // 3
+        D = _dev(desc, np.uint32).reshape(-1)
+        mn, mx = _dev(min_dist, np.float32), _dev(max_dist, np.float32)
+        nr = _dev(normal, np.float32).reshape(-1)
+        idt = _dev(ids, np.int32) if ids is not None else None
+        pz = _dev(poses, np.float64).reshape(-1)
+        mt = _dev(matched, np.uint8) if (matched is not None and mode_i == L.PGO_MATCH_SEARCH) else None
+        match = torch.empty((self.K, P), dtype=torch.int32, device="cuda")
+        dist = torch.empty((self.K, P), dtype=torch.int32, device="cuda")
+        fuse = torch.empty((self.K, P), dtype=torch.int32, device="cuda") if mode_i == L.PGO_MATCH_FUSE else None
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else None  # noqa: E731
+        pd = L.PointsDesc()
+        pd.n_points = P
+        pd.xyz, pd.desc, pd.min_dist, pd.max_dist, pd.normal, pd.id = (ptr(X), ptr(D), ptr(mn), ptr(mx), ptr(nr),
+                                                                       ptr(idt))
+        L.check(self._lib.pgo_project_match(self._h, ctypes.byref(params), mode_i, ptr(pz), ptr(mt), ctypes.byref(pd),
+                                            ptr(match), ptr(dist), ptr(fuse)))
+        self._keep = (X, D, mn, mx, nr, idt, pz, mt)
+        return match, dist, fuse
+
+    def match_workload(self, w, mode, th=10.0, th_low=50, cos_min=0.5, poses=None):
+        """project_match with the arrays of a synthetic MatchWorkload."""
+        p = match_params(w.camera, w.n_levels, w.scale_factor, th, cos_min, th_low)
+        return self.project_match(p, mode, w.poses if poses is None else poses, w.points, w.pdesc, w.min_dist,
+                                  w.max_dist, w.normal, w.pid, w.fskip if mode == "search" else None)

@@ -274,6 +274,46 @@ void launch_eval_cost_raw(int N, int E, const int* ei, const int* ej, const doub
 void launch_eval_cost_raw_blocks(int N, int E, const int* ei, const int* ej, const double* meas, const double* w,
                                  const double* poses, double* partial, unsigned* ticket, int* bad,
                                  double* cost_out, int* bad_out, int blocks, cudaStream_t s);
+// ---- projection search and loop fusion (matching.cu) ----
+constexpr int kGridCols = 64;   // image grid of the feature buckets
+constexpr int kGridRows = 48;
+
+// Device view of a frames object: K keyframes' features sorted by grid cell.
+struct FramesDev {
+  int K, n_features;
+  float inv_cw, inv_ch;          // grid cells per pixel (x, y)
+  const int* kf_ptr;             // K + 1: first feature of each keyframe (caller order)
+  const int* cell_ptr;           // K * cells + 1: first sorted feature of each (keyframe, cell)
+  const float2* uv;              // sorted: keypoint position
+  const int* oct;                // sorted: octave
+  const int* orig;               // sorted: the caller's feature index within its keyframe
+  const uint4* desc;             // sorted: 256-bit descriptor (2 x uint4)
+  const int* mp;                 // caller order: map point id at each feature (-1: none)
+  const int* obs_ptr;            // K + 1
+  const int* obs_ids;            // per keyframe, ascending: the map point ids it observes
+  float* kf_tab;                 // K x 16: per-call keyframe pose table
+  unsigned long long* win;       // n_features: per-call claims (distance, point)
+};
+
+struct MatchParams {
+  float fx, fy, cx, cy, min_x, max_x, min_y, max_y, scale_factor, th, cos_min;
+  int n_levels, th_low;
+};
+
+struct PointsDev {
+  int n;
+  const float* xyz;              // n x 3
+  const unsigned* desc;          // n x 8
+  const float* min_dist;
+  const float* max_dist;
+  const float* normal;           // n x 3
+  const int* id;                 // n (fusion)
+};
+
+cudaError_t launch_project_match(const FramesDev& F, const MatchParams& mp, int mode, const double* poses,
+                                 const unsigned char* matched, const PointsDev& pts, int* match, int* dist, int* fuse,
+                                 cudaStream_t s);
+
 // Loop-correction steps around the optimisation (correction.cu).
 cudaError_t launch_propagate_correction(int n, const double* poses, int current, const double* corrected, int n_conn,
                                         const int* conn, double* out, int* bad, cudaStream_t s);

@@ -582,5 +582,6 @@ def make_match_workload(mode="search", n_kf=3, n_points=4000, features_per_kf=12
         poses=np.ascontiguousarray(S), feat_ptr=np.array(feat_ptr, dtype=np.int32),
         fu=np.concatenate(fu), fv=np.concatenate(fv), foct=np.concatenate(foct),
         fdesc=np.ascontiguousarray(np.concatenate(fdesc)), fskip=np.concatenate(fskip), fmp=np.concatenate(fmp),
-        points=np.ascontiguousarray(X), pdesc=pdesc, min_dist=min_dist, max_dist=max_dist,
-        normal=np.ascontiguousarray(nrm), pid=pid, truth=truth)
+        points=np.ascontiguousarray(X, dtype=np.float32), pdesc=pdesc, min_dist=min_dist.astype(np.float32),
+        max_dist=max_dist.astype(np.float32), normal=np.ascontiguousarray(nrm, dtype=np.float32), pid=pid,
+        truth=truth)

@@ -117,3 +117,32 @@ def test_allocation_limit_gives_oom_and_no_handle(lib):
         assert b"exceeds the test limit" in lib.pgo_last_error()
     finally:
         lib.pgo_test_set_alloc_limit(0)
+
+
+@pytest.mark.parametrize("case", ["no_keyframes", "bounds", "ptr_order", "nan_uv"])
+def test_frames_create_rejects_bad_input(lib, case):
+    """pgo_frames_create validates on the host before any device work."""
+    K, F = 2, 6
+    ptr = np.array([0, 3, 6], np.int32)
+    uv = np.zeros((F, 2), np.float32)
+    oct_ = np.zeros(F, np.int32)
+    desc = np.zeros((F, 8), np.uint32)
+    d = L.FramesDesc()
+    d.n_keyframes = K
+    d.mem_space = L.PGO_MEM_HOST
+    d.min_x, d.max_x, d.min_y, d.max_y = 0.0, 752.0, 0.0, 480.0
+    if case == "no_keyframes":
+        d.n_keyframes = 0
+    elif case == "bounds":
+        d.max_x = 0.0
+    elif case == "ptr_order":
+        ptr[1] = 7
+    elif case == "nan_uv":
+        uv[4, 1] = np.nan
+    d.feat_ptr = ptr.ctypes.data
+    d.uv = uv.ctypes.data
+    d.octave = oct_.ctypes.data
+    d.desc = desc.ctypes.data
+    h = ctypes.c_void_p()
+    assert lib.pgo_frames_create(ctypes.byref(d), ctypes.byref(h)) == L.PGO_ERR_INVALID_ARG
+    assert h.value is None
