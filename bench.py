@@ -475,12 +475,13 @@ def single_leg(name, steps, flush, torch, max_iters=MAX_ITERS):
     return out
 
 
-def correction_leg(torch, flush, name="c3_corridor_8k", points_per_kf=150, reps=10):
+def correction_leg(torch, flush, name="c3_corridor_8k", points_per_kf=150, reps=50):
     """Loop-correction steps on a graph's keyframes and map points
     (`points_per_kf` per keyframe): pgo_propagate_correction of the connected
     keyframes and pgo_correct_points of every map point (the post-optimisation
-    pass), device-resident arrays, L2 flushed before each timed call, CUDA
-    events on the current stream, median of `reps`.  Roofline of the point
+    pass), device-resident arrays, L2 flushed before the timed calls, CUDA
+    events on the current stream around `reps` back-to-back C ABI calls
+    (mean per call).  Roofline of the point
     pass: 52 bytes (point read and write, reference index) and 9 FP64 fused
     multiply-adds (18 flops) per point; the FP64 rate bounds it."""
     import numpy as np
@@ -495,23 +496,31 @@ def correction_leg(torch, flush, name="c3_corridor_8k", points_per_kf=150, reps=
     X, ref = t(lc.points), t(lc.ref, torch.int32)
     out_p = propagate_correction(poses, lc.current, corr, conn)
     out_x = correct_points(poses, out_p, X, ref)
-
-    def timed(fn):
-        ms = []
-        for _ in range(reps):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            fn()
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
-        return statistics.median(ms)
-
-    ms_prop = timed(lambda: propagate_correction(poses, lc.current, corr, conn))
-    ms_pts = timed(lambda: correct_points(poses, out_p, X, ref, out=out_x))
+    # the C ABI calls with their device pointers marshalled once, `reps` calls
+    # back to back between the events: the device time, not Python's
+    import ctypes
+    from paper_2603_17201_gb300 import _lib
+    lib = _lib.load()
+    ptr = lambda x: ctypes.c_void_p(x.data_ptr())  # noqa: E731
+    h_stream = ctypes.c_void_p(stream.cuda_stream)
     P, N = X.shape[0], g.n_vertices
+    prop_args = (N, ptr(poses), int(lc.current), ptr(corr), int(conn.numel()), ptr(conn), ptr(out_p), None, h_stream)
+    pts_args = (N, ptr(poses), ptr(out_p), P, ptr(X), ptr(ref), ptr(out_x), None, h_stream)
+
+    def timed(fn, args):
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn(*args)
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    ms_prop = timed(lib.pgo_propagate_correction, prop_args)
+    ms_pts = timed(lib.pgo_correct_points, pts_args)
     bytes_ = 52 * P + N * (2 * 64 + 2 * 128)
     flops = 18 * P
     peaks, peak_kind = measured_peaks()
@@ -533,10 +542,10 @@ def correction_leg(torch, flush, name="c3_corridor_8k", points_per_kf=150, reps=
 
 def matching_leg(torch, flush, reps=20):
     """Projection search PS3a-c (3 keyframes, 4,000 map points) and loop
-    fusion (30 connected keyframes, 4,000 loop map points): one
-    pgo_project_match call each on device-resident features (a frames
-    object) and points, L2 flushed before each timed call, CUDA events on
-    the current stream, median of `reps`.  Throughput in (keyframe, point)
+    fusion (30 connected keyframes, 4,000 loop map points): pgo_project_match
+    on device-resident features (a frames object) and points, L2 flushed
+    before the timed calls, CUDA events on the current stream around `reps`
+    back-to-back C ABI calls (mean per call).  Throughput in (keyframe, point)
     pairs per second; the compulsory traffic (points, features and outputs
     once) is a few MB, so the call is bound by latency and the integer
     popcount work of the candidate comparisons, not by HBM."""
@@ -554,18 +563,30 @@ def matching_leg(torch, flush, reps=20):
         args = (t(w.poses, torch.float64), t(w.points, torch.float32), t(w.pdesc.view(np.int32), torch.int32),
                 t(w.min_dist, torch.float32), t(w.max_dist, torch.float32), t(w.normal, torch.float32),
                 t(w.pid, torch.int32), t(w.fskip, torch.uint8) if mode == "search" else None)
-        call = lambda: fr.project_match(prm, mode, *args[:7], matched=args[7])  # noqa: E731
-        m, _, _ = call()
-        ms = []
+        m, _, f = fr.project_match(prm, mode, *args[:7], matched=args[7])
+        # the C ABI call with its arguments marshalled once, `reps` calls back
+        # to back between the events
+        import ctypes
+        from paper_2603_17201_gb300 import _lib
+        lib = _lib.load()
+        ptr = lambda x: ctypes.c_void_p(x.data_ptr()) if x is not None else None  # noqa: E731
+        pdsc = _lib.PointsDesc()
+        pdsc.n_points = int(w.points.shape[0])
+        pdsc.xyz, pdsc.desc, pdsc.min_dist, pdsc.max_dist, pdsc.normal, pdsc.id = (
+            ptr(args[1]), ptr(args[2]), ptr(args[3]), ptr(args[4]), ptr(args[5]), ptr(args[6]))
+        dist = torch.empty_like(m)
+        cargs = (fr._h, ctypes.byref(prm), 0 if mode == "search" else 1, ptr(args[0]), ptr(args[7]),
+                 ctypes.byref(pdsc), ptr(m), ptr(dist), ptr(f))
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
         for _ in range(reps):
-            flush.fill_(1.0)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            call()
-            e1.record(stream)
-            e1.synchronize()
-            ms.append(e0.elapsed_time(e1))
+            lib.pgo_project_match(*cargs)
+        e1.record(stream)
+        e1.synchronize()
+        ms = [e0.elapsed_time(e1) / reps]
         tm = statistics.median(ms)
         P = w.points.shape[0]
         out[name] = {"keyframes": K, "points": P, "features": int(w.feat_ptr[-1]), "us_per_call": 1e3 * tm,

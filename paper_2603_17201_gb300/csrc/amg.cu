@@ -835,7 +835,7 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
   const AmgDev& A = sA;
   unsigned* counter = &st->ticket[T_AMG];
   int* abort_flag = reinterpret_cast<int*>(&st->ticket[T_AMG_ABORT]);
-  GridTarget target(g.opt->barrier_limit_ns);
+  unsigned target = 0;
   constexpr int BLK = AV<V>::BLK;
   const V lam = V(st->lambda);
   const int cur = st->cur;
@@ -1134,6 +1134,12 @@ cudaError_t launch_amg_setup(const DevGraph& g, const AmgDev& amg, int mixed, in
   cudaError_t e = cudaFuncSetAttribute(k_amg_setup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   return cudaLaunchKernelEx(&cfg, k_amg_setup<double>, g, lm);
+}
+
+// Test hook: the grid-barrier wait limit of this file's kernels (0: 2 s).
+void set_barrier_limit_amg(unsigned long long ns) {
+  cudaMemcpyToSymbol(g_barrier_limit_ns, &ns, sizeof(ns));
+  cudaGetLastError();
 }
 
 }  // namespace pgo

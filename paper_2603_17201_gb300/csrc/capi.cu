@@ -50,10 +50,9 @@ pgo_status fail(pgo_status st, const char* fmt, ...) {
 
 // Test hook: fail device allocations above this many bytes (0 = off).
 size_t g_alloc_limit = 0;
-// Test hooks of the bounded grid barrier: a PCG block that never arrives
-// (-1 = off) and the wait limit in ns (0 = the 2 s default).
+// Test hook of the bounded grid barrier: a PCG block that never arrives
+// (-1 = off).
 int g_test_absent_block = -1;
-unsigned long long g_barrier_limit_ns = 0;
 
 // One device arena per graph, sub-allocated with 256-byte alignment.
 struct Arena {
@@ -181,7 +180,6 @@ void fill_dev_options(const pgo_solve_options& o, DevOptions* d) {
   d->lambda_fixed = 0.0;
   d->amg_refresh = o.multigrid_refresh;
   d->test_absent_block = g_test_absent_block;
-  d->barrier_limit_ns = g_barrier_limit_ns;
 }
 
 pgo_status check_options(const pgo_solve_options& o) {
@@ -438,7 +436,9 @@ void pgo_test_set_alloc_limit(size_t bytes) { g_alloc_limit = bytes; }
 // the other blocks wait out the limit, the solve stops and reports
 // PGO_ERR_CUDA: this exercises the bounded wait without any device fault.
 void pgo_test_set_barrier(double limit_s, int absent_block) {
-  g_barrier_limit_ns = limit_s > 0.0 ? (unsigned long long)(limit_s * 1e9) : 0ull;
+  const unsigned long long ns = limit_s > 0.0 ? (unsigned long long)(limit_s * 1e9) : 0ull;
+  set_barrier_limit_pcg(ns);
+  set_barrier_limit_amg(ns);
   g_test_absent_block = absent_block;
 }
 

@@ -21,33 +21,31 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
 
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;   // 2 s: only reached on a fault
 
-// Per-block barrier state of one launch: the arrival count the next barrier
-// waits for, and the wait limit (DevOptions::barrier_limit_ns, 2 s unless a
-// test shortens it).
-struct GridTarget {
-  unsigned n;
-  unsigned long long limit_ns;
-  __device__ explicit GridTarget(unsigned long long limit) : n(0u), limit_ns(limit ? limit : kBarrierTimeoutNs) {}
-};
+// Wait limit of the grid barriers in ns (0: the 2 s default).  Each
+// translation unit with grid barriers has its own copy, which a test hook
+// shortens (set_barrier_limit_*); it is read only after 256 spins.
+static __device__ unsigned long long g_barrier_limit_ns = 0ull;
 
 // All blocks of the (co-resident) grid arrive; returns false if the wait
 // exceeded the time limit or another block reported a timeout.  The counter
-// is monotone within a launch (the target advances by gridDim.x per barrier).
-__device__ __forceinline__ bool grid_sync(unsigned* counter, int* abort_flag, GridTarget& target) {
+// is monotone within a launch (target advances by gridDim.x per barrier).
+__device__ __forceinline__ bool grid_sync(unsigned* counter, int* abort_flag, unsigned& target) {
   __shared__ int ok;
   __syncthreads();
-  target.n += gridDim.x;
+  target += gridDim.x;
   if (threadIdx.x == 0) {
     ok = 1;
     red_release_add(counter, 1u);
     const unsigned long long t0 = globaltimer_ns();
     unsigned spins = 0;
-    while (ld_acquire_u32(counter) < target.n) {
-      if ((++spins & 255u) == 0u &&
-          (globaltimer_ns() - t0 > target.limit_ns || *(volatile int*)abort_flag)) {
-        atomicExch(abort_flag, 1);
-        ok = 0;
-        break;
+    while (ld_acquire_u32(counter) < target) {
+      if ((++spins & 255u) == 0u) {
+        const unsigned long long lim = *(volatile unsigned long long*)&g_barrier_limit_ns;
+        if (globaltimer_ns() - t0 > (lim ? lim : kBarrierTimeoutNs) || *(volatile int*)abort_flag) {
+          atomicExch(abort_flag, 1);
+          ok = 0;
+          break;
+        }
       }
     }
   }

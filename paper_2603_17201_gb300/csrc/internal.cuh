@@ -51,7 +51,6 @@ struct DevOptions {
   double lambda_fixed;   // lambda of a standalone re-solve
   int amg_refresh;       // rebuild the coarse multigrid levels every k-th LM linearisation
   int test_absent_block; // test hook: this block of the PCG launch never arrives (-1: none)
-  unsigned long long barrier_limit_ns;   // grid-barrier wait limit (0: the 2 s default)
 };
 
 // ---- smoothed-aggregation multigrid preconditioner ----
@@ -321,5 +320,8 @@ size_t point_table_bytes(int n);
 cudaError_t launch_correct_points(int n, const double* before, const double* after, int P, const double* X,
                                   const int* ref, double* table, double* out, int* bad, cudaStream_t s);
 void set_last_error(const char* msg);   // message returned by pgo_last_error()
+// test hooks: grid-barrier wait limit of the PCG and set-up kernels (ns, 0 = 2 s)
+void set_barrier_limit_pcg(unsigned long long ns);
+void set_barrier_limit_amg(unsigned long long ns);
 
 }  // namespace pgo

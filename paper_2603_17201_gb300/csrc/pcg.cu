@@ -410,7 +410,7 @@ constexpr int GC = 32;
 // false on a barrier timeout.
 template <class V, class S, int G>
 __device__ bool vcycle_rest(const DevGraph& g, const AmgDev& A, const L0Ctx<V>& c0, const V* r0v, V* s0, V* z,
-                            S& rz_loc, unsigned* counter, int* abort_flag, GridTarget& target) {
+                            S& rz_loc, unsigned* counter, int* abort_flag, unsigned& target) {
   constexpr int BLK = AV<V>::BLK;
   const int sl = threadIdx.x & (G - 1);
   const int sslot = threadIdx.x / G;
@@ -673,7 +673,7 @@ __global__ void __launch_bounds__(sizeof(V) == 8 ? 256 : 512) k_pcg(DevGraph g, 
   unsigned* counter = &st->ticket[T_PCG_SPMV];
   int* abort_flag = reinterpret_cast<int*>(&st->ticket[T_PCG_UPDATE]);
   S* partial = reinterpret_cast<S*>(g.partial);
-  GridTarget target(o->barrier_limit_ns);
+  unsigned target = 0;
   // test hook: this block never arrives, so the others reach the wait limit
   if ((int)blockIdx.x == o->test_absent_block) return;
 
@@ -1110,6 +1110,12 @@ void launch_refine_residual(const DevGraph& g, int first, cudaStream_t s) {
 
 void launch_refine_accumulate(const DevGraph& g, cudaStream_t s) {
   k_refine_accumulate<<<(g.N * VEC + 255) / 256, 256, 0, s>>>(g);
+}
+
+// Test hook: the grid-barrier wait limit of this file's kernels (0: 2 s).
+void set_barrier_limit_pcg(unsigned long long ns) {
+  cudaMemcpyToSymbol(g_barrier_limit_ns, &ns, sizeof(ns));
+  cudaGetLastError();
 }
 
 }  // namespace pgo
