@@ -53,6 +53,9 @@ def parse():
     ap.add_argument("--roofline-only", action="store_true",
                     help="only the roofline leg: linearise once, then the capped FP32 PCG re-solves "
                          "(an ncu capture of k_pcg should skip 2 launches: the third runs 9 iterations)")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="only one FP64 and one mixed solve of the workload with host-issued launches "
+                         "(every kernel a launch of its own), for per-kernel ncu captures")
     ap.add_argument("--batch", action="store_true",
                     help="the batched form instead: 256 uneven graphs (100..5,000 keyframes) in one persistent "
                          "launch per solve, beside sequential single-graph solves of a sample of them")
@@ -327,6 +330,20 @@ def setup_leg(pg, N, E, stream, flush, torch, reps=7):
             "ms_per_setup": t, "algorithmic_bytes_per_setup": b, "peak_kind": peak_kind}
 
 
+def run_profile_solve(args):
+    import torch
+    from paper_2603_17201_gb300 import PoseGraph
+    from paper_2603_17201_gb300 import synthetic as syn
+    torch.cuda.set_device(0)
+    g = syn.make_config(args.workload)
+    for precision in ("fp64", "mixed"):
+        pg = PoseGraph.from_synthetic(g)
+        rep = pg.solve(max_iters=MAX_ITERS, precision=precision, schedule=SCHED["eager"])
+        print(json.dumps({"precision": precision, "final_cost": rep["final_cost"], "iterations": rep["iterations"],
+                          "pcg_iterations": rep["pcg_iterations"]}), flush=True)
+        pg.close()
+
+
 def run_roofline_only(args):
     import torch
     from paper_2603_17201_gb300 import PoseGraph
@@ -595,6 +612,53 @@ def matching_leg(torch, flush, reps=20):
     return out
 
 
+def solver_sweep_leg(torch, flush, sizes=(100, 200, 300, 400, 600, 800, 1000, 1500, 2000), steps=3):
+    """Direct block Cholesky against the multigrid PCG by graph size (the
+    shape of the paper's Fig. 4 size sweep): figure-8 graphs of N keyframes
+    (window 15, one loop per 400 keyframes), full LM solves from the drifted
+    estimate in each precision, device-resident, L2 flushed before each,
+    CUDA events on the graph's stream, median of `steps`."""
+    from paper_2603_17201_gb300 import PGOError, PoseGraph
+    from paper_2603_17201_gb300 import synthetic as syn
+    dev = torch.device("cuda", torch.cuda.current_device())
+    stream = torch.cuda.current_stream(dev)
+    rows = []
+    for n in sizes:
+        g = syn.make_graph("figure8", n, seed=100 + n, window=15, n_loops=max(1, n // 400))
+        init = torch.as_tensor(g.poses_init, device=dev)
+        pg = PoseGraph(g.n_vertices, g.edge_i, g.edge_j, g.meas, None, None, g.poses_init, 0)
+        row = {"n_vertices": n, "n_edges": g.n_edges}
+        for precision in ("fp64", "mixed"):
+            for solver in ("pcg", "direct"):
+                ms = []
+                try:
+                    for k in range(steps + 1):
+                        flush.fill_(1.0)
+                        e0 = torch.cuda.Event(enable_timing=True)
+                        e1 = torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        pg.set_poses(init)
+                        pg.solve_async(max_iters=MAX_ITERS, precision=precision, linear_solver=solver)
+                        e1.record(stream)
+                        e1.synchronize()
+                        if k > 0:
+                            ms.append(e0.elapsed_time(e1))
+                    rep = pg.solve_report()
+                    row[f"{precision}_{solver}_ms"] = statistics.median(ms)
+                    row[f"{precision}_{solver}_cost"] = rep["final_cost"]
+                except PGOError as e:
+                    row[f"{precision}_{solver}_ms"] = None
+                    row[f"{precision}_{solver}_why"] = str(e)[:80]
+        pg.close()
+        rows.append(row)
+    cross = {}
+    for precision in ("fp64", "mixed"):
+        faster = [r["n_vertices"] for r in rows if r.get(f"{precision}_direct_ms") is not None
+                  and r[f"{precision}_direct_ms"] < r[f"{precision}_pcg_ms"]]
+        cross[precision] = max(faster) if faster else 0
+    return {"rows": rows, "direct_faster_up_to_vertices": cross}
+
+
 def adjoint_leg(steps, torch):
     """The differentiation workload (4,000-keyframe noisy figure-8, 67,857
     edges, weights 1): FP64 forward solve to a stationary point (LM plus
@@ -708,6 +772,7 @@ def run_ours(args):
     if not args.no_extra:
         extra["loop_correction"] = correction_leg(torch, flush)
         extra["matching"] = matching_leg(torch, flush)
+        extra["solver_sweep"] = solver_sweep_leg(torch, flush)
 
     # ---- correctness gate: final cost vs the FP64 oracle ----
     cpu = None
@@ -770,7 +835,9 @@ def main():
     if args.batch:
         run_batch(args)
         return
-    if args.roofline_only:
+    if args.profile_solve:
+        run_profile_solve(args)
+    elif args.roofline_only:
         run_roofline_only(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -121,7 +121,25 @@ typedef struct {
   int32_t multigrid_refresh; /* multigrid inside LM: rebuild the coarse levels
                              at every k-th linearisation, refresh only the
                              finest level in between (1 = always rebuild) */
+  int32_t linear_solver;  /* pgo_linear_solver (PGO_SOLVER_PCG) */
 } pgo_solve_options;
+
+/* Linear solver of the damped step (Sec. IV-F; Fig. 4 compares a direct
+ * factorisation with a GPU sparse solver by problem size).  PCG: the
+ * preconditioned conjugate gradient method with opt->preconditioner.
+ * DIRECT: a block Cholesky factorisation on the GPU -- in keyframe order the
+ * normal matrix is block-banded; the free endpoints of edges longer than 20
+ * keyframes (loop edges) are ordered last as separators (at most 16), and
+ * one thread block factors the band right-looking with its window in shared
+ * memory, then the separators' dense block; the mixed-precision solve
+ * factors in FP32 once per LM iteration and reuses the factor in every FP64
+ * refinement pass.  PGO_ERR_INVALID_ARG if the graph does not fit these
+ * limits (pgo_solve, pgo_graph_damped_step, pgo_graph_resolve only; the
+ * adjoint, the Newton polish and the batched form use PCG).  AUTO: DIRECT
+ * when the graph fits and has at most PGO_DIRECT_CROSSOVER_VERTICES
+ * vertices, PCG otherwise (the crossover measured on GB300). */
+typedef enum { PGO_SOLVER_PCG = 0, PGO_SOLVER_DIRECT = 1, PGO_SOLVER_AUTO = 2 } pgo_linear_solver;
+#define PGO_DIRECT_CROSSOVER_VERTICES 600
 
 /* Solve report. */
 typedef struct {

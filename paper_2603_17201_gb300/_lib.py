@@ -56,7 +56,7 @@ class SolveOptions(ctypes.Structure):
                 ("lambda_init", c_double), ("ftol", c_double), ("gtol", c_double),
                 ("pcg_tol", c_double), ("pcg_max_iters", c_int32), ("refine_steps", c_int32),
                 ("refine_tol", c_double), ("polish_iters", c_int32), ("schedule", c_int32),
-                ("preconditioner", c_int32), ("multigrid_refresh", c_int32)]
+                ("preconditioner", c_int32), ("multigrid_refresh", c_int32), ("linear_solver", c_int32)]
 
 
 class FramesDesc(ctypes.Structure):
@@ -172,6 +172,8 @@ def default_options(**overrides) -> SolveOptions:
     for k, v in overrides.items():
         if k == "precision" and isinstance(v, str):
             v = {"fp64": PGO_FP64, "mixed": PGO_MIXED}[v.lower()]
+        if k == "linear_solver" and isinstance(v, str):
+            v = {"pcg": 0, "direct": 1, "auto": 2}[v.lower()]
         if k == "preconditioner" and isinstance(v, str):
             v = {"block_jacobi": 0, "jacobi": 0, "multigrid": 1, "amg": 1}[v.lower()]
         if not hasattr(o, k):

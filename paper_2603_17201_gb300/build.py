@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpgo_gb300.so")
-SOURCES = ["capi.cu", "kernels.cu", "pcg.cu", "amg.cu", "aux_kernels.cu", "adjoint.cu", "batch.cu", "noalloc.cu", "correction.cu", "matching.cu", "frames.cu"] + [
+SOURCES = ["capi.cu", "kernels.cu", "pcg.cu", "amg.cu", "aux_kernels.cu", "adjoint.cu", "batch.cu", "noalloc.cu", "correction.cu", "matching.cu", "frames.cu", "direct.cu"] + [
     f"batch_part{k}.cu" for k in range(8)]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]

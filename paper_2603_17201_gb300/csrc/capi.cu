@@ -144,6 +144,10 @@ struct pgo_graph {
   // multigrid hierarchy, analysed at the first solve that uses it
   AmgHost* amg = nullptr;
   bool amg_failed = false;
+  // direct block Cholesky structure, analysed at the first solve that asks for it
+  DirectHost* direct = nullptr;
+  bool direct_failed = false;
+  std::string direct_why;
   std::vector<int> h_inc_ptr, h_inc_code, h_inc_other;
 };
 
@@ -192,8 +196,17 @@ pgo_status check_options(const pgo_solve_options& o) {
   if (o.preconditioner != PGO_PRECOND_BLOCK_JACOBI && o.preconditioner != PGO_PRECOND_MULTIGRID)
     return fail(PGO_ERR_INVALID_ARG, "options: unknown preconditioner %d", o.preconditioner);
   if (o.multigrid_refresh < 1) return fail(PGO_ERR_INVALID_ARG, "options: multigrid_refresh must be >= 1");
+  if (o.linear_solver != PGO_SOLVER_PCG && o.linear_solver != PGO_SOLVER_DIRECT && o.linear_solver != PGO_SOLVER_AUTO)
+    return fail(PGO_ERR_INVALID_ARG, "options: unknown linear_solver %d", o.linear_solver);
   return PGO_OK;
 }
+
+// How one damped linear solve runs: the direct factorisation (dd) or PCG with
+// the multigrid hierarchy (amg) or block-Jacobi (both nullptr).
+struct LinSolve {
+  const AmgDev* amg = nullptr;
+  const DirectDev* dd = nullptr;
+};
 
 // The preconditioner set-up and the PCG launches of one linear solve at the
 // current linearisation (amg: multigrid hierarchy, nullptr: block-Jacobi).
@@ -211,31 +224,49 @@ void enqueue_precond(const DevGraph& g, int mixed, const AmgDev* amg, cudaStream
   }
 }
 
-// The linear-solve part of one LM iteration: the preconditioner (block-Jacobi
-// blocks, plus the multigrid hierarchy when enabled), then one persistent PCG
-// launch (FP64), or, in mixed precision, FP32 PCG launches inside FP64
-// iterative refinement (refine_steps passes, each skipped on the device once
-// the FP64 residual meets pcg_tol).
-void enqueue_linear_solve(const DevGraph& g, int mixed, int refine_steps, const AmgDev* amg, cudaStream_t s,
+// The linear-solve part of one LM iteration.  PCG: the preconditioner
+// (block-Jacobi blocks, plus the multigrid hierarchy when enabled), then one
+// persistent PCG launch (FP64), or, in mixed precision, FP32 PCG launches
+// inside FP64 iterative refinement (refine_steps passes, each skipped on the
+// device once the FP64 residual meets pcg_tol).  Direct: the block Cholesky
+// factorisation, then the triangular solves (in mixed precision one FP32
+// factorisation serves every refinement pass).
+void enqueue_linear_solve(const DevGraph& g, int mixed, int refine_steps, LinSolve ls, cudaStream_t s,
                           cudaError_t* err, int lm = 0) {
-  enqueue_precond(g, mixed, amg, s, err, lm);
+  auto keep = [&](cudaError_t e) {
+    if (e != cudaSuccess && *err == cudaSuccess) *err = e;
+  };
+  if (ls.dd) {
+    keep(launch_direct_factor(g, *ls.dd, mixed, s));
+    if (!mixed) {
+      keep(launch_direct_solve(g, *ls.dd, 0, 0, s));
+      return;
+    }
+    for (int pass = 0; pass < refine_steps; ++pass) {
+      launch_refine_residual(g, pass == 0, s);
+      keep(launch_direct_solve(g, *ls.dd, 1, 1, s));
+      launch_refine_accumulate(g, s);
+    }
+    return;
+  }
+  enqueue_precond(g, mixed, ls.amg, s, err, lm);
   if (!mixed) {
-    enqueue_pcg(g, 0, amg, 0, s, err);
+    enqueue_pcg(g, 0, ls.amg, 0, s, err);
     return;
   }
   for (int pass = 0; pass < refine_steps; ++pass) {
     launch_refine_residual(g, pass == 0, s);
-    enqueue_pcg(g, 1, amg, 1, s, err);
+    enqueue_pcg(g, 1, ls.amg, 1, s, err);
     launch_refine_accumulate(g, s);
   }
 }
 
 // One LM iteration (the body of the WHILE node, or one host-driven step).
-void enqueue_lm_body(const DevGraph& g, int mixed, int refine_steps, const AmgDev* amg, cudaStream_t s,
+void enqueue_lm_body(const DevGraph& g, int mixed, int refine_steps, LinSolve ls, cudaStream_t s,
                      unsigned long long lm_cond, cudaError_t* err) {
   launch_linearize(g, mixed, s);
   launch_assemble(g, mixed, s);
-  enqueue_linear_solve(g, mixed, refine_steps, amg, s, err, 1);
+  enqueue_linear_solve(g, mixed, refine_steps, ls, s, err, 1);
   launch_update(g, mixed, s);
   launch_cost(g, 1, s, lm_cond);
 }
@@ -264,7 +295,46 @@ pgo_status ensure_amg(pgo_graph* G, int precond) {
   return PGO_OK;
 }
 
-pgo_status build_solve_graph(pgo_graph* G, int mixed, int refine_steps, const AmgDev* amg, cudaGraphExec_t* out) {
+// The linear solver of a solve: analyses the direct structure (and the
+// multigrid hierarchy) the first time they are asked for.  DIRECT on a graph
+// that does not fit its limits is an error; AUTO falls back to PCG.
+pgo_status choose_solver(pgo_graph* G, const pgo_solve_options& o, LinSolve* ls) {
+  *ls = LinSolve{};
+  const int mixed = o.precision == PGO_MIXED;
+  if (o.linear_solver != PGO_SOLVER_PCG) {
+    const bool want = o.linear_solver == PGO_SOLVER_DIRECT || G->N <= PGO_DIRECT_CROSSOVER_VERTICES;
+    if (want && !G->direct && !G->direct_failed) {
+      const char* why = nullptr;
+      if (G->N < 2) {
+        G->direct_failed = true;
+        G->direct_why = "the graph has no free vertex";
+      } else {
+        G->direct = direct_build(G->N, G->fixed, G->h_inc_ptr.data(), G->h_inc_code.data(), G->h_inc_other.data(),
+                                 G->stream, &why);
+        if (!G->direct) {
+          G->direct_failed = true;
+          G->direct_why = why ? why : "unknown";
+        }
+      }
+    }
+    if (want && G->direct) {
+      const char* why = nullptr;
+      if (direct_fits(G->direct, mixed, &why)) {
+        ls->dd = direct_desc(G->direct);
+        return PGO_OK;
+      }
+      if (o.linear_solver == PGO_SOLVER_DIRECT) return fail(PGO_ERR_INVALID_ARG, "direct solver: %s", why);
+    } else if (o.linear_solver == PGO_SOLVER_DIRECT) {
+      return fail(PGO_ERR_INVALID_ARG, "direct solver: %s", G->direct_why.c_str());
+    }
+  }
+  pgo_status st = ensure_amg(G, o.preconditioner);
+  if (st != PGO_OK) return st;
+  ls->amg = amg_for(G, o.preconditioner);
+  return PGO_OK;
+}
+
+pgo_status build_solve_graph(pgo_graph* G, int mixed, int refine_steps, LinSolve ls, cudaGraphExec_t* out) {
   const DevGraph& g = G->g;
   cudaGraph_t graph;
   CUDA_TRY(cudaGraphCreate(&graph, 0));
@@ -279,7 +349,7 @@ pgo_status build_solve_graph(pgo_graph* G, int mixed, int refine_steps, const Am
   if (body) {
     GraphBuilder lb{G->cap_stream};
     cudaError_t le = cudaSuccess;
-    lb.capture(body, [&](cudaStream_t s) { enqueue_lm_body(g, mixed, refine_steps, amg, s, hl, &le); });
+    lb.capture(body, [&](cudaStream_t s) { enqueue_lm_body(g, mixed, refine_steps, ls, s, hl, &le); });
     if (lb.err != cudaSuccess) b.err = lb.err;
     if (le != cudaSuccess) b.err = le;
   }
@@ -295,7 +365,7 @@ pgo_status build_solve_graph(pgo_graph* G, int mixed, int refine_steps, const Am
 
 // A linear solve at a given lambda (pgo_graph_damped_step): linearise, then
 // the same linear-solve sequence as one LM iteration.
-pgo_status build_step_graph(pgo_graph* G, int mixed, int refine_steps, const AmgDev* amg, cudaGraphExec_t* out) {
+pgo_status build_step_graph(pgo_graph* G, int mixed, int refine_steps, LinSolve ls, cudaGraphExec_t* out) {
   const DevGraph& g = G->g;
   cudaGraph_t graph;
   CUDA_TRY(cudaGraphCreate(&graph, 0));
@@ -304,7 +374,7 @@ pgo_status build_step_graph(pgo_graph* G, int mixed, int refine_steps, const Amg
   b.capture(graph, [&](cudaStream_t s) {
     launch_linearize(g, mixed, s);
     launch_assemble(g, mixed, s);
-    enqueue_linear_solve(g, mixed, refine_steps, amg, s, &le);
+    enqueue_linear_solve(g, mixed, refine_steps, ls, s, &le);
   });
   if (le != cudaSuccess) b.err = le;
   if (b.err != cudaSuccess) {
@@ -319,7 +389,7 @@ pgo_status build_step_graph(pgo_graph* G, int mixed, int refine_steps, const Amg
 
 // Host-driven LM loop with plain stream launches (schedule 1): the same
 // kernels, for profilers that cannot look inside conditional graph nodes.
-pgo_status run_eager(pgo_graph* G, int mixed, int refine_steps, int max_iters, const AmgDev* amg) {
+pgo_status run_eager(pgo_graph* G, int mixed, int refine_steps, int max_iters, LinSolve ls) {
   const DevGraph& g = G->g;
   cudaStream_t s = G->stream;
   cudaError_t le = cudaSuccess;
@@ -329,7 +399,7 @@ pgo_status run_eager(pgo_graph* G, int mixed, int refine_steps, int max_iters, c
     CUDA_TRY(cudaMemcpyAsync(G->h_state, g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
     if (G->h_state->done || G->h_state->it >= max_iters) break;
-    enqueue_lm_body(g, mixed, refine_steps, amg, s, 0, &le);
+    enqueue_lm_body(g, mixed, refine_steps, ls, s, 0, &le);
     CUDA_TRY(le);
     CUDA_TRY(cudaGetLastError());
   }
@@ -337,7 +407,7 @@ pgo_status run_eager(pgo_graph* G, int mixed, int refine_steps, int max_iters, c
 }
 
 // Re-solve at the last linearisation: state reset, then the linear solve.
-pgo_status build_resolve_graph(pgo_graph* G, int mixed, int refine_steps, const AmgDev* amg, cudaGraphExec_t* out) {
+pgo_status build_resolve_graph(pgo_graph* G, int mixed, int refine_steps, LinSolve ls, cudaGraphExec_t* out) {
   const DevGraph& g = G->g;
   cudaGraph_t graph;
   CUDA_TRY(cudaGraphCreate(&graph, 0));
@@ -345,7 +415,7 @@ pgo_status build_resolve_graph(pgo_graph* G, int mixed, int refine_steps, const 
   cudaError_t le = cudaSuccess;
   b.capture(graph, [&](cudaStream_t s) {
     launch_resolve_reset(g, s);
-    enqueue_linear_solve(g, mixed, refine_steps, amg, s, &le);
+    enqueue_linear_solve(g, mixed, refine_steps, ls, s, &le);
   });
   if (le != cudaSuccess) b.err = le;
   if (b.err != cudaSuccess) {
@@ -358,18 +428,18 @@ pgo_status build_resolve_graph(pgo_graph* G, int mixed, int refine_steps, const 
   return PGO_OK;
 }
 
-pgo_status get_exec(pgo_graph* G, int kind, int mixed, int refine_steps, const AmgDev* amg, cudaGraphExec_t* out) {
-  const long long key = ((long long)kind << 32) | ((long long)(amg != nullptr) << 24) | ((long long)mixed << 16) |
-                        (mixed ? refine_steps : 0);
+pgo_status get_exec(pgo_graph* G, int kind, int mixed, int refine_steps, LinSolve ls, cudaGraphExec_t* out) {
+  const long long key = ((long long)kind << 32) | ((long long)(ls.dd != nullptr) << 25) |
+                        ((long long)(ls.amg != nullptr) << 24) | ((long long)mixed << 16) | (mixed ? refine_steps : 0);
   auto it = G->execs.find(key);
   if (it != G->execs.end()) {
     *out = it->second;
     return PGO_OK;
   }
   cudaGraphExec_t ex = nullptr;
-  pgo_status st = kind == 0   ? build_solve_graph(G, mixed, refine_steps, amg, &ex)
-                  : kind == 1 ? build_step_graph(G, mixed, refine_steps, amg, &ex)
-                              : build_resolve_graph(G, mixed, refine_steps, amg, &ex);
+  pgo_status st = kind == 0   ? build_solve_graph(G, mixed, refine_steps, ls, &ex)
+                  : kind == 1 ? build_step_graph(G, mixed, refine_steps, ls, &ex)
+                              : build_resolve_graph(G, mixed, refine_steps, ls, &ex);
   if (st != PGO_OK) return st;
   G->execs[key] = ex;
   *out = ex;
@@ -458,6 +528,7 @@ pgo_status pgo_default_options(pgo_solve_options* opt) {
   opt->schedule = -1;
   opt->preconditioner = PGO_PRECOND_MULTIGRID;
   opt->multigrid_refresh = 1;
+  opt->linear_solver = PGO_SOLVER_PCG;
   return PGO_OK;
 }
 
@@ -692,6 +763,7 @@ void pgo_graph_destroy(pgo_graph* G) {
   if (G->h_opt) cudaFreeHost(G->h_opt);
   if (G->arena.base) cudaFree(G->arena.base);
   amg_free(G->amg);
+  direct_free(G->direct);
   delete G;
 }
 
@@ -823,9 +895,10 @@ pgo_status pgo_graph_damped_step(pgo_graph* G, const pgo_solve_options* opt, dou
   if (st != PGO_OK) return st;
   const int mixed = o.precision == PGO_MIXED;
   cudaGraphExec_t ex;
-  st = ensure_amg(G, o.preconditioner);
+  LinSolve ls;
+  st = choose_solver(G, o, &ls);
   if (st != PGO_OK) return st;
-  st = get_exec(G, 1, mixed, o.refine_steps, amg_for(G, o.preconditioner), &ex);
+  st = get_exec(G, 1, mixed, o.refine_steps, ls, &ex);
   if (st != PGO_OK) return st;
   st = prepare_standalone(G, o, lambda);
   if (st != PGO_OK) return st;
@@ -912,9 +985,10 @@ pgo_status pgo_graph_resolve(pgo_graph* G, const pgo_solve_options* opt, double 
   if (st != PGO_OK) return st;
   const int mixed = o.precision == PGO_MIXED;
   cudaGraphExec_t ex;
-  st = ensure_amg(G, o.preconditioner);
+  LinSolve ls;
+  st = choose_solver(G, o, &ls);
   if (st != PGO_OK) return st;
-  st = get_exec(G, 2, mixed, o.refine_steps, amg_for(G, o.preconditioner), &ex);
+  st = get_exec(G, 2, mixed, o.refine_steps, ls, &ex);
   if (st != PGO_OK) return st;
   cudaStream_t s = G->stream;
   fill_dev_options(o, G->h_opt);
@@ -1020,10 +1094,11 @@ pgo_status pgo_solve(pgo_graph* G, const pgo_solve_options* opt, pgo_report* rep
   const int mixed = o.precision == PGO_MIXED;
   const bool eager = o.schedule == 1;
   cudaGraphExec_t ex = nullptr;
-  st = ensure_amg(G, o.preconditioner);
+  LinSolve ls;
+  st = choose_solver(G, o, &ls);
   if (st != PGO_OK) return st;
   if (!eager) {
-    st = get_exec(G, 0, mixed, o.refine_steps, amg_for(G, o.preconditioner), &ex);
+    st = get_exec(G, 0, mixed, o.refine_steps, ls, &ex);
     if (st != PGO_OK) return st;
   }
   cudaStream_t s = G->stream;
@@ -1031,7 +1106,7 @@ pgo_status pgo_solve(pgo_graph* G, const pgo_solve_options* opt, pgo_report* rep
   CUDA_TRY(cudaMemcpyAsync(G->g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
   CUDA_TRY(cudaEventRecord(G->ev0, s));
   if (eager) {
-    st = run_eager(G, mixed, o.refine_steps, o.max_iters, amg_for(G, o.preconditioner));
+    st = run_eager(G, mixed, o.refine_steps, o.max_iters, ls);
     if (st != PGO_OK) return st;
   } else {
     CUDA_TRY(cudaGraphLaunch(ex, s));

@@ -313,6 +313,29 @@ cudaError_t launch_project_match(const FramesDev& F, const MatchParams& mp, int 
                                  const unsigned char* matched, const PointsDev& pts, int* match, int* dist, int* fuse,
                                  cudaStream_t s);
 
+// ---- direct block Cholesky solve of the damped system (direct.cu) ----
+struct DirectDev {
+  int nb, ns, w;          // band vertices, separators, bandwidth (blocks)
+  int n_targets;          // assembled blocks
+  long long n_blocks;     // storage blocks (band nb (w+1), border ns nb, corner ns ns)
+  size_t border0, corner0;   // offsets (values) of the border and corner storage
+  const int* band_v;      // nb: vertex of each band position
+  const int* sep_v;       // ns: vertex of each separator
+  const int* r_ptr;       // n_targets + 1: recipe of each assembled block
+  const int* r_code;      // edge * 2 + transposed, or -(vertex + 1) for a damped diagonal block
+  const int* r_dst;       // n_targets: storage block of each target
+  float* s32;             // storage (49 values per block), FP32 and FP64
+  double* s64;
+};
+struct DirectHost;
+DirectHost* direct_build(int N, int fixed, const int* inc_ptr, const int* inc_code, const int* inc_other,
+                         cudaStream_t s, const char** why);
+void direct_free(DirectHost* h);
+const DirectDev* direct_desc(const DirectHost* h);
+bool direct_fits(const DirectHost* h, int mixed, const char** why);
+cudaError_t launch_direct_factor(const DevGraph& g, const DirectDev& D, int mixed, cudaStream_t s);
+cudaError_t launch_direct_solve(const DevGraph& g, const DirectDev& D, int mixed, int from_residual, cudaStream_t s);
+
 // Loop-correction steps around the optimisation (correction.cu).
 cudaError_t launch_propagate_correction(int n, const double* poses, int current, const double* corrected, int n_conn,
                                         const int* conn, double* out, int* bad, cudaStream_t s);
