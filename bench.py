@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--roofline-only", action="store_true",
                     help="only the roofline leg: linearise once, then the capped FP32 PCG re-solves "
                          "(an ncu capture of k_pcg should skip 2 launches: the third runs 9 iterations)")
+    ap.add_argument("--solver-sweep", action="store_true",
+                    help="only the direct-versus-PCG size sweep (one JSON line)")
     ap.add_argument("--profile-solve", action="store_true",
                     help="only one FP64 and one mixed solve of the workload with host-issued launches "
                          "(every kernel a launch of its own), for per-kernel ncu captures")
@@ -835,7 +837,12 @@ def main():
     if args.batch:
         run_batch(args)
         return
-    if args.profile_solve:
+    if args.solver_sweep:
+        import torch
+        torch.cuda.set_device(0)
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+        print(json.dumps({"solver_sweep": solver_sweep_leg(torch, flush)}), flush=True)
+    elif args.profile_solve:
         run_profile_solve(args)
     elif args.roofline_only:
         run_roofline_only(args)

@@ -114,9 +114,8 @@ __global__ void __launch_bounds__(1024, 1) k_direct_factor(DevGraph g, DirectDev
   V* win = reinterpret_cast<V*>(smem_raw);              // band ring: W1 rows x W1 blocks (offset o = row - col)
   V* bwin = win + (size_t)W1 * W1 * 49;                 // separator ring: ns rows x W1 columns (column c at c % W1)
   V* corner = bwin + (size_t)ns * W1 * 49;              // ns x ns blocks (lower)
-  V* piv = corner + (size_t)ns * ns * 49;               // L_kk^-1 (49)
   __shared__ int s_fail;
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   if (tid == 0) s_fail = 0;
   // initial window: band rows 0..w (their blocks with col >= 0), separator columns 0..w, D
   for (int r = 0; r < min(W1, nb); ++r)
@@ -130,76 +129,84 @@ __global__ void __launch_bounds__(1024, 1) k_direct_factor(DevGraph g, DirectDev
   }
   for (int t = tid; t < ns * ns * 49; t += nt) corner[t] = S[D.corner0 + t];
   __syncthreads();
+  // each thread's share of the row (and separator column) entering the window
+  const int pre_n = (W1 + ns) * 49;
+  constexpr int kPre = 2;   // (W1 + ns) * 49 <= 2 * 1024 for the size limits
   for (int k = 0; k < nb; ++k) {
     V* Akk = win + ((size_t)(k % W1) * W1 + 0) * 49;
-    // 1. Cholesky of the pivot block and its inverse (warp 0)
-    if (tid < 32) {
-      if (tid == 0) {
-        V L[7][7];
-        bool ok = true;
-        for (int j = 0; j < 7; ++j) {
-          const V a0 = Akk[j * 7 + j];
-          V d = a0;
-          for (int q = 0; q < j; ++q) d -= L[j][q] * L[j][q];
-          // single precision at a large condition number: a pivot lost to
-          // rounding is regularised (the FP64 refinement and the LM gain ratio
-          // absorb the error); in FP64 it is a numerical failure
-          if (!(d > V(0))) {
-            if (sizeof(V) == 8) ok = false;
-            d = fabs(a0) * V(1e-6) + V(1e-30);
-          }
-          d = sqrt(d);
-          L[j][j] = d;
-          for (int i = j + 1; i < 7; ++i) {
-            V s = Akk[i * 7 + j];
-            for (int q = 0; q < j; ++q) s -= L[i][q] * L[j][q];
-            L[i][j] = s / d;
-          }
-          for (int i = 0; i < j; ++i) L[i][j] = V(0);
+    const int rn = k + W1;   // enters the window in the slot of row k
+    // prefetch row rn and separator column rn (consumed after the update)
+    V pre[kPre];
+#pragma unroll
+    for (int u = 0; u < kPre; ++u) {
+      const int t = tid + u * nt;
+      pre[u] = V(0);
+      if (rn < nb && t < pre_n) {
+        if (t < W1 * 49) pre[u] = S[((size_t)rn * W1 + t / 49) * 49 + t % 49];
+        else {
+          const int q = t - W1 * 49;
+          pre[u] = S[D.border0 + ((size_t)(q / 49) * nb + rn) * 49 + q % 49];
         }
-        // inverse of the lower-triangular L by forward substitution
-        for (int c = 0; c < 7; ++c)
-          for (int r = 0; r < 7; ++r) {
-            if (r < c) { piv[r * 7 + c] = V(0); continue; }
-            V s = (r == c) ? V(1) : V(0);
-            for (int q = c; q < r; ++q) s -= L[r][q] * piv[q * 7 + c];
-            piv[r * 7 + c] = s / L[r][r];
-          }
-        for (int e = 0; e < 49; ++e) Akk[e] = L[e / 7][e % 7];
-        if (!ok) s_fail = 1;
       }
+    }
+    // 1. Cholesky of the pivot block on warp 0: lane i < 7 holds row i in registers
+    if (tid < 32) {
+      V a[7];
+#pragma unroll
+      for (int c = 0; c < 7; ++c) a[c] = lane < 7 ? Akk[lane * 7 + c] : V(0);
+      bool ok = true;
+#pragma unroll
+      for (int j = 0; j < 7; ++j) {
+        V d = __shfl_sync(0xffffffffu, a[j], j);
+        const V a0 = __shfl_sync(0xffffffffu, Akk[j * 7 + j], 0);
+        // single precision at a large condition number: a pivot lost to
+        // rounding is regularised (the FP64 refinement and the LM gain ratio
+        // absorb the error); in FP64 it is a numerical failure
+        if (!(d > V(0))) {
+          if (sizeof(V) == 8) ok = false;
+          d = fabs(a0) * V(1e-6) + V(1e-30);
+        }
+        const V ljj = sqrt(d);
+        if (lane == j) a[j] = ljj;
+        if (lane > j) a[j] = a[j] / ljj;
+#pragma unroll
+        for (int c = j + 1; c < 7; ++c) {
+          const V lcj = __shfl_sync(0xffffffffu, a[j], c);
+          if (lane >= c) a[c] -= a[j] * lcj;
+        }
+      }
+      if (lane < 7) {
+#pragma unroll
+        for (int c = 0; c < 7; ++c) Akk[lane * 7 + c] = c <= lane ? a[c] : V(0);
+      }
+      if (lane == 0 && !ok) s_fail = 1;
     }
     __syncthreads();
     if (s_fail) break;
-    // 2. panel: band rows k+1..k+w and every separator row, X <- X L_kk^-T
+    // 2. panel: every row of the band blocks (k+1..k+nr, k) and of the
+    // separators' blocks (s, k) solves x L_kk^T = a by forward substitution
+    // (one thread per row; it reads and writes only its own row); L_kk goes out
     const int nr = min(w, nb - 1 - k);
-    {
-      const int tasks = (nr + ns) * 49;
-      V vals[2];
-      int idx[2];
-      int cnt = 0;
-      // two passes so that every entry is read before any is written
-      for (int t = tid; t < tasks; t += nt) {
-        const int b = t / 49, e = t - 49 * b;
-        V* X = b < nr ? win + ((size_t)((k + 1 + b) % W1) * W1 + (b + 1)) * 49
-                      : bwin + ((size_t)(b - nr) * W1 + (k % W1)) * 49;
-        const V v = panel_entry(X, piv, e / 7, e % 7);
-        if (cnt < 2) { vals[cnt] = v; idx[cnt] = t; }
-        ++cnt;
+    for (int t = tid; t < (nr + ns) * 7; t += nt) {
+      const int b = t / 7, r = t - 7 * b;
+      V* X = (b < nr ? win + ((size_t)((k + 1 + b) % W1) * W1 + (b + 1)) * 49
+                     : bwin + ((size_t)(b - nr) * W1 + (k % W1)) * 49) + r * 7;
+      V x[7];
+#pragma unroll
+      for (int c = 0; c < 7; ++c) {
+        V v = X[c];
+#pragma unroll
+        for (int q = 0; q < c; ++q) v -= x[q] * Akk[c * 7 + q];
+        x[c] = v / Akk[c * 7 + c];
       }
-      __syncthreads();
-      cnt = 0;
-      for (int t = tid; t < tasks; t += nt) {
-        const int b = t / 49, e = t - 49 * b;
-        V* X = b < nr ? win + ((size_t)((k + 1 + b) % W1) * W1 + (b + 1)) * 49
-                      : bwin + ((size_t)(b - nr) * W1 + (k % W1)) * 49;
-        if (cnt < 2 && idx[cnt] == t) X[e] = vals[cnt];
-        ++cnt;
-      }
+#pragma unroll
+      for (int c = 0; c < 7; ++c) X[c] = x[c];
     }
+    for (int t = tid; t < 49; t += nt) S[((size_t)k * W1) * 49 + t] = Akk[t];
     __syncthreads();
     // 3. rank-7 updates: band A_ij -= L_ik L_jk^T (k < j <= i <= k+w), separator
-    // rows C_sj -= L_sk L_jk^T (k < j <= k+w), corner D_st -= L_sk L_tk^T (t <= s)
+    // rows C_sj -= L_sk L_jk^T (k < j <= k+w), corner D_st -= L_sk L_tk^T (t <= s);
+    // column k retires to global memory in the same phase (it is only read here)
     {
       const int nband = nr * (nr + 1) / 2, nsep = ns * nr, ncorner = ns * (ns + 1) / 2;
       const int tasks = (nband + nsep + ncorner) * 49;
@@ -237,30 +244,29 @@ __global__ void __launch_bounds__(1024, 1) k_direct_factor(DevGraph g, DirectDev
         for (int q = 0; q < 7; ++q) acc += Li[r * 7 + q] * Lj[c * 7 + q];
         Y[e] -= acc;
       }
-    }
-    __syncthreads();
-    // 4. retire column k (band rows k..k+nr and the separators' column k) to
-    // global memory, then bring in band row k+w+1 and separator column k+w+1
-    for (int t = tid; t < (nr + 1) * 49; t += nt) {
-      const int b = t / 49, i = k + b;
-      S[((size_t)i * W1 + b) * 49 + t % 49] = win[((size_t)(i % W1) * W1 + b) * 49 + t % 49];
-    }
-    for (int t = tid; t < ns * 49; t += nt) {
-      const int s = t / 49;
-      S[D.border0 + ((size_t)s * nb + k) * 49 + t % 49] = bwin[((size_t)s * W1 + (k % W1)) * 49 + t % 49];
-    }
-    __syncthreads();
-    const int rn = k + W1;   // enters the window in the slot of row k
-    if (rn < nb)
-      for (int t = tid; t < W1 * 49; t += nt) {
-        const int o = t / 49;   // column rn - o >= k + 1 for o <= w
-        win[((size_t)(rn % W1) * W1 + o) * 49 + t % 49] = S[((size_t)rn * W1 + o) * 49 + t % 49];
+      for (int t = tid; t < nr * 49; t += nt) {
+        const int b = t / 49 + 1, i = k + b;
+        S[((size_t)i * W1 + b) * 49 + t % 49] = win[((size_t)(i % W1) * W1 + b) * 49 + t % 49];
       }
-    if (rn < nb)
       for (int t = tid; t < ns * 49; t += nt) {
         const int s = t / 49;
-        bwin[((size_t)s * W1 + (rn % W1)) * 49 + t % 49] = S[D.border0 + ((size_t)s * nb + rn) * 49 + t % 49];
+        S[D.border0 + ((size_t)s * nb + k) * 49 + t % 49] = bwin[((size_t)s * W1 + (k % W1)) * 49 + t % 49];
       }
+    }
+    __syncthreads();
+    // 4. the prefetched row and separator column take the slot of row k
+    if (rn < nb) {
+#pragma unroll
+      for (int u = 0; u < kPre; ++u) {
+        const int t = tid + u * nt;
+        if (t >= pre_n) continue;
+        if (t < W1 * 49) win[((size_t)(rn % W1) * W1 + t / 49) * 49 + t % 49] = pre[u];
+        else {
+          const int q = t - W1 * 49;
+          bwin[((size_t)(q / 49) * W1 + (rn % W1)) * 49 + q % 49] = pre[u];
+        }
+      }
+    }
     __syncthreads();
   }
   // 5. dense Cholesky of the updated corner (7 ns x 7 ns, lower), column by column
@@ -296,19 +302,50 @@ __global__ void __launch_bounds__(1024, 1) k_direct_factor(DevGraph g, DirectDev
 
 // ---- forward and backward substitution -------------------------------------------
 // rhs: -b (from_residual = 0) or the FP64 refinement residual; x = (H + lambda I)^-1 rhs
-// in the graph's vertex order (fixed vertex 0).  One thread block; the band
-// sweeps run on one warp (lane l < 7 owns component l of the current row).
+// in the graph's vertex order (fixed vertex 0).  One thread block of 512.  The
+// band sweeps are sequential: warp 0 carries them (lane l < 7 owns component l
+// of the current row) while warps 1..15 stage the factor blocks each row needs
+// into a ring of shared-memory slots ahead of it (a row's blocks (r, r - o)
+// forward, a column's blocks (r + o, r) backward).  A slot holds sweep index i
+// when ring_row[slot] == i; warp 0 publishes how many indices it has consumed.
+// Every wait is bounded; a wait that runs out reports a numerical failure.
+constexpr int kSolveThreads = 512;
+constexpr long long kSpinLimit = 1ll << 26;
+
 template <class V>
-__global__ void __launch_bounds__(512, 1) k_direct_solve(DevGraph g, DirectDev D, int from_residual) {
-  const SolverState* st = g.st;
+__device__ __forceinline__ void stage_slot(const V* S, V* slot, int r, int nb, int W1, int forward, int lane) {
+  for (int t = lane; t < W1 * 49; t += 32) {
+    const int o = t / 49;
+    V v = V(0);
+    if (forward) {
+      if (o <= r) v = S[((size_t)r * W1 + o) * 49 + t % 49];          // block (r, r - o)
+    } else {
+      if (r + o < nb) v = S[((size_t)(r + o) * W1 + o) * 49 + t % 49];  // block (r + o, r)
+    }
+    slot[t] = v;
+  }
+}
+
+template <class V>
+__global__ void __launch_bounds__(kSolveThreads, 1) k_direct_solve(DevGraph g, DirectDev D, int from_residual,
+                                                                   int ring) {
+  SolverState* st = g.st;
   if (st->done || (from_residual && st->ref_done)) return;
   const int nb = D.nb, w = D.w, ns = D.ns, W1 = D.w + 1, m = 7 * ns;
   const V* S = DV<V>::store(D);
   V* x = DV<V>::x(g);
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  V* y = reinterpret_cast<V*>(smem_raw);   // band values, 7 per band row (nb * 7)
-  V* ys = y + (size_t)nb * 7;             // separator values (m)
-  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
+  V* slots = reinterpret_cast<V*>(smem_raw);         // ring x W1 x 49
+  V* y = slots + (size_t)ring * W1 * 49;             // band values, 7 per band row (nb * 7)
+  V* ys = y + (size_t)nb * 7;                        // separator values (m)
+  __shared__ int ring_row[32];
+  __shared__ int consumed, s_fail;
+  const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
+  if (tid < 32) ring_row[tid] = -1;
+  if (tid == 0) {
+    consumed = 0;
+    s_fail = 0;
+  }
   // gather the right-hand side in the factor's order
   for (int t = tid; t < (nb + ns) * 7; t += nt) {
     const int r = t / 7, a = t % 7;
@@ -317,105 +354,143 @@ __global__ void __launch_bounds__(512, 1) k_direct_solve(DevGraph g, DirectDev D
     y[t] = V(rv);
   }
   __syncthreads();
-  // forward: band rows in order, y_r = L_rr^-1 (y_r - sum_{o=1..w} L_{r,r-o} y_{r-o})
-  if (tid < 32) {
-    for (int r = 0; r < nb; ++r) {
-      V acc = V(0);
-      if (lane < 7)
-        for (int o = 1; o <= min(w, r); ++o) {
-          const V* L = S + ((size_t)r * W1 + o) * 49 + lane * 7;
-          const V* yy = y + (size_t)(r - o) * 7;
-#pragma unroll
-          for (int q = 0; q < 7; ++q) acc += L[q] * yy[q];
+  for (int pass = 0; pass < 2; ++pass) {
+    const int forward = pass == 0;
+    if (warp > 0) {
+      // producers: warp p stages sweep indices p - 1, p - 1 + (nwarps - 1), ...
+      for (int i = warp - 1; i < nb; i += nwarps - 1) {
+        long long spins = 0;
+        while (*(volatile int*)&consumed <= i - ring && !*(volatile int*)&s_fail && ++spins < kSpinLimit) {
         }
-      V val = lane < 7 ? y[(size_t)r * 7 + lane] - acc : V(0);
-      const V* Lrr = S + ((size_t)r * W1) * 49;
-      // triangular solve of the 7x7 pivot, row by row
-#pragma unroll
-      for (int a = 0; a < 7; ++a) {
-        const V ya = __shfl_sync(0xffffffffu, val, a) / Lrr[a * 7 + a];
-        if (lane == a) val = ya;
-        if (lane > a && lane < 7) val -= Lrr[lane * 7 + a] * ya;
-      }
-      if (lane < 7) y[(size_t)r * 7 + lane] = val;
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  // separators: ys -= L_C y_B, one warp per separator row (lanes over the
-  // band columns, then a shuffle reduction), then the dense forward and
-  // backward solves with L_D on warp 0 (lanes over the row's entries)
-  {
-    const int warp = tid >> 5, nwarps = nt >> 5;
-    for (int R = warp; R < m; R += nwarps) {
-      const int sR = R / 7, a = R % 7;
-      V acc = V(0);
-      for (int t = lane; t < nb * 7; t += 32) {
-        const int c = t / 7, q = t % 7;
-        acc += S[D.border0 + ((size_t)sR * nb + c) * 49 + a * 7 + q] * y[t];
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) ys[R] -= acc;
-    }
-  }
-  __syncthreads();
-  auto LD = [&](int R, int C) -> V { return S[D.corner0 + ((size_t)(R / 7) * ns + C / 7) * 49 + (R % 7) * 7 + C % 7]; };
-  if (tid < 32) {
-    for (int R = 0; R < m; ++R) {
-      V acc = V(0);
-      for (int C = lane; C < R; C += 32) acc += LD(R, C) * ys[C];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) ys[R] = (ys[R] - acc) / LD(R, R);
-      __syncwarp();
-    }
-    for (int R = m - 1; R >= 0; --R) {
-      V acc = V(0);
-      for (int C = R + 1 + lane; C < m; C += 32) acc += LD(C, R) * ys[C];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-      if (lane == 0) ys[R] = (ys[R] - acc) / LD(R, R);
-      __syncwarp();
-    }
-  }
-  __syncthreads();
-  // backward: band rows y_B -= L_C^T x_S (columns in parallel), then in reverse order
-  // x_r = L_rr^-T (y_r - sum_{o=1..w} L_{r+o,r}^T x_{r+o})
-  for (int t = tid; t < nb * 7; t += nt) {
-    const int c = t / 7, a = t % 7;
-    V acc = V(0);
-    for (int s = 0; s < ns; ++s) {
-      const V* L = S + D.border0 + ((size_t)s * nb + c) * 49;
-#pragma unroll
-      for (int q = 0; q < 7; ++q) acc += L[q * 7 + a] * ys[s * 7 + q];
-    }
-    y[t] -= acc;
-  }
-  __syncthreads();
-  if (tid < 32) {
-    for (int r = nb - 1; r >= 0; --r) {
-      V acc = V(0);
-      if (lane < 7)
-        for (int o = 1; o <= min(w, nb - 1 - r); ++o) {
-          const V* L = S + ((size_t)(r + o) * W1 + o) * 49;   // block (r+o, r)
-          const V* xx = y + (size_t)(r + o) * 7;
-#pragma unroll
-          for (int q = 0; q < 7; ++q) acc += L[q * 7 + lane] * xx[q];
+        if (spins >= kSpinLimit || *(volatile int*)&s_fail) {
+          if (lane == 0) s_fail = 1;
+          break;
         }
-      V val = lane < 7 ? y[(size_t)r * 7 + lane] - acc : V(0);
-      const V* Lrr = S + ((size_t)r * W1) * 49;
-#pragma unroll
-      for (int a = 6; a >= 0; --a) {
-        const V xa = __shfl_sync(0xffffffffu, val, a) / Lrr[a * 7 + a];
-        if (lane == a) val = xa;
-        if (lane < a) val -= Lrr[a * 7 + lane] * xa;
+        const int r = forward ? i : nb - 1 - i;
+        stage_slot<V>(S, slots + (size_t)(i % ring) * W1 * 49, r, nb, W1, forward, lane);
+        __syncwarp();
+        __threadfence_block();
+        if (lane == 0) *(volatile int*)&ring_row[i % ring] = i;
+        if (*(volatile int*)&s_fail) break;
       }
-      if (lane < 7) y[(size_t)r * 7 + lane] = val;
-      __syncwarp();
+    } else {
+      for (int i = 0; i < nb; ++i) {
+        long long spins = 0;
+        while (*(volatile int*)&ring_row[i % ring] != i && !*(volatile int*)&s_fail && ++spins < kSpinLimit) {
+        }
+        if (spins >= kSpinLimit || *(volatile int*)&s_fail) {
+          if (lane == 0) s_fail = 1;
+          break;
+        }
+        __threadfence_block();
+        const V* sl = slots + (size_t)(i % ring) * W1 * 49;
+        const int r = forward ? i : nb - 1 - i;
+        V acc = V(0);
+        if (forward) {
+          // y_r = L_rr^-1 (y_r - sum_o L_{r,r-o} y_{r-o})
+          if (lane < 7)
+            for (int o = 1; o <= min(w, r); ++o) {
+              const V* L = sl + (size_t)o * 49 + lane * 7;
+              const V* yy = y + (size_t)(r - o) * 7;
+#pragma unroll
+              for (int q = 0; q < 7; ++q) acc += L[q] * yy[q];
+            }
+          V val = lane < 7 ? y[(size_t)r * 7 + lane] - acc : V(0);
+#pragma unroll
+          for (int a = 0; a < 7; ++a) {
+            const V ya = __shfl_sync(0xffffffffu, val, a) / sl[a * 7 + a];
+            if (lane == a) val = ya;
+            if (lane > a && lane < 7) val -= sl[lane * 7 + a] * ya;
+          }
+          if (lane < 7) y[(size_t)r * 7 + lane] = val;
+        } else {
+          // x_r = L_rr^-T (y_r - sum_o L_{r+o,r}^T x_{r+o})
+          if (lane < 7)
+            for (int o = 1; o <= min(w, nb - 1 - r); ++o) {
+              const V* L = sl + (size_t)o * 49;
+              const V* xx = y + (size_t)(r + o) * 7;
+#pragma unroll
+              for (int q = 0; q < 7; ++q) acc += L[q * 7 + lane] * xx[q];
+            }
+          V val = lane < 7 ? y[(size_t)r * 7 + lane] - acc : V(0);
+#pragma unroll
+          for (int a = 6; a >= 0; --a) {
+            const V xa = __shfl_sync(0xffffffffu, val, a) / sl[a * 7 + a];
+            if (lane == a) val = xa;
+            if (lane < a) val -= sl[a * 7 + lane] * xa;
+          }
+          if (lane < 7) y[(size_t)r * 7 + lane] = val;
+        }
+        __syncwarp();
+        __threadfence_block();
+        if (lane == 0) *(volatile int*)&consumed = i + 1;
+        if (*(volatile int*)&s_fail) break;
+      }
+    }
+    __syncthreads();
+    if (s_fail) break;
+    if (tid < 32) ring_row[tid] = -1;
+    if (tid == 0) consumed = 0;
+    if (forward) {
+      // separators: ys -= L_C y_B, one warp per separator row (lanes over the
+      // band columns, then a shuffle reduction), then the dense forward and
+      // backward solves with L_D on warp 0 (lanes over the row's entries)
+      for (int R = warp; R < m; R += nwarps) {
+        const int sR = R / 7, a = R % 7;
+        V acc = V(0);
+        for (int t = lane; t < nb * 7; t += 32) {
+          const int c = t / 7, q = t % 7;
+          acc += S[D.border0 + ((size_t)sR * nb + c) * 49 + a * 7 + q] * y[t];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) ys[R] -= acc;
+      }
+      __syncthreads();
+      auto LD = [&](int R, int C) -> V {
+        return S[D.corner0 + ((size_t)(R / 7) * ns + C / 7) * 49 + (R % 7) * 7 + C % 7];
+      };
+      if (tid < 32) {
+        for (int R = 0; R < m; ++R) {
+          V acc = V(0);
+          for (int C = lane; C < R; C += 32) acc += LD(R, C) * ys[C];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (lane == 0) ys[R] = (ys[R] - acc) / LD(R, R);
+          __syncwarp();
+        }
+        for (int R = m - 1; R >= 0; --R) {
+          V acc = V(0);
+          for (int C = R + 1 + lane; C < m; C += 32) acc += LD(C, R) * ys[C];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (lane == 0) ys[R] = (ys[R] - acc) / LD(R, R);
+          __syncwarp();
+        }
+      }
+      __syncthreads();
+      // y_B -= L_C^T x_S (band columns in parallel)
+      for (int t = tid; t < nb * 7; t += nt) {
+        const int c = t / 7, a = t % 7;
+        V acc = V(0);
+        for (int s2 = 0; s2 < ns; ++s2) {
+          const V* L = S + D.border0 + ((size_t)s2 * nb + c) * 49;
+#pragma unroll
+          for (int q = 0; q < 7; ++q) acc += L[q * 7 + a] * ys[s2 * 7 + q];
+        }
+        y[t] -= acc;
+      }
+      __syncthreads();
     }
   }
-  __syncthreads();
+  if (s_fail) {
+    if (tid == 0) {
+      st->status = PGO_ERR_NUMERICAL;
+      st->stop_reason = 4;
+      st->done = 1;
+    }
+    return;
+  }
   // scatter to the vertex order; the fixed vertex stays 0
   for (int t = tid; t < g.N * VEC; t += nt) x[t] = V(0);
   __syncthreads();
@@ -428,10 +503,14 @@ __global__ void __launch_bounds__(512, 1) k_direct_solve(DevGraph g, DirectDev D
 
 size_t factor_smem(int w, int ns, size_t vbytes) {
   const size_t W1 = (size_t)w + 1;
-  return (W1 * W1 + (size_t)ns * W1 + (size_t)ns * ns + 1) * 49 * vbytes;
+  return (W1 * W1 + (size_t)ns * W1 + (size_t)ns * ns) * 49 * vbytes;
 }
 
-size_t solve_smem(int nb, int ns, size_t vbytes) { return ((size_t)nb * 7 + 7 * (size_t)ns) * vbytes; }
+int solve_ring(size_t vbytes) { return vbytes == 4 ? 16 : 8; }
+
+size_t solve_smem(int nb, int ns, int w, size_t vbytes) {
+  return ((size_t)solve_ring(vbytes) * (w + 1) * 49 + (size_t)nb * 7 + 7 * (size_t)ns) * vbytes;
+}
 
 int smem_optin() {
   static int v = 0;
@@ -597,7 +676,7 @@ bool direct_fits(const DirectHost* H, int mixed, const char** why) {
     *why = "the band window and separator rows exceed shared memory";
     return false;
   }
-  if (solve_smem(D.nb, D.ns, vb) + 1024 > (size_t)smem_optin()) {
+  if (solve_smem(D.nb, D.ns, D.w, vb) + 1024 > (size_t)smem_optin()) {
     *why = "the band vector exceeds shared memory";
     return false;
   }
@@ -628,16 +707,17 @@ cudaError_t launch_direct_factor(const DevGraph& g, const DirectDev& D, int mixe
 
 cudaError_t launch_direct_solve(const DevGraph& g, const DirectDev& D, int mixed, int from_residual, cudaStream_t s) {
   const size_t vb = mixed ? sizeof(float) : sizeof(double);
-  const size_t smem = solve_smem(D.nb, D.ns, vb);
+  const size_t smem = solve_smem(D.nb, D.ns, D.w, vb);
+  const int ring = solve_ring(vb);
   cudaError_t e;
   if (mixed) {
     e = cudaFuncSetAttribute(k_direct_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_direct_solve<float><<<1, 512, smem, s>>>(g, D, from_residual);
+    k_direct_solve<float><<<1, kSolveThreads, smem, s>>>(g, D, from_residual, ring);
   } else {
     e = cudaFuncSetAttribute(k_direct_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_direct_solve<double><<<1, 512, smem, s>>>(g, D, from_residual);
+    k_direct_solve<double><<<1, kSolveThreads, smem, s>>>(g, D, from_residual, ring);
   }
   return cudaGetLastError();
 }
