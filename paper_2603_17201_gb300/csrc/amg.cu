@@ -414,6 +414,7 @@ void layout(Uploader& U, std::vector<HostLevel>& H, int L, int N, const std::vec
     D.h32 = U.take<float>(nd * D.nL * BLK32);
   }
   D.rho = U.take<double>((size_t)nseg * (AMG_MAXL + 1));
+  D.rho_next = U.take<double>((size_t)nseg * (AMG_MAXL + 1));
   for (int k = 0; k < 2; ++k) {
     D.pw64[k] = U.take<double>((size_t)N * VEC);
     D.pw32[k] = U.take<float>((size_t)N * VEC);
@@ -710,45 +711,38 @@ __device__ __forceinline__ void coarsest_dense(const AmgLevel& Lc, W* dense) {
   __syncthreads();
 }
 
-// In-place Gauss-Jordan inverse of the SPD n7 x n7 matrix in shared memory
-// (no pivoting), one pass per column: column k and row k saved first, the
-// pivot's reciprocal formed once (thread 0), element (i, j) to thread
-// (i mod rows, j mod 64) of the block seen as rows x 64.  Returns false on a
-// non-positive or non-finite pivot.  colk, rowk: n7 entries each.
+// Gauss-Jordan inverse of the SPD n7 x n7 matrix in shared memory (no
+// pivoting), double-buffered: step k reads buffer k % 2 and writes the other,
+// every thread forms the pivot's reciprocal itself, so a step is one block
+// barrier (the matrix's row and column k are read from the previous buffer
+// while the new one is written).  Element (i, j) goes to thread
+// (i mod rows, j mod 64) of the block seen as rows x 64.  The inverse ends in
+// the buffer returned (dense or dense + n7 * n7); nullptr on a non-positive or
+// non-finite pivot.
 template <class W>
-__device__ bool gauss_jordan_spd(W* dense, int n7, W* colk, W* rowk) {
-  __shared__ int bad;
-  __shared__ W s_ip;
+__device__ W* gauss_jordan_spd(W* dense, int n7) {
   const int j0 = threadIdx.x & 63, i0 = threadIdx.x >> 6, istep = blockDim.x >> 6;
-  bool ok = true;
+  W* in = dense;
+  W* out = dense + (size_t)n7 * n7;
   for (int k = 0; k < n7; ++k) {
-    if (threadIdx.x == 0) {
-      const W piv = dense[k * n7 + k];
-      const bool okp = piv > W(0) && isfinite(piv);
-      bad = okp ? 0 : 1;
-      s_ip = okp ? W(1) / piv : W(0);
-    }
-    for (int i = threadIdx.x; i < n7; i += blockDim.x) {
-      colk[i] = dense[i * n7 + k];
-      rowk[i] = dense[k * n7 + i];
-    }
-    __syncthreads();
-    if (bad) {   // uniform: every thread reads the same flag
-      ok = false;
-      break;
-    }
-    const W ip = s_ip;
-    for (int i = i0; i < n7; i += istep)
+    const W piv = in[k * n7 + k];
+    if (!(piv > W(0) && isfinite(piv))) return nullptr;   // uniform: every thread reads the same value
+    const W ip = W(1) / piv;
+    for (int i = i0; i < n7; i += istep) {
+      const W cik = in[i * n7 + k];
       for (int j = j0; j < n7; j += 64) {
         W o;
-        if (i == k) o = (j == k) ? ip : rowk[j] * ip;
-        else o = (j == k) ? -colk[i] * ip : dense[i * n7 + j] - colk[i] * (rowk[j] * ip);
-        dense[i * n7 + j] = o;
+        if (i == k) o = (j == k) ? ip : in[k * n7 + j] * ip;
+        else o = (j == k) ? -cik * ip : in[i * n7 + j] - cik * (in[k * n7 + j] * ip);
+        out[i * n7 + j] = o;
       }
+    }
     __syncthreads();
+    W* t = in;
+    in = out;
+    out = t;
   }
-  __syncthreads();
-  return ok;
+  return in;
 }
 
 // C^-1 of the coarsest level into AV<V>::cinv (symmetrised; zero and the
@@ -757,14 +751,16 @@ __device__ void coarsest_inverse_f64(const AmgDev& A, double* dense) {
   const AmgLevel& Lc = A.lv[A.L];
   const int nL = Lc.n, n7 = 7 * nL;
   coarsest_dense<double, double>(Lc, dense);
-  const bool ok = gauss_jordan_spd<double>(dense, n7, dense + (size_t)n7 * n7, dense + (size_t)n7 * n7 + n7);
+  const double* inv = gauss_jordan_spd<double>(dense, n7);
+  const bool ok = inv != nullptr;
+  if (!ok) inv = dense;
   double* Ci = AV<double>::cinv(A);
   for (int t = threadIdx.x; t < nL * nL * 49; t += blockDim.x) {
     const int cd = t / 49, ij = t - 49 * cd;
     const int c = cd / nL, d = cd - nL * c;
     const int i = ij / 7, j = ij - 7 * (ij / 7);
     const int R = 7 * c + i, C = 7 * d + j;
-    Ci[(size_t)cd * BLK64 + ij] = ok ? 0.5 * (dense[R * n7 + C] + dense[C * n7 + R]) : 0.0;
+    Ci[(size_t)cd * BLK64 + ij] = ok ? 0.5 * (inv[R * n7 + C] + inv[C * n7 + R]) : 0.0;
   }
   if (threadIdx.x == 0 && !ok) *A.flag = 1;
 }
@@ -779,9 +775,7 @@ __device__ void coarsest_inverse_f32(const AmgDev& A, float* dense) {
   const AmgLevel& Lc = A.lv[A.L];
   const int nL = Lc.n, n7 = 7 * nL;
   coarsest_dense<float, float>(Lc, dense);
-  float* colk = dense + (size_t)n7 * n7;
-  float* rowk = colk + n7;
-  float* sc = rowk + n7;
+  float* sc = dense + 2 * (size_t)n7 * n7;
   for (int i = threadIdx.x; i < n7; i += blockDim.x) {
     const float d = dense[i * n7 + i];
     sc[i] = d > 0.f && isfinite(d) ? rsqrtf(d) : 1.f;
@@ -792,14 +786,16 @@ __device__ void coarsest_inverse_f32(const AmgDev& A, float* dense) {
     dense[t] *= sc[i] * sc[j];
   }
   __syncthreads();
-  const bool ok = gauss_jordan_spd<float>(dense, n7, colk, rowk);
+  const float* inv = gauss_jordan_spd<float>(dense, n7);
+  const bool ok = inv != nullptr;
+  if (!ok) inv = dense;
   float* Ci = AV<float>::cinv(A);
   for (int t = threadIdx.x; t < nL * nL * 49; t += blockDim.x) {
     const int cd = t / 49, ij = t - 49 * cd;
     const int c = cd / nL, d = cd - nL * c;
     const int i = ij / 7, j = ij - 7 * (ij / 7);
     const int R = 7 * c + i, C = 7 * d + j;
-    Ci[(size_t)cd * BLK32 + ij] = ok ? 0.5f * (dense[R * n7 + C] + dense[C * n7 + R]) * sc[R] * sc[C] : 0.f;
+    Ci[(size_t)cd * BLK32 + ij] = ok ? 0.5f * (inv[R * n7 + C] + inv[C * n7 + R]) * sc[R] * sc[C] : 0.f;
   }
   if (threadIdx.x == 0 && !ok) *A.flag = 1;
 }
@@ -884,14 +880,31 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
   for (int l = 0; l < (lagged ? 1 : A.L); ++l) {
     const AmgLevel& Lv = A.lv[l];
     const AmgLevel& Ln = A.lv[l + 1];
-    // ---- rho(D^-1 A) by power iteration ----
+    // ---- rho(D^-1 A) ----
+    // A warm set-up takes the estimate the previous set-up refined (H, lambda
+    // and the poses change little between linearisations; never below the rho
+    // of the previous hierarchy) and refines it for the next one with three
+    // power steps that ride along with the P, A P and P^T A P phases below, so
+    // they add no grid barrier.  The first set-up of a graph (and a lagged
+    // one) runs its power iteration in phases of its own.
     double rho;
-    {
-      // start from the vector the previous set-up of this graph ended with
-      // (H, lambda and the poses change little between linearisations),
+    const bool fuse = warm && !lagged;
+    V* pv = AV<V>::pv(Lv);
+    if (fuse) {
+      const double rho_prev = __ldcg(A.rho + l), rho_est = __ldcg(A.rho_next + l);
+      rho = rho_prev;
+      if (rho_est > rho && isfinite(rho_est)) rho = rho_est;
+      if (!(rho > 1e-30) || !isfinite(rho)) rho = 1.0;
+      // (A.rho[l] is written in the A P phase, after every block has read it)
+      if (threadIdx.x == 0) {
+        rho_f[0] = 4.0 / (3.0 * rho);
+        rho_f[1] = 1.0 / rho;
+      }
+      __syncthreads();
+    } else {
+      // start from the vector the previous set-up of this graph ended with,
       // else from a fixed smooth vector
       V* x0 = AV<V>::pw(A, 0);
-      V* pv = AV<V>::pv(Lv);
       const double rho_prev = __ldcg(A.rho + l);   // written after the barriers below
       double nrm = 0.0;
       for (int t = gtid; t < Lv.n * VEC; t += gthreads) {
@@ -919,7 +932,10 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
       // a few warm iterations approach rho from below; never go under the
       // previous estimate (an underestimate weakens the smoother's damping)
       if (warm && rho_prev > rho && isfinite(rho_prev)) rho = rho_prev;
-      if (gtid == 0) A.rho[l] = rho;
+      if (gtid == 0) {
+        A.rho[l] = rho;
+        A.rho_next[l] = rho;
+      }
       // the smoother's factors, divided once per block
       if (threadIdx.x == 0) {
         rho_f[0] = 4.0 / (3.0 * rho);
@@ -930,6 +946,10 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
       for (int t = gtid; t < Lv.n * VEC; t += gthreads) pv[t] = __ldcg(yl + t);
     }
     // ---- P = T_agg - 4/(3 rho) D^-1 (A T) ----
+    if (fuse) {   // power step 1: y1 = D^-1 A pv
+      const double ny2 = power_step<V>(g, Lv, l, lam, pv, V(1), AV<V>::pw(A, 0));
+      block_partial(ny2, partial);
+    }
     {
       const double f = rho_f[0];
       const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
@@ -963,6 +983,12 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
     if (!grid_sync(counter, abort_flag, target)) goto timeout;
     // ---- AP = A P; single-graph hierarchies also Q = P - D^-1 (A P) / rho,
     // from the team's AP block in shared memory (a 64-thread barrier per team) ----
+    if (fuse) {   // power step 2: y2 = D^-1 A y1 / |y1|; every block has read A.rho[l]
+      const double2 nn = grid_norm_after_sync(partial);
+      const double ny2 = power_step<V>(g, Lv, l, lam, AV<V>::pw(A, 0), V(nn.y), AV<V>::pw(A, 1));
+      block_partial(ny2, partial + gridDim.x);
+      if (gtid == 0) A.rho[l] = rho;
+    }
     {
       const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
       const int i = t / 7, j = t - 7 * (t / 7);
@@ -1002,6 +1028,11 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
     if (!grid_sync(counter, abort_flag, target)) goto timeout;
     if (lagged) break;   // the coarse levels of the last complete set-up stay
     // ---- A_next = P^T (A P), upper blocks ----
+    if (fuse) {   // power step 3: y3 = D^-1 A y2 / |y2|
+      const double2 nn = grid_norm_after_sync(partial + gridDim.x);
+      const double ny2 = power_step<V>(g, Lv, l, lam, AV<V>::pw(A, 1), V(nn.y), AV<V>::pw(A, 0));
+      block_partial(ny2, partial);
+    }
     {
       const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
       const int i = t / 7, j = t - 7 * (t / 7);
@@ -1016,6 +1047,12 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
       }
     }
     if (!grid_sync(counter, abort_flag, target)) goto timeout;
+    if (fuse) {   // the refined estimate |y3| and the vector for the next set-up
+      const double2 nn = grid_norm_after_sync(partial);
+      if (gtid == 0 && nn.x > 1e-30 && isfinite(nn.x)) A.rho_next[l] = nn.x;
+      const V* y3 = AV<V>::pw(A, 0);
+      for (int t = gtid; t < Lv.n * VEC; t += gthreads) pv[t] = __ldcg(y3 + t);
+    }
     // ---- mirror the lower blocks, and the next level's D^-1 in the same
     // phase (it reads only diagonal blocks, which the products wrote; the
     // mirror writes only lower blocks) ----
@@ -1115,7 +1152,8 @@ static int amg_sms() {
 cudaError_t launch_amg_setup(const DevGraph& g, const AmgDev& amg, int mixed, int lm, cudaStream_t s) {
   const int blocks = amg_sms();
   const size_t n7 = (size_t)7 * amg.nL;
-  const size_t smem = (n7 * n7 + 2 * n7) * sizeof(double);
+  // block 0: the coarsest operator twice (double-buffered elimination) and a scale vector
+  const size_t smem = (2 * n7 * n7 + n7) * sizeof(double);
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(blocks);
   cfg.blockDim = dim3(mixed ? SetupShape<float>::THREADS : SetupShape<double>::THREADS);

@@ -104,8 +104,10 @@ __device__ __forceinline__ V panel_entry(const V* X, const V* Li, int r, int c) 
   return s;
 }
 
+constexpr int kFactorThreads = 256;
+
 template <class V>
-__global__ void __launch_bounds__(1024, 1) k_direct_factor(DevGraph g, DirectDev D) {
+__global__ void __launch_bounds__(kFactorThreads, 1) k_direct_factor(DevGraph g, DirectDev D) {
   SolverState* st = g.st;
   if (st->done) return;
   const int nb = D.nb, w = D.w, ns = D.ns, W1 = D.w + 1;
@@ -115,6 +117,7 @@ __global__ void __launch_bounds__(1024, 1) k_direct_factor(DevGraph g, DirectDev
   V* bwin = win + (size_t)W1 * W1 * 49;                 // separator ring: ns rows x W1 columns (column c at c % W1)
   V* corner = bwin + (size_t)ns * W1 * 49;              // ns x ns blocks (lower)
   __shared__ int s_fail;
+  __shared__ V s_rdiag[7];   // 1 / L_kk[a][a] of the current pivot
   const int tid = threadIdx.x, nt = blockDim.x, lane = tid & 31;
   if (tid == 0) s_fail = 0;
   // initial window: band rows 0..w (their blocks with col >= 0), separator columns 0..w, D
@@ -131,7 +134,7 @@ __global__ void __launch_bounds__(1024, 1) k_direct_factor(DevGraph g, DirectDev
   __syncthreads();
   // each thread's share of the row (and separator column) entering the window
   const int pre_n = (W1 + ns) * 49;
-  constexpr int kPre = 2;   // (W1 + ns) * 49 <= 2 * 1024 for the size limits
+  constexpr int kPre = 8;   // (W1 + ns) * 49 <= 8 * 256 for the size limits
   for (int k = 0; k < nb; ++k) {
     V* Akk = win + ((size_t)(k % W1) * W1 + 0) * 49;
     const int rn = k + W1;   // enters the window in the slot of row k
@@ -178,6 +181,11 @@ __global__ void __launch_bounds__(1024, 1) k_direct_factor(DevGraph g, DirectDev
       if (lane < 7) {
 #pragma unroll
         for (int c = 0; c < 7; ++c) Akk[lane * 7 + c] = c <= lane ? a[c] : V(0);
+        V dl = a[0];
+#pragma unroll
+        for (int c = 1; c < 7; ++c)
+          if (c == lane) dl = a[c];
+        s_rdiag[lane] = V(1) / dl;
       }
       if (lane == 0 && !ok) s_fail = 1;
     }
@@ -197,21 +205,23 @@ __global__ void __launch_bounds__(1024, 1) k_direct_factor(DevGraph g, DirectDev
         V v = X[c];
 #pragma unroll
         for (int q = 0; q < c; ++q) v -= x[q] * Akk[c * 7 + q];
-        x[c] = v / Akk[c * 7 + c];
+        x[c] = v * s_rdiag[c];
       }
 #pragma unroll
       for (int c = 0; c < 7; ++c) X[c] = x[c];
     }
-    for (int t = tid; t < 49; t += nt) S[((size_t)k * W1) * 49 + t] = Akk[t];
+    // the stored pivot block keeps the reciprocals on its diagonal (the solves multiply)
+    for (int t = tid; t < 49; t += nt)
+      S[((size_t)k * W1) * 49 + t] = (t % 8 == 0) ? s_rdiag[t / 8] : Akk[t];
     __syncthreads();
     // 3. rank-7 updates: band A_ij -= L_ik L_jk^T (k < j <= i <= k+w), separator
     // rows C_sj -= L_sk L_jk^T (k < j <= k+w), corner D_st -= L_sk L_tk^T (t <= s);
     // column k retires to global memory in the same phase (it is only read here)
     {
       const int nband = nr * (nr + 1) / 2, nsep = ns * nr, ncorner = ns * (ns + 1) / 2;
-      const int tasks = (nband + nsep + ncorner) * 49;
-      for (int t = tid; t < tasks; t += nt) {
-        const int b = t / 49, e = t - 49 * b, r = e / 7, c = e % 7;
+      const int tasks = nband + nsep + ncorner;
+      // one output block per thread: L_j in registers, then row by row of L_i
+      for (int b = tid; b < tasks; b += nt) {
         const V *Li, *Lj;
         V* Y;
         if (b < nband) {
@@ -239,10 +249,22 @@ __global__ void __launch_bounds__(1024, 1) k_direct_factor(DevGraph g, DirectDev
           Lj = bwin + ((size_t)u * W1 + (k % W1)) * 49;
           Y = corner + ((size_t)s * ns + u) * 49;
         }
-        V acc = V(0);
+        V lj[49];
 #pragma unroll
-        for (int q = 0; q < 7; ++q) acc += Li[r * 7 + q] * Lj[c * 7 + q];
-        Y[e] -= acc;
+        for (int e = 0; e < 49; ++e) lj[e] = Lj[e];
+#pragma unroll
+        for (int r = 0; r < 7; ++r) {
+          V li[7];
+#pragma unroll
+          for (int q = 0; q < 7; ++q) li[q] = Li[r * 7 + q];
+#pragma unroll
+          for (int c = 0; c < 7; ++c) {
+            V acc = V(0);
+#pragma unroll
+            for (int q = 0; q < 7; ++q) acc += li[q] * lj[c * 7 + q];
+            Y[r * 7 + c] -= acc;
+          }
+        }
       }
       for (int t = tid; t < nr * 49; t += nt) {
         const int b = t / 49 + 1, i = k + b;
@@ -398,7 +420,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_direct_solve(DevGraph g, D
           V val = lane < 7 ? y[(size_t)r * 7 + lane] - acc : V(0);
 #pragma unroll
           for (int a = 0; a < 7; ++a) {
-            const V ya = __shfl_sync(0xffffffffu, val, a) / sl[a * 7 + a];
+            const V ya = __shfl_sync(0xffffffffu, val, a) * sl[a * 7 + a];
             if (lane == a) val = ya;
             if (lane > a && lane < 7) val -= sl[lane * 7 + a] * ya;
           }
@@ -415,7 +437,7 @@ __global__ void __launch_bounds__(kSolveThreads, 1) k_direct_solve(DevGraph g, D
           V val = lane < 7 ? y[(size_t)r * 7 + lane] - acc : V(0);
 #pragma unroll
           for (int a = 6; a >= 0; --a) {
-            const V xa = __shfl_sync(0xffffffffu, val, a) / sl[a * 7 + a];
+            const V xa = __shfl_sync(0xffffffffu, val, a) * sl[a * 7 + a];
             if (lane == a) val = xa;
             if (lane < a) val -= sl[a * 7 + lane] * xa;
           }
@@ -695,12 +717,12 @@ cudaError_t launch_direct_factor(const DevGraph& g, const DirectDev& D, int mixe
     k_direct_assemble<float><<<blocks, 256, 0, s>>>(g, D);
     e = cudaFuncSetAttribute(k_direct_factor<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_direct_factor<float><<<1, 1024, smem, s>>>(g, D);
+    k_direct_factor<float><<<1, kFactorThreads, smem, s>>>(g, D);
   } else {
     k_direct_assemble<double><<<blocks, 256, 0, s>>>(g, D);
     e = cudaFuncSetAttribute(k_direct_factor<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    k_direct_factor<double><<<1, 1024, smem, s>>>(g, D);
+    k_direct_factor<double><<<1, kFactorThreads, smem, s>>>(g, D);
   }
   return cudaGetLastError();
 }

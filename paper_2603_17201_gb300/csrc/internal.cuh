@@ -139,7 +139,8 @@ struct AmgDev {
   float* w32;
   double* h64;
   float* h32;
-  double* rho;            // per segment and level: estimate of rho(D^-1 A)
+  double* rho;            // per segment and level: the rho(D^-1 A) the hierarchy was built with
+  double* rho_next;       // single graph, per level: the estimate refined during the last set-up
   double* pw64[2];        // power-iteration vectors
   float* pw32[2];
   int* flag;              // per segment, nonzero: the coarsest factorisation failed
