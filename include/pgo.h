@@ -137,9 +137,13 @@ typedef struct {
  * limits (pgo_solve, pgo_graph_damped_step, pgo_graph_resolve only; the
  * adjoint, the Newton polish and the batched form use PCG).  AUTO: DIRECT
  * when the graph fits and has at most PGO_DIRECT_CROSSOVER_VERTICES
- * vertices, PCG otherwise (the crossover measured on GB300). */
+ * vertices, PCG otherwise.  The crossover is the size below which DIRECT was
+ * measured faster on GB300: on figure-8 graphs of 100 to 2,000 keyframes the
+ * multigrid PCG was faster at every size (the sequential factorisation pays
+ * a few microseconds of latency per keyframe), so it is 0 and AUTO selects
+ * PCG. */
 typedef enum { PGO_SOLVER_PCG = 0, PGO_SOLVER_DIRECT = 1, PGO_SOLVER_AUTO = 2 } pgo_linear_solver;
-#define PGO_DIRECT_CROSSOVER_VERTICES 600
+#define PGO_DIRECT_CROSSOVER_VERTICES 0
 
 /* Solve report. */
 typedef struct {

@@ -25,10 +25,19 @@ with it, as after ORB-SLAM-style loop correction), loop measurements from the
 ground truth; optional i.i.d. measurement noise of the same form perturbs every
 edge.
 
+Also built here: the inputs of the loop-correction steps around the
+optimisation (the keyframe that closed the loop, its Sim(3) correction, its
+connected keyframes and map points in front of every keyframe;
+``make_loop_correction``), and keyframes with ORB-like features for the
+projection search and loop fusion (a 752 x 480 camera, random 256-bit
+descriptors, features at the projections of the map points plus clutter;
+``make_match_workload``).
+
 This module holds problem construction only (quaternion products to compose
-poses).  It contains none of the solver's arithmetic: no exp/log maps, no
-residuals, no Jacobians, no normal equations.  Randomness comes only from
-``numpy.random.Generator(PCG64(seed))``.
+poses, a pinhole projection to place features).  It contains none of the
+method's arithmetic: no exp/log maps, residuals, Jacobians or normal
+equations, no loop correction, no search or matching.  Randomness comes only
+from ``numpy.random.Generator(PCG64(seed))``.
 """
 from __future__ import annotations
 
