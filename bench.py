@@ -333,8 +333,15 @@ def setup_leg(pg, N, E, stream, flush, torch, reps=7):
 
 
 def run_profile_solve(args):
+    """One host-scheduled FP64 and one mixed solve of the workload (every
+    kernel of the solve a launch of its own), then one call of each other
+    kernel family: the loop-correction steps (150 map points per keyframe),
+    the projection search PS3a-c and loop fusion (4,000 map points), a
+    direct-solver solve of the 200-keyframe circle and the stateless cost."""
+    import numpy as np
     import torch
-    from paper_2603_17201_gb300 import PoseGraph
+    from paper_2603_17201_gb300 import (Frames, PoseGraph, correct_points, evaluate_cost, match_params,
+                                        propagate_correction)
     from paper_2603_17201_gb300 import synthetic as syn
     torch.cuda.set_device(0)
     g = syn.make_config(args.workload)
@@ -344,6 +351,23 @@ def run_profile_solve(args):
         print(json.dumps({"precision": precision, "final_cost": rep["final_cost"], "iterations": rep["iterations"],
                           "pcg_iterations": rep["pcg_iterations"]}), flush=True)
         pg.close()
+    lc = syn.make_loop_correction(g, points_per_kf=150, seed=1)
+    out = propagate_correction(g.poses_init, lc.current, lc.corrected, lc.connected)
+    correct_points(g.poses_init, out, lc.points, lc.ref)
+    for mode, K, th in (("search", 3, 10.0), ("fusion", 30, 4.0)):
+        w = syn.make_match_workload(mode, n_kf=K, n_points=4000, seed=7)
+        fr = Frames.from_workload(w)
+        fr.match_workload(w, mode, th=th)
+        torch.cuda.synchronize()
+        fr.close()
+    c1 = syn.make_config("c1_circle200")
+    pd = PoseGraph.from_synthetic(c1)
+    rep = pd.solve(max_iters=MAX_ITERS, precision="mixed", linear_solver="direct", schedule=SCHED["eager"])
+    t = lambda a, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(a), dtype=dt, device="cuda")  # noqa: E731
+    evaluate_cost(g.n_vertices, t(g.edge_i, torch.int32), t(g.edge_j, torch.int32), t(g.meas), None,
+                  t(g.poses_init))
+    torch.cuda.synchronize()
+    print(json.dumps({"direct_c1_mixed_final_cost": rep["final_cost"]}), flush=True)
 
 
 def run_roofline_only(args):

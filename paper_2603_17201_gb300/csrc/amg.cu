@@ -771,6 +771,52 @@ __device__ void coarsest_inverse_f64(const AmgDev& A, double* dense) {
 // 0.2 ms on one SM; the scaling keeps the FP32 elimination's error at the
 // scaled matrix's condition number, and the operator itself comes from FP32
 // products.
+// Inverse of one SPD 7x7 block by Gauss-Jordan on a warp: lane r < 7 holds
+// row r of [B | I] in registers, the pivot row goes round by shuffles.
+// Returns false on a non-positive or non-finite pivot (every lane).
+__device__ __forceinline__ bool inv7_warp(const float* B, float* out) {
+  const int lane = threadIdx.x & 31;
+  float a[7], e[7];
+#pragma unroll
+  for (int c = 0; c < 7; ++c) {
+    a[c] = lane < 7 ? B[lane * 7 + c] : 0.f;
+    e[c] = (lane == c) ? 1.f : 0.f;
+  }
+  bool ok = true;
+#pragma unroll
+  for (int p = 0; p < 7; ++p) {
+    float pa[7], pe[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      pa[c] = __shfl_sync(0xffffffffu, a[c], p);
+      pe[c] = __shfl_sync(0xffffffffu, e[c], p);
+    }
+    const float piv = pa[p];
+    ok = ok && piv > 0.f && isfinite(piv);
+    const float ip = piv > 0.f ? 1.f / piv : 0.f;
+    const float f = (lane == p) ? 0.f : a[p];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      if (lane == p) {
+        a[c] *= ip;
+        e[c] *= ip;
+      } else {
+        a[c] -= f * (pa[c] * ip);
+        e[c] -= f * (pe[c] * ip);
+      }
+    }
+  }
+  if (lane < 7)
+#pragma unroll
+    for (int c = 0; c < 7; ++c) out[lane * 7 + c] = e[c];
+  return ok;
+}
+
+// C^-1 of the coarsest level for the FP32 set-up, on the Jacobi-scaled
+// operator S C S (unit diagonal): Gauss-Jordan over 7x7 blocks, nL steps of
+// three block barriers each -- the pivot block's inverse on warp 0, the
+// scaled pivot row R = P M_k* with the pivot column saved, then every block
+// M_ij -= M_ik R_j (the pivot column -M_ik P, the pivot row R).
 __device__ void coarsest_inverse_f32(const AmgDev& A, float* dense) {
   const AmgLevel& Lc = A.lv[A.L];
   const int nL = Lc.n, n7 = 7 * nL;
@@ -786,16 +832,67 @@ __device__ void coarsest_inverse_f32(const AmgDev& A, float* dense) {
     dense[t] *= sc[i] * sc[j];
   }
   __syncthreads();
-  const float* inv = gauss_jordan_spd<float>(dense, n7);
-  const bool ok = inv != nullptr;
-  if (!ok) inv = dense;
+  float* M = dense;
+  float* R = dense + (size_t)n7 * n7;   // 7 x n7: the scaled pivot row
+  float* Cc = R + 7 * (size_t)n7;       // n7 x 7: the pivot column before the step
+  float* Pv = Cc + 7 * (size_t)n7;      // 7 x 7: the pivot block's inverse
+  __shared__ int s_bad;
+  if (threadIdx.x == 0) s_bad = 0;
+  __syncthreads();
+  for (int kb = 0; kb < nL; ++kb) {
+    const int k7 = 7 * kb;
+    if (threadIdx.x < 32) {
+      // gather the pivot block into Pv first (rows of M are n7 apart)
+      if (threadIdx.x < 7)
+#pragma unroll
+        for (int c = 0; c < 7; ++c) Pv[threadIdx.x * 7 + c] = M[(size_t)(k7 + threadIdx.x) * n7 + k7 + c];
+      __syncwarp();
+      const bool ok = inv7_warp(Pv, Pv);
+      if (threadIdx.x == 0 && !ok) s_bad = 1;
+    }
+    __syncthreads();
+    if (s_bad) break;   // uniform
+    for (int t = threadIdx.x; t < 7 * n7; t += blockDim.x) {
+      const int a = t / n7, J = t - n7 * a;
+      float v;
+      if (J >= k7 && J < k7 + 7) {
+        v = Pv[a * 7 + (J - k7)];
+      } else {
+        v = 0.f;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) v += Pv[a * 7 + q] * M[(size_t)(k7 + q) * n7 + J];
+      }
+      R[t] = v;
+      const int I = t / 7, q = t - 7 * I;   // the same 7 n7 entries as the pivot column
+      Cc[t] = M[(size_t)I * n7 + k7 + q];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n7 * n7; t += blockDim.x) {
+      const int I = t / n7, J = t - n7 * I;
+      float v;
+      if (I >= k7 && I < k7 + 7) {
+        v = R[(I - k7) * n7 + J];
+      } else if (J >= k7 && J < k7 + 7) {
+        v = 0.f;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) v -= Cc[I * 7 + q] * Pv[q * 7 + (J - k7)];
+      } else {
+        v = M[t];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) v -= Cc[I * 7 + q] * R[q * n7 + J];
+      }
+      M[t] = v;
+    }
+    __syncthreads();
+  }
+  const bool ok = !s_bad;
   float* Ci = AV<float>::cinv(A);
   for (int t = threadIdx.x; t < nL * nL * 49; t += blockDim.x) {
     const int cd = t / 49, ij = t - 49 * cd;
     const int c = cd / nL, d = cd - nL * c;
     const int i = ij / 7, j = ij - 7 * (ij / 7);
-    const int R = 7 * c + i, C = 7 * d + j;
-    Ci[(size_t)cd * BLK32 + ij] = ok ? 0.5f * (inv[R * n7 + C] + inv[C * n7 + R]) * sc[R] * sc[C] : 0.f;
+    const int Rr = 7 * c + i, C = 7 * d + j;
+    Ci[(size_t)cd * BLK32 + ij] = ok ? 0.5f * (M[Rr * n7 + C] + M[C * n7 + Rr]) * sc[Rr] * sc[C] : 0.f;
   }
   if (threadIdx.x == 0 && !ok) *A.flag = 1;
 }

@@ -199,11 +199,14 @@ __global__ void k_resolve_reset(DevGraph g) {
 
 void launch_resolve_reset(const DevGraph& g, cudaStream_t s) { k_resolve_reset<<<1, 1, 0, s>>>(g); }
 
+// The edge and vertex kernels below are latency chains of FP64 arithmetic
+// (log and exp maps) over a few thousand items: small thread blocks spread
+// them over every SM instead of a few.
 void launch_cost(const DevGraph& g, int mode, cudaStream_t s, unsigned long long lm_cond) {
-  int blocks = (g.E + 255) / 256;
+  int blocks = (g.E + 127) / 128;
   if (blocks > g.partial_cap) blocks = g.partial_cap;
   if (blocks < 1) blocks = 1;
-  k_cost<<<blocks, 256, 0, s>>>(g, mode, lm_cond);
+  k_cost<<<blocks, 128, 0, s>>>(g, mode, lm_cond);
 }
 
 void launch_linearize(const DevGraph& g, int mixed, cudaStream_t s) {
@@ -213,13 +216,13 @@ void launch_linearize(const DevGraph& g, int mixed, cudaStream_t s) {
 }
 
 void launch_assemble(const DevGraph& g, int mixed, cudaStream_t s) {
-  int blocks = (g.N * 8 + 255) / 256;
-  k_assemble<<<blocks, 256, 0, s>>>(g, mixed, 0);
+  int blocks = (g.N * 8 + 127) / 128;
+  k_assemble<<<blocks, 128, 0, s>>>(g, mixed, 0);
 }
 
 void launch_assemble_mode(const DevGraph& g, int mode, cudaStream_t s) {
-  int blocks = (g.N * 8 + 255) / 256;
-  k_assemble<<<blocks, 256, 0, s>>>(g, 0, mode);
+  int blocks = (g.N * 8 + 127) / 128;
+  k_assemble<<<blocks, 128, 0, s>>>(g, 0, mode);
 }
 
 // 0: standalone step at opt->lambda_fixed; 1: swap the current pose buffer.
@@ -251,7 +254,7 @@ void launch_scale_x(const DevGraph& g, double f, cudaStream_t s) {
 }
 
 void launch_update(const DevGraph& g, int mixed, cudaStream_t s) {
-  k_update<<<(g.N + 255) / 256, 256, 0, s>>>(g, mixed);
+  k_update<<<(g.N + 31) / 32, 32, 0, s>>>(g, mixed);
 }
 
 void launch_lm_reset(const DevGraph& g, cudaStream_t s) { k_lm_reset<<<1, 1, 0, s>>>(g); }

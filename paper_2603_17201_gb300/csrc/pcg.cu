@@ -1105,7 +1105,7 @@ cudaError_t launch_pcg(const DevGraph& g, int mixed, int from_residual, const Am
 }
 
 void launch_refine_residual(const DevGraph& g, int first, cudaStream_t s) {
-  k_refine_residual<<<(g.N * 8 + 255) / 256, 256, 0, s>>>(g, first);
+  k_refine_residual<<<(g.N * 8 + 127) / 128, 128, 0, s>>>(g, first);
 }
 
 void launch_refine_accumulate(const DevGraph& g, cudaStream_t s) {
