@@ -34,10 +34,12 @@ SCHED = {"graph": -1, "eager": 1}
 MAX_ITERS = 20
 METRIC = "Sim(3) PGO ms/solve & edges/s at rel cost <=1e-6: mixed vs plain FP64, one GB300"
 UNIT = "edges/s"
-# DRAM bytes (read + write) of one PCG iteration of the roofline kernel from an
-# ncu capture of `bench.py --roofline-only`; None whenever the kernel has
-# changed since the counters were taken.
-TRAFFIC_PER_ITERATION = None
+# DRAM bytes (read + write) of one PCG iteration of the roofline kernel,
+# k_pcg<float,float,32> on the bench graph: one ncu capture of the 9-iteration
+# launch of `bench.py --roofline-only` read 21,229,568 B and wrote 19,712 B
+# (profiles/k_pcg_float_c2_figure8_2k.md), amortised over its 9 iterations.
+# Set to None whenever the kernel changes until it is captured again.
+TRAFFIC_PER_ITERATION = (21229568 + 19712) / 9
 
 
 def parse():

@@ -897,11 +897,22 @@ __device__ void coarsest_inverse_f32(const AmgDev& A, float* dense) {
   if (threadIdx.x == 0 && !ok) *A.flag = 1;
 }
 
-// ---- FP32 block products, one thread per output block ----------------------
-// acc (7x7 in registers) += op(A) X for 16-byte-aligned padded blocks: A is
-// streamed four entries at a time with vector loads (through the
-// non-coherent cache when NC, i.e. written by an earlier launch, else from
-// L2), X is held whole in registers; op(A) = A, or A^T when TR.
+// The FP32 products run eight lanes per output block where a phase has at
+// least kRowLanesMin output blocks; below that the 64-thread teams (one
+// output entry per thread) are faster: all their blocks fit in one pass of
+// the grid, and a team's term costs 7 FMA where a lane's costs 49.
+constexpr int kRowLanesMin = 4096;
+template <class V>
+__device__ __forceinline__ bool row_lanes(int n_out) {
+  return sizeof(V) == 4 && n_out >= kRowLanesMin;
+}
+
+// ---- FP32 block products, one lane per output row --------------------------
+// Eight lanes take one 7x7 output block (lane r < 7 its row r, lane 7 idle),
+// four blocks per warp.  Per recipe term a lane holds the whole right operand
+// block in registers (sixteen-byte loads, the same addresses on the block's
+// lanes) and streams its row of the left operand, so a term costs 20 loads
+// and 49 FMA per lane.
 template <bool NC>
 __device__ __forceinline__ float4 ld4(const float* p) {
   return NC ? __ldg(reinterpret_cast<const float4*>(p)) : __ldcg(reinterpret_cast<const float4*>(p));
@@ -919,94 +930,76 @@ __device__ __forceinline__ void ld_x52(const float* p, float (&X)[52]) {
   }
 }
 
-template <bool NC, bool TR, int N>
-__device__ __forceinline__ void mac_block(const float* A, const float (&X)[N], float (&acc)[49]) {
-  static_assert(N >= 49, "a 7x7 block");
+template <bool NC>
+__device__ __forceinline__ float ld1(const float* p) {
+  return NC ? __ldg(p) : __ldcg(p);
+}
+
+// acc[j] += sum_k op(A)[r][k] X[k][j]; op(A) = A, or A^T when TR
+template <bool NC, bool TR>
+__device__ __forceinline__ void mac_row(const float* A, int r, const float (&X)[52], float (&acc)[7]) {
 #pragma unroll
-  for (int ch = 0; ch < 13; ++ch) {
-    const float4 v = ld4<NC>(A + 4 * ch);
-    const float av[4] = {v.x, v.y, v.z, v.w};
+  for (int k = 0; k < 7; ++k) {
+    const float a = ld1<NC>(A + (TR ? k * 7 + r : r * 7 + k));
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      const int e = 4 * ch + m;
-      if (e < 49) {
-        const int r = e / 7, c = e % 7;
-#pragma unroll
-        for (int j = 0; j < 7; ++j) {
-          if (TR) acc[c * 7 + j] += av[m] * X[r * 7 + j];
-          else acc[r * 7 + j] += av[m] * X[c * 7 + j];
-        }
-      }
-    }
+    for (int j = 0; j < 7; ++j) acc[j] += a * X[k * 7 + j];
   }
 }
 
-// acc = sum over the recipe terms (a, x) of op(A_a) X_x, with A the level's
-// operator: at level 0 a < 0 is the damped diagonal block of vertex -a - 1
-// and a >= 0 the stored off-diagonal block a >> 1 (transposed if a & 1); at
-// the coarser levels a indexes the level's own (full-row) blocks.
-__device__ __forceinline__ void recipe_blocks_f32(const DevGraph& g, const AmgLevel& Lv, int l, float lam,
-                                                  const int2* rec, int e0, int e1, const float* X0,
-                                                  float (&acc)[49]) {
+// row r of the sum over the recipe terms (a, x) of op(A_a) X_x, with A the
+// level's operator: at level 0 a < 0 is the damped diagonal block of vertex
+// -a - 1 and a >= 0 the stored off-diagonal block a >> 1 (transposed if
+// a & 1); at the coarser levels a indexes the level's own (full-row) blocks.
+__device__ __forceinline__ void recipe_row_f32(const DevGraph& g, const AmgLevel& Lv, int l, float lam,
+                                               const int2* rec, int e0, int e1, const float* X0, int r,
+                                               float (&acc)[7]) {
   for (int e = e0; e < e1; ++e) {
     const int2 t = __ldg(rec + e);
+    const float* Xp = X0 + (size_t)t.y * BLK32;
     float X[52];
-    ld_x52<false>(X0 + (size_t)t.y * BLK32, X);
+    ld_x52<false>(Xp, X);
     if (l == 0) {
       if (t.x < 0) {
-        mac_block<true, false>(g.diag32 + (size_t)(-t.x - 1) * BLK32, X, acc);
+        mac_row<true, false>(g.diag32 + (size_t)(-t.x - 1) * BLK32, r, X, acc);
 #pragma unroll
-        for (int q = 0; q < 49; ++q) acc[q] += lam * X[q];
+        for (int j = 0; j < 7; ++j) acc[j] += lam * ld1<false>(Xp + r * 7 + j);
       } else if (t.x & 1) {
-        mac_block<true, true>(g.off32 + (size_t)(t.x >> 1) * BLK32, X, acc);
+        mac_row<true, true>(g.off32 + (size_t)(t.x >> 1) * BLK32, r, X, acc);
       } else {
-        mac_block<true, false>(g.off32 + (size_t)(t.x >> 1) * BLK32, X, acc);
+        mac_row<true, false>(g.off32 + (size_t)(t.x >> 1) * BLK32, r, X, acc);
       }
     } else {
-      mac_block<false, false>(Lv.a32 + (size_t)t.x * BLK32, X, acc);
+      mac_row<false, false>(Lv.a32 + (size_t)t.x * BLK32, r, X, acc);
     }
   }
 }
 
-// dst = v (a padded block, 16-byte stores, zero padding)
-__device__ __forceinline__ void st_block(float* dst, const float (&v)[49]) {
-  float4* d4 = reinterpret_cast<float4*>(dst);
-#pragma unroll
-  for (int ch = 0; ch < 13; ++ch) {
-    float w[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) w[m] = (4 * ch + m < 49) ? v[4 * ch + m] : 0.f;
-    d4[ch] = make_float4(w[0], w[1], w[2], w[3]);
-  }
-}
-
-// dst = Y - f M acc (M streamed, Y a block written by this launch, or zero)
+// row r of Y - f M B, with B's rows held by the eight lanes of this block
+// (row k in lane base + k) and M a block in memory; Y: a block or nullptr.
 template <bool NC>
-__device__ __forceinline__ void st_smoothed(float* dst, const float* M, const float (&acc)[49], const float* Y,
-                                            float f) {
-  float out[49];
+__device__ __forceinline__ void smooth_row(const float* M, const float* Y, float f, int r, int base,
+                                           const float (&b)[7], float (&out)[7]) {
+  float s[7];
 #pragma unroll
-  for (int q = 0; q < 49; ++q) out[q] = 0.f;
-  mac_block<NC, false>(M, acc, out);
-  float4* d4 = reinterpret_cast<float4*>(dst);
+  for (int j = 0; j < 7; ++j) s[j] = 0.f;
 #pragma unroll
-  for (int ch = 0; ch < 13; ++ch) {
-    const float4 y = Y ? ld4<false>(Y + 4 * ch) : make_float4(0.f, 0.f, 0.f, 0.f);
-    const float yv[4] = {y.x, y.y, y.z, y.w};
-    float w[4];
+  for (int k = 0; k < 7; ++k) {
+    const float m = M ? ld1<NC>(M + r * 7 + k) : 0.f;
 #pragma unroll
-    for (int m = 0; m < 4; ++m) w[m] = (4 * ch + m < 49) ? yv[m] - f * out[4 * ch + m] : 0.f;
-    d4[ch] = make_float4(w[0], w[1], w[2], w[3]);
+    for (int j = 0; j < 7; ++j) s[j] += m * __shfl_sync(0xffffffffu, b[j], base + k);
   }
+#pragma unroll
+  for (int j = 0; j < 7; ++j) out[j] = (Y ? ld1<false>(Y + r * 7 + j) : 0.f) - f * s[j];
 }
 
-// Block shape of the set-up: 256 threads, 64-thread teams for the per-node
-// D^-1 inverses and the FP64 products (one 7x7 output block per team); the
-// FP32 products take one output block per thread, with its accumulators and
-// one operand block in registers (252 registers, no spills at 256 threads).
+// Block shape of the set-up: 64-thread teams (one 7x7 output block each)
+// for the per-node D^-1 inverses and the FP64 products, eight lanes per
+// output block for the FP32 products.  FP32 runs 8 teams per block (more
+// loads in flight per SM); FP64 runs 4, which leaves it the registers of its
+// unrolled products.
 template <class V>
 struct SetupShape {
-  static constexpr int THREADS = 256;
+  static constexpr int THREADS = sizeof(V) == 4 ? 512 : 256;
   static constexpr int TEAMS = THREADS / 64;
 };
 
@@ -1151,20 +1144,32 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
       const double ny2 = power_step<V>(g, Lv, l, lam, pv, V(1), AV<V>::pw(A, 0));
       block_partial(ny2, partial);
     }
-    if constexpr (sizeof(V) == 4) {
-      // FP32: one thread per P block (the 7x7 products in registers)
-      const float f = (float)rho_f[0];
-      const float* Tb = Lv.t32;
-      float* Pb = Lv.p32;
-      for (int b = gtid; b < Lv.nnz_p; b += gthreads) {
-        const int u = __ldg(Lv.p_row + b), c = __ldg(Lv.p_col + b);
-        float acc[49];
+    if (row_lanes<V>(Lv.nnz_p)) {
+      if constexpr (sizeof(V) == 4) {
+        // FP32: eight lanes per P block, lane r its row
+        const float f = (float)rho_f[0];
+        const float* Tb = Lv.t32;
+        float* Pb = Lv.p32;
+        const int lane = threadIdx.x & 31, r = lane & 7, gbase = lane & 24;
+        for (int w0 = (gtid >> 5) << 2; w0 < Lv.nnz_p; w0 += (gthreads >> 5) << 2) {
+          const int b = w0 + (lane >> 3);
+          const bool on = b < Lv.nnz_p && r < 7;
+          float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          int u = 0, c = -1;
+          if (on) {
+            u = __ldg(Lv.p_row + b);
+            c = __ldg(Lv.p_col + b);
+            recipe_row_f32(g, Lv, l, (float)lam, Lv.r1, __ldg(Lv.r1_ptr + b), __ldg(Lv.r1_ptr + b + 1), Tb, r, acc);
+          }
+          const float* M = on ? (l == 0 ? g.minv32 : Lv.dinv32) + (size_t)u * BLK32 : nullptr;
+          const float* Y = (on && c == __ldg(Lv.agg + u)) ? Tb + (size_t)u * BLK32 : nullptr;
+          float out[7];
+          if (l == 0) smooth_row<true>(M, Y, f, r, gbase, acc, out);
+          else smooth_row<false>(M, Y, f, r, gbase, acc, out);
+          if (on)
 #pragma unroll
-        for (int q = 0; q < 49; ++q) acc[q] = 0.f;
-        recipe_blocks_f32(g, Lv, l, (float)lam, Lv.r1, __ldg(Lv.r1_ptr + b), __ldg(Lv.r1_ptr + b + 1), Tb, acc);
-        const float* Y = (c == __ldg(Lv.agg + u)) ? Tb + (size_t)u * BLK32 : nullptr;
-        if (l == 0) st_smoothed<true>(Pb + (size_t)b * BLK32, g.minv32 + (size_t)u * BLK32, acc, Y, f);
-        else st_smoothed<false>(Pb + (size_t)b * BLK32, Lv.dinv32 + (size_t)u * BLK32, acc, Y, f);
+            for (int jj = 0; jj < 7; ++jj) Pb[(size_t)b * BLK32 + r * 7 + jj] = out[jj];
+        }
       }
     } else {
       const double f = rho_f[0];
@@ -1205,23 +1210,38 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
       block_partial(ny2, partial + gridDim.x);
       if (gtid == 0) A.rho[l] = rho;
     }
-    if constexpr (sizeof(V) == 4) {
-      // FP32: one thread per A P block, then Q from the block in registers
-      const float* Pb = Lv.p32;
-      float* APb = Lv.ap32;
-      float* Qb = Lv.q32;
-      const float wl = (float)rho_f[1];
-      for (int b = gtid; b < Lv.nnz_ap; b += gthreads) {
-        float acc[49];
+    if (row_lanes<V>(Lv.nnz_ap)) {
+      if constexpr (sizeof(V) == 4) {
+        // FP32: eight lanes per A P block, then Q from the block's rows
+        const float* Pb = Lv.p32;
+        float* APb = Lv.ap32;
+        float* Qb = Lv.q32;
+        const float wl = (float)rho_f[1];
+        const int lane = threadIdx.x & 31, r = lane & 7, gbase = lane & 24;
+        for (int w0 = (gtid >> 5) << 2; w0 < Lv.nnz_ap; w0 += (gthreads >> 5) << 2) {
+          const int b = w0 + (lane >> 3);
+          const bool on = b < Lv.nnz_ap && r < 7;
+          float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          if (on) {
+            recipe_row_f32(g, Lv, l, (float)lam, Lv.r2, __ldg(Lv.r2_ptr + b), __ldg(Lv.r2_ptr + b + 1), Pb, r, acc);
 #pragma unroll
-        for (int q = 0; q < 49; ++q) acc[q] = 0.f;
-        recipe_blocks_f32(g, Lv, l, (float)lam, Lv.r2, __ldg(Lv.r2_ptr + b), __ldg(Lv.r2_ptr + b + 1), Pb, acc);
-        st_block(APb + (size_t)b * BLK32, acc);
-        if (A.dense) {
-          const int u = __ldg(Lv.ap_row + b), pb = __ldg(Lv.ap_pblk + b);
-          const float* Y = pb >= 0 ? Pb + (size_t)pb * BLK32 : nullptr;
-          if (l == 0) st_smoothed<true>(Qb + (size_t)b * BLK32, g.minv32 + (size_t)u * BLK32, acc, Y, wl);
-          else st_smoothed<false>(Qb + (size_t)b * BLK32, Lv.dinv32 + (size_t)u * BLK32, acc, Y, wl);
+            for (int jj = 0; jj < 7; ++jj) APb[(size_t)b * BLK32 + r * 7 + jj] = acc[jj];
+          }
+          if (A.dense) {
+            int u = 0, pb = -1;
+            if (on) {
+              u = __ldg(Lv.ap_row + b);
+              pb = __ldg(Lv.ap_pblk + b);
+            }
+            const float* M = on ? (l == 0 ? g.minv32 : Lv.dinv32) + (size_t)u * BLK32 : nullptr;
+            const float* Y = (on && pb >= 0) ? Pb + (size_t)pb * BLK32 : nullptr;
+            float out[7];
+            if (l == 0) smooth_row<true>(M, Y, wl, r, gbase, acc, out);
+            else smooth_row<false>(M, Y, wl, r, gbase, acc, out);
+            if (on)
+#pragma unroll
+              for (int jj = 0; jj < 7; ++jj) Qb[(size_t)b * BLK32 + r * 7 + jj] = out[jj];
+          }
         }
       }
     } else {
@@ -1268,24 +1288,28 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
       const double ny2 = power_step<V>(g, Lv, l, lam, AV<V>::pw(A, 1), V(nn.y), AV<V>::pw(A, 0));
       block_partial(ny2, partial);
     }
-    if constexpr (sizeof(V) == 4) {
-      // FP32: one thread per upper block of the next level, sum of P^T (A P)
-      const float* Pb = Lv.p32;
-      const float* APb = Lv.ap32;
-      float* An = Ln.a32;
-      for (int b = gtid; b < Lv.nnz_next; b += gthreads) {
-        const int e0 = __ldg(Lv.r3_ptr + b), e1 = __ldg(Lv.r3_ptr + b + 1);
-        if (e0 == e1) continue;   // mirrored block
-        float acc[49];
+    if (row_lanes<V>(Lv.nnz_next)) {
+      if constexpr (sizeof(V) == 4) {
+        // FP32: eight lanes per upper block of the next level, sum of P^T (A P)
+        const float* Pb = Lv.p32;
+        const float* APb = Lv.ap32;
+        float* An = Ln.a32;
+        const int lane = threadIdx.x & 31, r = lane & 7;
+        for (int w0 = (gtid >> 5) << 2; w0 < Lv.nnz_next; w0 += (gthreads >> 5) << 2) {
+          const int b = w0 + (lane >> 3);
+          if (b >= Lv.nnz_next || r >= 7) continue;
+          const int e0 = __ldg(Lv.r3_ptr + b), e1 = __ldg(Lv.r3_ptr + b + 1);
+          if (e0 == e1) continue;   // mirrored block
+          float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+          for (int e = e0; e < e1; ++e) {
+            const int2 t = __ldg(Lv.r3 + e);
+            float X[52];
+            ld_x52<false>(APb + (size_t)t.y * BLK32, X);
+            mac_row<false, true>(Pb + (size_t)t.x * BLK32, r, X, acc);
+          }
 #pragma unroll
-        for (int q = 0; q < 49; ++q) acc[q] = 0.f;
-        for (int e = e0; e < e1; ++e) {
-          const int2 t = __ldg(Lv.r3 + e);
-          float X[52];
-          ld_x52<false>(APb + (size_t)t.y * BLK32, X);
-          mac_block<false, true>(Pb + (size_t)t.x * BLK32, X, acc);
+          for (int jj = 0; jj < 7; ++jj) An[(size_t)b * BLK32 + r * 7 + jj] = acc[jj];
         }
-        st_block(An + (size_t)b * BLK32, acc);
       }
     } else {
       const int slot = threadIdx.x >> 6, t = threadIdx.x & 63;
