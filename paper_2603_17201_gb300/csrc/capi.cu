@@ -261,14 +261,28 @@ void enqueue_linear_solve(const DevGraph& g, int mixed, int refine_steps, LinSol
   }
 }
 
+// Linearisation and assembly at the current poses: FP64 per edge, then the
+// per-vertex gather; mixed, the fused kernel (cached: the cost kernel of
+// these poses stored their residuals).
+void linearize_assemble(const DevGraph& g, int mixed, int cached, cudaStream_t s) {
+  if (mixed) {
+    launch_lin_assemble_mixed(g, cached, s);
+    return;
+  }
+  launch_linearize(g, 0, s);
+  launch_assemble(g, 0, s);
+}
+
 // One LM iteration (the body of the WHILE node, or one host-driven step).
+// The mixed mode linearises with the fused kernel from the residuals that
+// the cost kernel of the same poses stored (the start cost, or the accepted
+// candidate's).
 void enqueue_lm_body(const DevGraph& g, int mixed, int refine_steps, LinSolve ls, cudaStream_t s,
                      unsigned long long lm_cond, cudaError_t* err) {
-  launch_linearize(g, mixed, s);
-  launch_assemble(g, mixed, s);
+  linearize_assemble(g, mixed, 1, s);
   enqueue_linear_solve(g, mixed, refine_steps, ls, s, err, 1);
   launch_update(g, mixed, s);
-  launch_cost(g, 1, s, lm_cond);
+  launch_cost(g, 1, s, lm_cond, mixed);
 }
 
 // The hierarchy (host descriptor) if the options ask for multigrid and the
@@ -343,7 +357,7 @@ pgo_status build_solve_graph(pgo_graph* G, int mixed, int refine_steps, LinSolve
   b.err = cudaGraphConditionalHandleCreate(&hl, graph, 0, 0);
   b.capture(graph, [&](cudaStream_t s) {
     launch_lm_reset(g, s);
-    launch_cost(g, 0, s, hl);
+    launch_cost(g, 0, s, hl, mixed);
   });
   cudaGraph_t body = b.add_while(graph, hl);
   if (body) {
@@ -372,8 +386,7 @@ pgo_status build_step_graph(pgo_graph* G, int mixed, int refine_steps, LinSolve 
   GraphBuilder b{G->cap_stream};
   cudaError_t le = cudaSuccess;
   b.capture(graph, [&](cudaStream_t s) {
-    launch_linearize(g, mixed, s);
-    launch_assemble(g, mixed, s);
+    linearize_assemble(g, mixed, 0, s);
     enqueue_linear_solve(g, mixed, refine_steps, ls, s, &le);
   });
   if (le != cudaSuccess) b.err = le;
@@ -394,7 +407,7 @@ pgo_status run_eager(pgo_graph* G, int mixed, int refine_steps, int max_iters, L
   cudaStream_t s = G->stream;
   cudaError_t le = cudaSuccess;
   launch_lm_reset(g, s);
-  launch_cost(g, 0, s, 0);
+  launch_cost(g, 0, s, 0, mixed);
   for (int it = 0; it < max_iters + 1; ++it) {
     CUDA_TRY(cudaMemcpyAsync(G->h_state, g.st, sizeof(SolverState), cudaMemcpyDeviceToHost, s));
     CUDA_TRY(cudaStreamSynchronize(s));
@@ -643,6 +656,7 @@ pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
   total += arena_bytes<double>(Ep * BLK64) + arena_bytes<float>(Ep * BLK32);
   total += 2 * arena_bytes<double>((size_t)N * BLK64) + 2 * arena_bytes<float>((size_t)N * BLK32);
   total += arena_bytes<double>((size_t)N * VEC) + arena_bytes<double>(Ep * 2 * CONTRIB);
+  total += arena_bytes<double>(Ep * 2 * 12);
   total += 8 * arena_bytes<double>((size_t)N * VEC) + 6 * arena_bytes<float>((size_t)N * VEC);
   total += arena_bytes<double>((size_t)pcap * 4) + arena_bytes<SolverState>(1) + arena_bytes<DevOptions>(1);
   total += arena_bytes<double>(G->scratch_doubles) + arena_bytes<double>(8);
@@ -689,6 +703,7 @@ pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
   g.minv32 = A.take<float>((size_t)N * BLK32);
   g.b = A.take<double>((size_t)N * VEC);
   g.contrib = A.take<double>(Ep * 2 * CONTRIB);
+  g.rcache = A.take<double>(Ep * 2 * 12);
   g.x64 = A.take<double>((size_t)N * VEC);
   g.r64 = A.take<double>((size_t)N * VEC);
   g.z64 = A.take<double>((size_t)N * VEC);
@@ -851,8 +866,7 @@ pgo_status pgo_graph_linearize(pgo_graph* G, int32_t precision, double* jac, dou
   if (st != PGO_OK) return st;
   cudaStream_t s = G->stream;
   const DevGraph& g = G->g;
-  launch_linearize(g, precision == PGO_MIXED, s);
-  launch_assemble(g, precision == PGO_MIXED, s);
+  linearize_assemble(g, precision == PGO_MIXED, 0, s);
   CUDA_TRY(cudaGetLastError());
   G->lin_valid = true;
   const int E = G->E, N = G->N;

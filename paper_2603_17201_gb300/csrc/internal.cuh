@@ -173,6 +173,7 @@ struct DevGraph {
   float* diag32;          // N x BLK32
   double* b;              // N x VEC
   double* contrib;        // E x 2 x CONTRIB per-edge-side contributions
+  double* rcache;         // 2 x E x 12 residual cache of the mixed LM loop (r and T per pose buffer)
   // preconditioner (explicit inverse of the damped diagonal block)
   double* minv64;         // N x BLK64
   float* minv32;          // N x BLK32
@@ -219,9 +220,13 @@ void launch_batch_reset(const DevGraph& g, const BatchArgs& a, cudaStream_t s);
 // ---- launchers (each enqueues on `s`; inside stream capture they become
 // graph nodes).  `cond` is a graph conditional handle set by the last block
 // of the kernel, or 0 when the kernel is not inside a conditional body. ----
-void launch_cost(const DevGraph& g, int mode, cudaStream_t s, unsigned long long lm_cond);
+void launch_cost(const DevGraph& g, int mode, cudaStream_t s, unsigned long long lm_cond, int store = 0);
 void launch_linearize(const DevGraph& g, int mixed, cudaStream_t s);
 void launch_assemble(const DevGraph& g, int mixed, cudaStream_t s);
+// Mixed precision: the fused linearisation and assembly (k_lin_assemble);
+// cached = 1 when the cost kernel has just stored the residuals of the current
+// poses (inside the LM loop), else a residual pass runs first.
+void launch_lin_assemble_mixed(const DevGraph& g, int cached, cudaStream_t s);
 // mode 1: full-Hessian assembly for the adjoint; mode 2: polish step
 // (both skip the LM lambda_0 and gradient-stop logic)
 void launch_assemble_mode(const DevGraph& g, int mode, cudaStream_t s);

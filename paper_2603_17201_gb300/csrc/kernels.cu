@@ -14,6 +14,8 @@
 namespace pgo {
 
 // Linearisation: one thread per edge (MIXED: FP32 Jacobians and H products).
+// The LM loop and the standalone entry points linearise the mixed mode with
+// the fused k_lin_assemble below; this per-edge form stays for FP64.
 template <int MIXED>
 __global__ void __launch_bounds__(128) k_linearize(DevGraph g) {
   const SolverState* st = g.st;
@@ -23,18 +25,12 @@ __global__ void __launch_bounds__(128) k_linearize(DevGraph g) {
   linearize_edge(g, st->cur, e, MIXED);
 }
 
-// Assembly: 8 lanes per vertex gather the incident edge-side contributions in edge
-// order (deterministic), then write H_vv (full symmetric) and b_v.  The last
-// block derives max diag(H), |b|_inf and |b|^2 over the free vertices, sets
-// lambda_0 on the first linearisation and applies the gradient stop test.
-__global__ void __launch_bounds__(256) k_assemble(DevGraph g, int mixed, int mode) {
+// End of an assembly pass (every block calls it once, all its threads): the
+// last block derives max diag(H), |b|_inf and |b|^2 over the free vertices
+// from the blocks' partials, sets lambda_0 on the first linearisation and
+// applies the gradient stop test (mode 0); other modes only store the norms.
+__device__ void assemble_finish(const DevGraph& g, double mdiag, double mgrad, double b2, int mode, double* sh) {
   SolverState* st = g.st;
-  if (mode == 0 && (st->done || !st->need_lin)) return;
-  __shared__ double sh[32 * 3];
-  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  const int v = tid >> 3, lane = tid & 7;
-  double mdiag = 0.0, mgrad = 0.0, b2 = 0.0;
-  if (v < g.N) assemble_vertex(g, v, lane, mixed, g.fixed, mdiag, mgrad, b2);
   double mx[2] = {mdiag, mgrad};
   double sm[1] = {b2};
   block_max<2>(mx, sh);
@@ -71,9 +67,103 @@ __global__ void __launch_bounds__(256) k_assemble(DevGraph g, int mixed, int mod
   }
 }
 
+// Assembly: 8 lanes per vertex gather the incident edge-side contributions in edge
+// order (deterministic), then write H_vv (full symmetric) and b_v.  The last
+// block derives max diag(H), |b|_inf and |b|^2 over the free vertices, sets
+// lambda_0 on the first linearisation and applies the gradient stop test.
+__global__ void __launch_bounds__(256) k_assemble(DevGraph g, int mixed, int mode) {
+  SolverState* st = g.st;
+  if (mode == 0 && (st->done || !st->need_lin)) return;
+  __shared__ double sh[32 * 3];
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v = tid >> 3, lane = tid & 7;
+  double mdiag = 0.0, mgrad = 0.0, b2 = 0.0;
+  if (v < g.N) assemble_vertex(g, v, lane, mixed, g.fixed, mdiag, mgrad, b2);
+  assemble_finish(g, mdiag, mgrad, b2, mode, sh);
+}
+
+// Mixed precision: linearisation and assembly in one pass (Sec. IV-F), a
+// warp per vertex.  Lane k of vertex v's warp takes v's incidence entries k,
+// k + 32, ...: the edge's FP32 Jacobian on v's side from the cached FP64
+// residual, the side's contribution [upper(w A^T A), w A^T r] and, on the i
+// side, the off-diagonal block.  The warp's contributions meet in a shared
+// memory table and lane u sums entry u over the lanes in lane order: a
+// segmented reduction whose segment is the vertex's incident edges, in a
+// fixed order (deterministic).  H_vv and b_v are written once; no per-edge
+// contribution goes through global memory.
+constexpr int kLinWarps = 4;
+__global__ void __launch_bounds__(kLinWarps * 32) k_lin_assemble(DevGraph g) {
+  SolverState* st = g.st;
+  if (st->done || !st->need_lin) return;
+  __shared__ double tab[kLinWarps][36 * 33];   // entry u of lane k at 33 u + k
+  __shared__ double sh[32 * 3];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int v = blockIdx.x * kLinWarps + warp;
+  double* t = tab[warp];
+  double mdiag = 0.0, mgrad = 0.0, b2 = 0.0;
+  if (v < g.N) {   // whole warps
+    const int cur = st->cur;
+    const int k0 = __ldg(g.inc_ptr + v), k1 = __ldg(g.inc_ptr + v + 1);
+    double acc0 = 0.0, acc1 = 0.0;   // entries u = lane and u = 32 + lane (lane < 4)
+    for (int kb = k0; kb < k1; kb += 32) {
+      const int k = kb + lane;
+      if (k < k1) {
+        lin_entry_mixed(g, cur, __ldg(g.inc_code + k), t + lane);
+      } else {
+#pragma unroll
+        for (int u = 0; u < 36; ++u) t[33 * u + lane] = 0.0;
+      }
+      __syncwarp();
+      const int n = min(32, k1 - kb);
+      for (int q = 0; q < n; ++q) acc0 += t[33 * lane + q];
+      if (lane < 4)
+        for (int q = 0; q < n; ++q) acc1 += t[33 * (32 + lane) + q];
+      __syncwarp();
+    }
+    const bool free_v = v != g.fixed;
+#pragma unroll
+    for (int m = 0; m < 2; ++m) {
+      const int u = m == 0 ? lane : 32 + lane;
+      const double a = m == 0 ? acc0 : acc1;
+      if (u < 28) {
+        const int ra = c_up_a[u], rc = c_up_c[u];
+        g.diag64[(size_t)v * BLK64 + ra * 7 + rc] = a;
+        g.diag64[(size_t)v * BLK64 + rc * 7 + ra] = a;
+        g.diag32[(size_t)v * BLK32 + ra * 7 + rc] = (float)a;
+        g.diag32[(size_t)v * BLK32 + rc * 7 + ra] = (float)a;
+        if (ra == rc && free_v) mdiag = fmax(mdiag, a);
+      } else if (u < 35) {
+        g.b[(size_t)v * VEC + (u - 28)] = a;
+        if (free_v) {
+          mgrad = fmax(mgrad, fabs(a));
+          b2 += a * a;
+        }
+      } else if (u == 35) {
+        g.b[(size_t)v * VEC + 7] = 0.0;
+      }
+    }
+  }
+  assemble_finish(g, mdiag, mgrad, b2, 0, sh);
+}
+
+// Residual cache of the current poses for the fused linearisation outside the
+// LM loop (one thread per edge).
+__global__ void __launch_bounds__(128) k_residual(DevGraph g) {
+  const SolverState* st = g.st;
+  if (st->done || !st->need_lin) return;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < g.E) (void)edge_cost(g, st->cur, e, true);
+}
+
+void launch_lin_assemble_mixed(const DevGraph& g, int cached, cudaStream_t s) {
+  if (!cached && g.E > 0) k_residual<<<(g.E + 127) / 128, 128, 0, s>>>(g);
+  k_lin_assemble<<<(g.N + kLinWarps - 1) / kLinWarps, kLinWarps * 32, 0, s>>>(g);
+}
+
 // mode 0: F at the current poses (start of a solve).
 // mode 1: F' at the candidate poses, then the LM accept/reject rule.
-__global__ void __launch_bounds__(256) k_cost(DevGraph g, int mode, unsigned long long lm_cond) {
+// store: leave the residual cache of the evaluated poses (mixed LM loop).
+__global__ void __launch_bounds__(256) k_cost(DevGraph g, int mode, unsigned long long lm_cond, int store) {
   SolverState* st = g.st;
   if (mode == 1 && st->done) {
     // stopped earlier in this iteration (gradient test): leave the LM loop
@@ -84,7 +174,7 @@ __global__ void __launch_bounds__(256) k_cost(DevGraph g, int mode, unsigned lon
   const int buf = mode == 0 ? st->cur : (st->cur ^ 1);
   double c[1] = {0.0};
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < g.E; e += gridDim.x * blockDim.x)
-    c[0] += edge_cost(g, buf, e);
+    c[0] += edge_cost(g, buf, e, store != 0);
   block_sum<1>(c, sh);
   if (!publish_partials<1>(c, g.partial, &st->ticket[T_COST])) return;
   double tot[1];
@@ -202,11 +292,11 @@ void launch_resolve_reset(const DevGraph& g, cudaStream_t s) { k_resolve_reset<<
 // The edge and vertex kernels below are latency chains of FP64 arithmetic
 // (log and exp maps) over a few thousand items: small thread blocks spread
 // them over every SM instead of a few.
-void launch_cost(const DevGraph& g, int mode, cudaStream_t s, unsigned long long lm_cond) {
+void launch_cost(const DevGraph& g, int mode, cudaStream_t s, unsigned long long lm_cond, int store) {
   int blocks = (g.E + 127) / 128;
   if (blocks > g.partial_cap) blocks = g.partial_cap;
   if (blocks < 1) blocks = 1;
-  k_cost<<<blocks, 128, 0, s>>>(g, mode, lm_cond);
+  k_cost<<<blocks, 128, 0, s>>>(g, mode, lm_cond, store);
 }
 
 void launch_linearize(const DevGraph& g, int mixed, cudaStream_t s) {
@@ -260,7 +350,7 @@ void launch_update(const DevGraph& g, int mixed, cudaStream_t s) {
 void launch_lm_reset(const DevGraph& g, cudaStream_t s) { k_lm_reset<<<1, 1, 0, s>>>(g); }
 
 int max_partials(int N, int E) {
-  int a = (N * 32 + 255) / 256;   // warp-per-row kernels
+  int a = (N + 3) / 4;            // warp-per-row kernels (4 rows per block)
   int c = (E + 255) / 256;
   int m = a > c ? a : c;
   return m + 8;

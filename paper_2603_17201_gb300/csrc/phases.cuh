@@ -6,6 +6,28 @@
 
 namespace pgo {
 
+// Residual cache of the mixed-precision LM loop: per pose buffer and edge,
+// the FP64 residual r = log(T) (7 doubles and a pad) and T = Z S_i S_j^-1
+// as 8 floats (q, then t and s).  The cost kernel writes the entry of the
+// poses it evaluates; the fused linearisation of the same poses reads it
+// instead of evaluating the log map again.
+constexpr int RC_STRIDE = 12;   // doubles per edge (96 bytes)
+__device__ __forceinline__ double* rcache_at(const DevGraph& g, int buf, int e) {
+  return g.rcache + ((size_t)buf * g.E + e) * RC_STRIDE;
+}
+
+__device__ __forceinline__ void rcache_store(double* c, const double (&r)[7], const Sim3T<double>& T) {
+  double2* c2 = reinterpret_cast<double2*>(c);
+  c2[0] = make_double2(r[0], r[1]);
+  c2[1] = make_double2(r[2], r[3]);
+  c2[2] = make_double2(r[4], r[5]);
+  c2[3] = make_double2(r[6], 0.0);
+  float4* c4 = reinterpret_cast<float4*>(c + 8);
+  c4[0] = make_float4((float)T.q[0], (float)T.q[1], (float)T.q[2], (float)T.q[3]);
+  c4[1] = make_float4((float)T.t[0], (float)T.t[1], (float)T.t[2], (float)T.s);
+}
+
+
 // packed upper-triangular index (a <= c) of a symmetric 7x7 block
 __device__ __forceinline__ int upk(int a, int c) { return a * 7 - (a * (a - 1)) / 2 + (c - a); }
 
@@ -112,6 +134,124 @@ __device__ __forceinline__ void linearize_edge(const DevGraph& g, int cur, int e
   }
 }
 
+// ---- mixed precision: fused linearisation and assembly --------------------
+// A <- L^T A in FP32 (L the packed lower-triangular factor of Omega).
+__device__ __forceinline__ void whiten_f32(const double* L, float (&A)[7][7]) {
+  float l[28];
+#pragma unroll
+  for (int k = 0; k < 28; ++k) l[k] = (float)__ldg(L + k);
+#pragma unroll
+  for (int col = 0; col < 7; ++col) {
+    float t[7];
+#pragma unroll
+    for (int c = 0; c < 7; ++c) {
+      float acc = 0.f;
+#pragma unroll
+      for (int a = c; a < 7; ++a) acc += l[a * (a + 1) / 2 + c] * A[a][col];
+      t[c] = acc;
+    }
+#pragma unroll
+    for (int c = 0; c < 7; ++c) A[c][col] = t[c];
+  }
+}
+
+// One side's contribution [upper(w A^T A) (FP32 products), w A^T r (FP64)]
+// into the column `col` of the warp's reduction table (entry u at col[33 u]).
+__device__ __forceinline__ void side_contribution(const float (&A)[7][7], const double (&r)[7], float w, double wd,
+                                                  double* col) {
+#pragma unroll
+  for (int a = 0; a < 7; ++a) {
+#pragma unroll
+    for (int c = a; c < 7; ++c) {
+      float sacc = 0.f;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) sacc += A[k][a] * A[k][c];
+      col[33 * upk(a, c)] = (double)(w * sacc);
+    }
+    double gacc = 0.0;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) gacc += (double)A[k][a] * r[k];
+    col[33 * (28 + a)] = wd * gacc;
+  }
+  col[33 * 35] = 0.0;
+}
+
+// Incidence entry `code` (edge code >> 1 seen from side code & 1; side 0:
+// the vertex is i) of the fused mixed linearisation at pose buffer `cur`:
+// the side's FP32 Jacobian from the cached FP64 residual (A_i = J_l^-1(r)
+// Adj(Z), A_j = -J_l^-1(r) Adj(T), the exact Jacobians of the log residual
+// for left perturbations), its contribution into `col`, and on the i side the
+// off-diagonal block w A_i^T Omega A_j (FP32, and promoted to FP64 for the
+// refinement residual).
+__device__ __forceinline__ void lin_entry_mixed(const DevGraph& g, int cur, int code, double* col) {
+  const int e = code >> 1;
+  const bool iside = (code & 1) == 0;
+  const double* c = rcache_at(g, cur, e);
+  double r[7];
+  {
+    const double2* c2 = reinterpret_cast<const double2*>(c);
+    const double2 a0 = c2[0], a1 = c2[1], a2 = c2[2], a3 = c2[3];
+    r[0] = a0.x; r[1] = a0.y; r[2] = a1.x; r[3] = a1.y; r[4] = a2.x; r[5] = a2.y; r[6] = a3.x;
+  }
+  const float4 tq = reinterpret_cast<const float4*>(c + 8)[0];
+  const float4 tts = reinterpret_cast<const float4*>(c + 8)[1];
+  float J[7][7];
+  left_jacobian_inv_f32(r, J);
+  const double* L = g.L ? g.L + (size_t)e * 28 : nullptr;
+  if (L) {   // whitened residual L^T r in FP64
+    double rr[7];
+#pragma unroll
+    for (int cc = 0; cc < 7; ++cc) {
+      double s2 = 0.0;
+#pragma unroll
+      for (int a = cc; a < 7; ++a) s2 += __ldg(L + a * (a + 1) / 2 + cc) * r[a];
+      rr[cc] = s2;
+    }
+#pragma unroll
+    for (int cc = 0; cc < 7; ++cc) r[cc] = rr[cc];
+  }
+  const double wd = g.w[e];
+  const float w = (float)wd;
+  float Aj[7][7];
+  {
+    const float q[4] = {tq.x, tq.y, tq.z, tq.w};
+    float R[9];
+    qmat(q, R);
+    const float t[3] = {tts.x, tts.y, tts.z};
+    jac_times_adj<float>(J, R, t, tts.w, -1.f, Aj);
+  }
+  if (L) whiten_f32(L, Aj);
+  if (!iside) {
+    side_contribution(Aj, r, w, wd, col);
+    return;
+  }
+  float Ai[7][7];
+  {
+    const D4 zq = g.zq[e], zt = g.zt[e];
+    const float q[4] = {(float)zq.x, (float)zq.y, (float)zq.z, (float)zq.w};
+    float R[9];
+    qmat(q, R);
+    const float t[3] = {(float)zt.x, (float)zt.y, (float)zt.z};
+    jac_times_adj<float>(J, R, t, (float)zt.w, 1.f, Ai);
+  }
+  if (L) whiten_f32(L, Ai);
+  double* off = g.off64 + (size_t)e * BLK64;
+  float* off32 = g.off32 + (size_t)e * BLK32;
+#pragma unroll
+  for (int a = 0; a < 7; ++a) {
+#pragma unroll
+    for (int cc = 0; cc < 7; ++cc) {
+      float sacc = 0.f;
+#pragma unroll
+      for (int k = 0; k < 7; ++k) sacc += Ai[k][a] * Aj[k][cc];
+      sacc *= w;
+      off32[a * 7 + cc] = sacc;
+      off[a * 7 + cc] = (double)sacc;
+    }
+  }
+  side_contribution(Ai, r, w, wd, col);
+}
+
 // Assembly for one vertex, lane `lane` of 8: gather the incident contributions in
 // incidence order (deterministic), write H_vv (full symmetric) and b_v, and
 // fold max diag, |b|_inf and |b|^2 (free vertices only) into the arguments.
@@ -153,14 +293,16 @@ __device__ __forceinline__ void assemble_vertex(const DevGraph& g, int v, int la
   }
 }
 
-// Cost of one edge at the poses in buffer `buf` (FP64).
-__device__ __forceinline__ double edge_cost(const DevGraph& g, int buf, int e) {
+// Cost of one edge at the poses in buffer `buf` (FP64); with `store`, also
+// its residual cache entry.
+__device__ __forceinline__ double edge_cost(const DevGraph& g, int buf, int e, bool store = false) {
   const int i = g.ei[e], j = g.ej[e];
   Sim3T<double> Si = load_pose(g, buf, i), Sj = load_pose(g, buf, j), Z = load_meas(g, e);
   Sim3T<double> T = compose(Z, compose(Si, inverse(Sj)));
   qnormalize(T.q);
   double r[7];
   sim3_log(T, r);
+  if (store) rcache_store(rcache_at(g, buf, e), r, T);
   double c = 0.0;
   if (g.L) {
     const double* L = g.L + (size_t)e * 28;
