@@ -140,7 +140,7 @@ __device__ __forceinline__ void left_jacobian_inv_f32(const double* xi, float (&
     double term = nrm / 2.0;   // |ad|^n / (n+1)! for n = 1
     while (term > 1e-9 && N < 40) {
       ++N;
-      term *= nrm / (N + 1);
+      term *= nrm * c_rcp[N];   // 1 / (N + 1)
     }
   }
   // Horner: J = I + ad/2 (I + ad/3 (I + ... (I + ad/(N+1))))

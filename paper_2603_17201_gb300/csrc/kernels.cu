@@ -95,51 +95,62 @@ constexpr int kLinWarps = 4;
 __global__ void __launch_bounds__(kLinWarps * 32) k_lin_assemble(DevGraph g) {
   SolverState* st = g.st;
   if (st->done || !st->need_lin) return;
-  __shared__ double tab[kLinWarps][36 * 33];   // entry u of lane k at 33 u + k
+  __shared__ float htab[kLinWarps][28 * 33];    // H entry u of lane k at 33 u + k
+  __shared__ double btab[kLinWarps][7 * 33];    // b entry a of lane k at 33 a + k
+  __shared__ double bpart[kLinWarps][4 * 7];    // b partial sums of 8 lanes
   __shared__ double sh[32 * 3];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int v = blockIdx.x * kLinWarps + warp;
-  double* t = tab[warp];
+  float* ht = htab[warp];
+  double* bt = btab[warp];
   double mdiag = 0.0, mgrad = 0.0, b2 = 0.0;
   if (v < g.N) {   // whole warps
     const int cur = st->cur;
     const int k0 = __ldg(g.inc_ptr + v), k1 = __ldg(g.inc_ptr + v + 1);
-    double acc0 = 0.0, acc1 = 0.0;   // entries u = lane and u = 32 + lane (lane < 4)
+    float hacc = 0.f;    // H entry `lane` (lane < 28)
+    double bacc = 0.0;   // b entry `lane` (lane < 7)
+    const int bc = lane % 7, bg = lane / 7;   // lanes < 28: b entry bc over lanes 8 bg .. 8 bg + 7
     for (int kb = k0; kb < k1; kb += 32) {
       const int k = kb + lane;
       if (k < k1) {
-        lin_entry_mixed(g, cur, __ldg(g.inc_code + k), t + lane);
+        lin_entry_mixed(g, cur, __ldg(g.inc_code + k), ht + lane, bt + lane);
       } else {
 #pragma unroll
-        for (int u = 0; u < 36; ++u) t[33 * u + lane] = 0.0;
+        for (int u = 0; u < 28; ++u) ht[33 * u + lane] = 0.f;
+#pragma unroll
+        for (int a = 0; a < 7; ++a) bt[33 * a + lane] = 0.0;
       }
       __syncwarp();
-      const int n = min(32, k1 - kb);
-      for (int q = 0; q < n; ++q) acc0 += t[33 * lane + q];
-      if (lane < 4)
-        for (int q = 0; q < n; ++q) acc1 += t[33 * (32 + lane) + q];
+      // sums in lane order: H in FP32 (one entry per lane), b in FP64 (four
+      // partial sums of 8 lanes, then lanes 0..6 add the four in order)
+      if (lane < 28) {
+#pragma unroll 8
+        for (int q = 0; q < 32; ++q) hacc += ht[33 * lane + q];
+        double p = 0.0;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) p += bt[33 * bc + 8 * bg + q];
+        bpart[warp][bg * 7 + bc] = p;
+      }
+      __syncwarp();
+      if (lane < 7) bacc += ((bpart[warp][lane] + bpart[warp][7 + lane]) + bpart[warp][14 + lane]) + bpart[warp][21 + lane];
       __syncwarp();
     }
     const bool free_v = v != g.fixed;
-#pragma unroll
-    for (int m = 0; m < 2; ++m) {
-      const int u = m == 0 ? lane : 32 + lane;
-      const double a = m == 0 ? acc0 : acc1;
-      if (u < 28) {
-        const int ra = c_up_a[u], rc = c_up_c[u];
-        g.diag64[(size_t)v * BLK64 + ra * 7 + rc] = a;
-        g.diag64[(size_t)v * BLK64 + rc * 7 + ra] = a;
-        g.diag32[(size_t)v * BLK32 + ra * 7 + rc] = (float)a;
-        g.diag32[(size_t)v * BLK32 + rc * 7 + ra] = (float)a;
-        if (ra == rc && free_v) mdiag = fmax(mdiag, a);
-      } else if (u < 35) {
-        g.b[(size_t)v * VEC + (u - 28)] = a;
-        if (free_v) {
-          mgrad = fmax(mgrad, fabs(a));
-          b2 += a * a;
-        }
-      } else if (u == 35) {
-        g.b[(size_t)v * VEC + 7] = 0.0;
+    if (lane < 28) {
+      const int ra = c_up_a[lane], rc = c_up_c[lane];
+      const double a = (double)hacc;
+      g.diag64[(size_t)v * BLK64 + ra * 7 + rc] = a;
+      g.diag64[(size_t)v * BLK64 + rc * 7 + ra] = a;
+      g.diag32[(size_t)v * BLK32 + ra * 7 + rc] = hacc;
+      g.diag32[(size_t)v * BLK32 + rc * 7 + ra] = hacc;
+      if (ra == rc && free_v) mdiag = a;
+    }
+    if (lane < 8) {
+      const double bv = lane < 7 ? bacc : 0.0;
+      g.b[(size_t)v * VEC + lane] = bv;
+      if (lane < 7 && free_v) {
+        mgrad = fabs(bv);
+        b2 = bv * bv;
       }
     }
   }

@@ -946,26 +946,50 @@ __global__ void __launch_bounds__(256) k_refine_residual(DevGraph g, int first) 
     const size_t base = (size_t)v * VEC;
     double y = 0.0;
     if (!first) {
-      const double xv = g.dx64[base + c7];
-      y = lam * xv;
-      const double* D = g.diag64 + (size_t)v * BLK64;
-#pragma unroll
-      for (int c = 0; c < 7; ++c) y += D[c7 * 7 + c] * __shfl_sync(gm8, xv, (threadIdx.x & ~7) + c);
+      // lane j of the row's 8 takes whole blocks j, j + 8, ... of the row
+      // (the damped diagonal block first), then the 8 lanes reduce: 4 blocks
+      // in sequence per lane instead of the row's 30
       const int k0 = g.inc_ptr[v], ks = g.inc_split[v], k1 = g.inc_ptr[v + 1];
-      for (int k = k0; k < ks; ++k) {   // side 0: H_vu
-        const int code = __ldg(g.inc_code + k);
-        const double xu = g.dx64[(size_t)__ldg(g.inc_other + k) * VEC + c7];
-        const double* B = g.off64 + (size_t)(code >> 1) * BLK64;
+      double yv[7] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+      for (int k = k0 - 1 + lane8; k < k1; k += 8) {
+        int u = v;
+        const double* B;
+        bool tr = false;
+        if (k < k0) {
+          B = g.diag64 + (size_t)v * BLK64;
+        } else {
+          const int code = __ldg(g.inc_code + k);
+          u = __ldg(g.inc_other + k);
+          B = g.off64 + (size_t)(code >> 1) * BLK64;
+          tr = k >= ks;   // side 1: H_uv^T
+        }
+        double xu[8];
+        const double2* x2 = reinterpret_cast<const double2*>(g.dx64 + (size_t)u * VEC);
 #pragma unroll
-        for (int c = 0; c < 7; ++c) y += B[c7 * 7 + c] * __shfl_sync(gm8, xu, (threadIdx.x & ~7) + c);
-      }
-      for (int k = ks; k < k1; ++k) {   // side 1: H_uv^T
-        const int code = __ldg(g.inc_code + k);
-        const double xu = g.dx64[(size_t)__ldg(g.inc_other + k) * VEC + c7];
-        const double* B = g.off64 + (size_t)(code >> 1) * BLK64;
+        for (int c = 0; c < 4; ++c) {
+          const double2 t2 = __ldcg(x2 + c);
+          xu[2 * c] = t2.x;
+          xu[2 * c + 1] = t2.y;
+        }
+        double Bv[49];
+        load_block(B, Bv);
 #pragma unroll
-        for (int c = 0; c < 7; ++c) y += B[c * 7 + c7] * __shfl_sync(gm8, xu, (threadIdx.x & ~7) + c);
+        for (int a = 0; a < 7; ++a) {
+          double t = (k < k0) ? lam * xu[a] : 0.0;
+#pragma unroll
+          for (int c = 0; c < 7; ++c) t += (tr ? Bv[c * 7 + a] : Bv[a * 7 + c]) * xu[c];
+          yv[a] += t;
+        }
       }
+#pragma unroll
+      for (int a = 0; a < 7; ++a) {
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) yv[a] += __shfl_xor_sync(gm8, yv[a], o);
+      }
+      y = yv[0];
+#pragma unroll
+      for (int a = 1; a < 7; ++a)
+        if (c7 == a) y = yv[a];
     } else if (act) {
       g.dx64[base + c7] = 0.0;
     }

@@ -155,10 +155,11 @@ __device__ __forceinline__ void whiten_f32(const double* L, float (&A)[7][7]) {
   }
 }
 
-// One side's contribution [upper(w A^T A) (FP32 products), w A^T r (FP64)]
-// into the column `col` of the warp's reduction table (entry u at col[33 u]).
-__device__ __forceinline__ void side_contribution(const float (&A)[7][7], const double (&r)[7], float w, double wd,
-                                                  double* col) {
+// One side's contribution: upper(w A^T A) into hcol (entry u at hcol[33 u])
+// and w A^T r into bcol (entry a at bcol[33 a]), both from FP32 products;
+// the sums over the vertex's edges run in FP32 for H and in FP64 for b.
+__device__ __forceinline__ void side_contribution(const float (&A)[7][7], const float (&r)[7], float w,
+                                                  float* hcol, double* bcol) {
 #pragma unroll
   for (int a = 0; a < 7; ++a) {
 #pragma unroll
@@ -166,24 +167,23 @@ __device__ __forceinline__ void side_contribution(const float (&A)[7][7], const 
       float sacc = 0.f;
 #pragma unroll
       for (int k = 0; k < 7; ++k) sacc += A[k][a] * A[k][c];
-      col[33 * upk(a, c)] = (double)(w * sacc);
+      hcol[33 * upk(a, c)] = w * sacc;
     }
-    double gacc = 0.0;
+    float gacc = 0.f;
 #pragma unroll
-    for (int k = 0; k < 7; ++k) gacc += (double)A[k][a] * r[k];
-    col[33 * (28 + a)] = wd * gacc;
+    for (int k = 0; k < 7; ++k) gacc += A[k][a] * r[k];
+    bcol[33 * a] = (double)(w * gacc);
   }
-  col[33 * 35] = 0.0;
 }
 
 // Incidence entry `code` (edge code >> 1 seen from side code & 1; side 0:
 // the vertex is i) of the fused mixed linearisation at pose buffer `cur`:
 // the side's FP32 Jacobian from the cached FP64 residual (A_i = J_l^-1(r)
 // Adj(Z), A_j = -J_l^-1(r) Adj(T), the exact Jacobians of the log residual
-// for left perturbations), its contribution into `col`, and on the i side the
-// off-diagonal block w A_i^T Omega A_j (FP32, and promoted to FP64 for the
-// refinement residual).
-__device__ __forceinline__ void lin_entry_mixed(const DevGraph& g, int cur, int code, double* col) {
+// for left perturbations), its contribution into the reduction table, and on
+// the i side the off-diagonal block w A_i^T Omega A_j (FP32, and promoted to
+// FP64 for the refinement residual).
+__device__ __forceinline__ void lin_entry_mixed(const DevGraph& g, int cur, int code, float* hcol, double* bcol) {
   const int e = code >> 1;
   const bool iside = (code & 1) == 0;
   const double* c = rcache_at(g, cur, e);
@@ -197,59 +197,63 @@ __device__ __forceinline__ void lin_entry_mixed(const DevGraph& g, int cur, int 
   const float4 tts = reinterpret_cast<const float4*>(c + 8)[1];
   float J[7][7];
   left_jacobian_inv_f32(r, J);
+  float rf[7];
+#pragma unroll
+  for (int k = 0; k < 7; ++k) rf[k] = (float)r[k];
   const double* L = g.L ? g.L + (size_t)e * 28 : nullptr;
-  if (L) {   // whitened residual L^T r in FP64
-    double rr[7];
+  if (L) {   // whitened residual L^T r
+    float rr[7];
 #pragma unroll
     for (int cc = 0; cc < 7; ++cc) {
-      double s2 = 0.0;
+      float s2 = 0.f;
 #pragma unroll
-      for (int a = cc; a < 7; ++a) s2 += __ldg(L + a * (a + 1) / 2 + cc) * r[a];
+      for (int a = cc; a < 7; ++a) s2 += (float)__ldg(L + a * (a + 1) / 2 + cc) * rf[a];
       rr[cc] = s2;
     }
 #pragma unroll
-    for (int cc = 0; cc < 7; ++cc) r[cc] = rr[cc];
+    for (int cc = 0; cc < 7; ++cc) rf[cc] = rr[cc];
   }
-  const double wd = g.w[e];
-  const float w = (float)wd;
-  float Aj[7][7];
+  const float w = (float)g.w[e];
+  float A[7][7];   // this side's Jacobian
   {
     const float q[4] = {tq.x, tq.y, tq.z, tq.w};
     float R[9];
     qmat(q, R);
     const float t[3] = {tts.x, tts.y, tts.z};
-    jac_times_adj<float>(J, R, t, tts.w, -1.f, Aj);
+    jac_times_adj<float>(J, R, t, tts.w, -1.f, A);   // A_j
   }
-  if (L) whiten_f32(L, Aj);
-  if (!iside) {
-    side_contribution(Aj, r, w, wd, col);
-    return;
-  }
-  float Ai[7][7];
-  {
-    const D4 zq = g.zq[e], zt = g.zt[e];
-    const float q[4] = {(float)zq.x, (float)zq.y, (float)zq.z, (float)zq.w};
-    float R[9];
-    qmat(q, R);
-    const float t[3] = {(float)zt.x, (float)zt.y, (float)zt.z};
-    jac_times_adj<float>(J, R, t, (float)zt.w, 1.f, Ai);
-  }
-  if (L) whiten_f32(L, Ai);
-  double* off = g.off64 + (size_t)e * BLK64;
-  float* off32 = g.off32 + (size_t)e * BLK32;
-#pragma unroll
-  for (int a = 0; a < 7; ++a) {
-#pragma unroll
-    for (int cc = 0; cc < 7; ++cc) {
-      float sacc = 0.f;
-#pragma unroll
-      for (int k = 0; k < 7; ++k) sacc += Ai[k][a] * Aj[k][cc];
-      sacc *= w;
-      off32[a * 7 + cc] = sacc;
-      off[a * 7 + cc] = (double)sacc;
+  if (L) whiten_f32(L, A);
+  if (iside) {
+    float Ai[7][7];
+    {
+      const D4 zq = g.zq[e], zt = g.zt[e];
+      const float q[4] = {(float)zq.x, (float)zq.y, (float)zq.z, (float)zq.w};
+      float R[9];
+      qmat(q, R);
+      const float t[3] = {(float)zt.x, (float)zt.y, (float)zt.z};
+      jac_times_adj<float>(J, R, t, (float)zt.w, 1.f, Ai);
     }
+    if (L) whiten_f32(L, Ai);
+    double* off = g.off64 + (size_t)e * BLK64;
+    float* off32 = g.off32 + (size_t)e * BLK32;
+#pragma unroll
+    for (int a = 0; a < 7; ++a) {
+#pragma unroll
+      for (int cc = 0; cc < 7; ++cc) {
+        float sacc = 0.f;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) sacc += Ai[k][a] * A[k][cc];
+        sacc *= w;
+        off32[a * 7 + cc] = sacc;
+        off[a * 7 + cc] = (double)sacc;
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 7; ++a)
+#pragma unroll
+      for (int cc = 0; cc < 7; ++cc) A[a][cc] = Ai[a][cc];
   }
-  side_contribution(Ai, r, w, wd, col);
+  side_contribution(A, rf, w, hcol, bcol);
 }
 
 // Assembly for one vertex, lane `lane` of 8: gather the incident contributions in
@@ -359,7 +363,10 @@ __device__ __forceinline__ void precond_vertex(const DevGraph& g, int v, int fix
   for (int a = 0; a < 7; ++a)
 #pragma unroll
     for (int c = 0; c < 7; ++c) A[a][c] = D[a * 7 + c] + (a == c ? lam : 0.0);
+  // Cholesky A = L L^T with the reciprocals of the pivots (7 divisions: on
+  // GB300 an FP64 divide costs many FP64 issue slots)
   bool ok = true;
+  double rd[7];
 #pragma unroll
   for (int j = 0; j < 7; ++j) {
     double d = A[j][j];
@@ -368,13 +375,13 @@ __device__ __forceinline__ void precond_vertex(const DevGraph& g, int v, int fix
     ok = ok && (d > 0.0);
     d = sqrt(fmax(d, 1e-300));
     A[j][j] = d;
-    const double inv = 1.0 / d;
+    rd[j] = 1.0 / d;
 #pragma unroll
     for (int i = j + 1; i < 7; ++i) {
       double s = A[i][j];
 #pragma unroll
       for (int k = 0; k < j; ++k) s -= A[i][k] * A[j][k];
-      A[i][j] = s * inv;
+      A[i][j] = s * rd[j];
     }
   }
   if (!ok) {
@@ -384,6 +391,7 @@ __device__ __forceinline__ void precond_vertex(const DevGraph& g, int v, int fix
       for (int c = 0; c < 7; ++c) M[a * 7 + c] = (a == c) ? V(1.0 / fmax(D[a * 8] + lam, 1e-300)) : V(0);
     return;
   }
+  // Li = L^-1 (lower triangular), then M = Li^T Li (symmetric: upper half)
   double Li[7][7];
 #pragma unroll
   for (int c = 0; c < 7; ++c) {
@@ -396,17 +404,18 @@ __device__ __forceinline__ void precond_vertex(const DevGraph& g, int v, int fix
       double s = (a == c) ? 1.0 : 0.0;
 #pragma unroll
       for (int k = c; k < a; ++k) s -= A[a][k] * Li[k][c];
-      Li[a][c] = s / A[a][a];
+      Li[a][c] = s * rd[a];
     }
   }
 #pragma unroll
   for (int a = 0; a < 7; ++a)
 #pragma unroll
-    for (int c = 0; c < 7; ++c) {
+    for (int c = a; c < 7; ++c) {
       double s = 0.0;
 #pragma unroll
-      for (int k = 0; k < 7; ++k) s += Li[k][a] * Li[k][c];
+      for (int k = c; k < 7; ++k) s += Li[k][a] * Li[k][c];
       M[a * 7 + c] = V(s);
+      M[c * 7 + a] = V(s);
     }
 }
 

@@ -70,6 +70,21 @@ __device__ __forceinline__ Sim3T<S> inverse(const Sim3T<S>& a) {
   return c;
 }
 
+// Reciprocals 1/m, m = 1..76 (c_rcp[m - 1]), rounded once by the compiler:
+// the moment series below scales by them with a loop-dependent m, where a
+// division would cost a full FP64 divide per term.
+static __device__ __constant__ double c_rcp[76] = {
+    1.0 / 1, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5, 1.0 / 6, 1.0 / 7, 1.0 / 8,
+    1.0 / 9, 1.0 / 10, 1.0 / 11, 1.0 / 12, 1.0 / 13, 1.0 / 14, 1.0 / 15, 1.0 / 16,
+    1.0 / 17, 1.0 / 18, 1.0 / 19, 1.0 / 20, 1.0 / 21, 1.0 / 22, 1.0 / 23, 1.0 / 24,
+    1.0 / 25, 1.0 / 26, 1.0 / 27, 1.0 / 28, 1.0 / 29, 1.0 / 30, 1.0 / 31, 1.0 / 32,
+    1.0 / 33, 1.0 / 34, 1.0 / 35, 1.0 / 36, 1.0 / 37, 1.0 / 38, 1.0 / 39, 1.0 / 40,
+    1.0 / 41, 1.0 / 42, 1.0 / 43, 1.0 / 44, 1.0 / 45, 1.0 / 46, 1.0 / 47, 1.0 / 48,
+    1.0 / 49, 1.0 / 50, 1.0 / 51, 1.0 / 52, 1.0 / 53, 1.0 / 54, 1.0 / 55, 1.0 / 56,
+    1.0 / 57, 1.0 / 58, 1.0 / 59, 1.0 / 60, 1.0 / 61, 1.0 / 62, 1.0 / 63, 1.0 / 64,
+    1.0 / 65, 1.0 / 66, 1.0 / 67, 1.0 / 68, 1.0 / 69, 1.0 / 70, 1.0 / 71, 1.0 / 72,
+    1.0 / 73, 1.0 / 74, 1.0 / 75, 1.0 / 76};
+
 // Moments I_n(sigma) = int_0^1 tau^n e^(sigma tau) dtau for n = 1..10 from
 // the power series sum_k sigma^k / (k! (n + k + 1)), summed until the term
 // is below 1e-18 of the leading moment (at most 64 terms).
@@ -81,10 +96,10 @@ __device__ __forceinline__ void moments(const S& sigma, S* I /* I[1..10] in I[0.
   double av = fabs((double)val(sigma));
   double mag = 1.0;
   for (int k = 1; k < 64; ++k) {
-    term = scal(term * sigma, 1.0 / k);
-    mag *= av / k;
+    term = scal(term * sigma, c_rcp[k - 1]);
+    mag *= av * c_rcp[k - 1];
 #pragma unroll
-    for (int n = 0; n < 10; ++n) I[n] = I[n] + scal(term, 1.0 / (n + 1 + k + 1));
+    for (int n = 0; n < 10; ++n) I[n] = I[n] + scal(term, c_rcp[n + k + 1]);
     if (mag < 1e-19) break;
   }
 }
