@@ -23,8 +23,14 @@
 // The sparsity of every level and the index lists of every product are built
 // once on the host (amg_build); the numeric setup (k_amg_setup) runs on the
 // device at every linearisation, because H, lambda and the poses change.
+#include <unistd.h>
+
 #include <algorithm>
+#include <atomic>
+#include <condition_variable>
 #include <cstring>
+#include <functional>
+#include <mutex>
 #include <thread>
 #include <vector>
 
@@ -84,6 +90,76 @@ struct NbrView {
 };
 
 
+// Host worker pool of the hierarchy analysis: created on first use, kept for
+// the life of the process (spawning threads per call cost as much as the
+// work on a 2,000-keyframe graph).  run(n, f) calls f(0) .. f(n - 1) on the
+// workers and the calling thread and returns when all are done; concurrent
+// callers take turns.  A process forked after the pool exists has no
+// workers: run() then executes the calls itself.
+class HostPool {
+ public:
+  static HostPool& get() {
+    static HostPool* p = new HostPool();   // never destroyed: workers idle at exit
+    return *p;
+  }
+  int width() const { return nthreads_ + 1; }
+  void run(int n, const std::function<void(int)>& f) {
+    std::lock_guard<std::mutex> serial(run_mu_);
+    if (n <= 1 || nthreads_ == 0 || getpid() != pid_) {
+      for (int i = 0; i < n; ++i) f(i);
+      return;
+    }
+    {
+      std::lock_guard<std::mutex> lk(mu_);
+      job_ = &f;
+      njobs_ = n;
+      next_.store(0);
+      pending_ = n;
+      ++gen_;
+    }
+    cv_.notify_all();
+    drain();
+    std::unique_lock<std::mutex> lk(mu_);
+    done_cv_.wait(lk, [&] { return pending_ == 0; });
+    job_ = nullptr;
+  }
+
+ private:
+  HostPool() : pid_(getpid()) {
+    const unsigned hw = std::thread::hardware_concurrency();
+    nthreads_ = (int)std::min<unsigned>(hw > 1 ? hw - 1 : 0, 15);
+    for (int t = 0; t < nthreads_; ++t) std::thread([this] { loop(); }).detach();
+  }
+  void drain() {
+    for (;;) {
+      const int i = next_.fetch_add(1);
+      if (i >= njobs_) return;
+      (*job_)(i);
+      std::lock_guard<std::mutex> lk(mu_);
+      if (--pending_ == 0) done_cv_.notify_all();
+    }
+  }
+  void loop() {
+    unsigned seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(mu_);
+        cv_.wait(lk, [&] { return gen_ != seen; });
+        seen = gen_;
+      }
+      drain();
+    }
+  }
+  const pid_t pid_;
+  int nthreads_ = 0;
+  std::mutex run_mu_, mu_;
+  std::condition_variable cv_, done_cv_;
+  const std::function<void(int)>* job_ = nullptr;
+  int njobs_ = 0, pending_ = 0;
+  unsigned gen_ = 0;
+  std::atomic<int> next_{0};
+};
+
 // Rows [0, n) of a block-sparse product, grouped by column: gen(row, emit)
 // emits terms emit(col, x, y); each row gets its distinct columns ascending
 // (plus `diag_col(row)` when that is >= 0) and each (row, column) block its
@@ -93,18 +169,23 @@ struct NbrView {
 // result does not depend on the thread count.
 template <class Gen, class Diag>
 void group_rows(int n, int ncols, Gen gen, Diag diag_col, std::vector<int>& row_ptr, std::vector<int>& col,
-                std::vector<int>& rec_ptr, std::vector<int2>& rec) {
+                std::vector<int>& rec_ptr, std::vector<int2>& rec, size_t n_terms = 0) {
   struct Chunk {
     std::vector<int> row_len, col, blk_len;
     std::vector<int2> rec;
   };
-  unsigned hw = std::thread::hardware_concurrency();
-  int T = (int)std::min<unsigned>(hw ? hw : 1, 16);
-  if (n < 512) T = 1;
+  HostPool& pool = HostPool::get();
+  int T = std::min(pool.width(), 16);
+  if (n < 128) T = 1;
   std::vector<Chunk> ch(T);
   auto work = [&](int t) {
     const int r0 = (int)((long long)n * t / T), r1 = (int)((long long)n * (t + 1) / T);
     Chunk& c = ch[t];
+    // the chunk's share of the terms, reserved once (growth by doubling
+    // copies the terms again and touches fresh pages each time)
+    if (n_terms) c.rec.reserve((size_t)((double)n_terms * (r1 - r0) / n * 1.05) + 256);
+    c.blk_len.reserve((size_t)(r1 - r0) * 8);
+    c.col.reserve((size_t)(r1 - r0) * 8);
     std::vector<int> slot(std::max(ncols, 1), -1), cols, cnt, fill, td;
     std::vector<int2> tv;
     for (int u = r0; u < r1; ++u) {
@@ -142,26 +223,28 @@ void group_rows(int n, int ncols, Gen gen, Diag diag_col, std::vector<int>& row_
       cols.clear();
     }
   };
-  if (T == 1) {
-    work(0);
-  } else {
-    std::vector<std::thread> th;
-    for (int t = 0; t < T; ++t) th.emplace_back(work, t);
-    for (auto& x : th) x.join();
-  }
+  pool.run(T, work);
+  // concatenate in chunk order; the first chunk's arrays are moved, not copied
   row_ptr.assign(n + 1, 0);
-  col.clear();
-  rec_ptr.assign(1, 0);
-  rec.clear();
+  size_t nblk = 0;
+  for (const Chunk& c : ch) nblk += c.blk_len.size();
+  rec_ptr.clear();
+  rec_ptr.reserve(nblk + 1);
+  rec_ptr.push_back(0);
+  col = std::move(ch[0].col);
+  rec = std::move(ch[0].rec);
   int u = 0;
-  for (const Chunk& c : ch) {
+  for (int t = 0; t < T; ++t) {
+    const Chunk& c = ch[t];
     for (int len : c.row_len) {
       row_ptr[u + 1] = row_ptr[u] + len;
       ++u;
     }
-    col.insert(col.end(), c.col.begin(), c.col.end());
     for (int len : c.blk_len) rec_ptr.push_back(rec_ptr.back() + len);
-    rec.insert(rec.end(), c.rec.begin(), c.rec.end());
+    if (t > 0) {
+      col.insert(col.end(), c.col.begin(), c.col.end());
+      rec.insert(rec.end(), c.rec.begin(), c.rec.end());
+    }
   }
 }
 
@@ -171,6 +254,8 @@ void group_rows(int n, int ncols, Gen gen, Diag diag_col, std::vector<int>& row_
 void build_level(HostLevel& L, const NbrView& nb, HostLevel& next, bool dense) {
   const int n = L.n, nn = L.n_next;
   // ---- P pattern (the aggregates of the node and of its neighbours) and R1 ----
+  size_t n_nb = 0;   // neighbour terms over all rows (an upper bound of R1)
+  for (int u = 0; u < n; ++u) nb.each(u, [&](int, int) { ++n_nb; });
   group_rows(
       n, nn,
       [&](int u, auto emit) {
@@ -179,7 +264,7 @@ void build_level(HostLevel& L, const NbrView& nb, HostLevel& next, bool dense) {
           if (L.agg[w] >= 0) emit(L.agg[w], a, w);
         });
       },
-      [&](int u) { return L.agg[u]; }, L.p_ptr, L.p_col, L.r1_ptr, L.r1);
+      [&](int u) { return L.agg[u]; }, L.p_ptr, L.p_col, L.r1_ptr, L.r1, n_nb);
   const int nnz_p = L.p_ptr[n];
   L.p_row.resize(nnz_p);
   for (int u = 0; u < n; ++u)
@@ -200,6 +285,9 @@ void build_level(HostLevel& L, const NbrView& nb, HostLevel& next, bool dense) {
       }
   }
   // ---- AP pattern and R2: AP_ud = sum_w A_uw P_wd ----
+  size_t n_r2 = 0;   // terms of R2: |P row w| per neighbour w of every row
+  for (int u = 0; u < n; ++u)
+    if (L.agg[u] >= 0) nb.each(u, [&](int, int w) { n_r2 += (size_t)(L.p_ptr[w + 1] - L.p_ptr[w]); });
   group_rows(
       n, nn,
       [&](int u, auto emit) {
@@ -208,7 +296,7 @@ void build_level(HostLevel& L, const NbrView& nb, HostLevel& next, bool dense) {
           for (int k = L.p_ptr[w]; k < L.p_ptr[w + 1]; ++k) emit(L.p_col[k], a, k);
         });
       },
-      [](int) { return -1; }, L.ap_ptr, L.ap_col, L.r2_ptr, L.r2);
+      [](int) { return -1; }, L.ap_ptr, L.ap_col, L.r2_ptr, L.r2, n_r2);
   if (dense) {
     // Q = (I - D^-1 A / rho) P lives in the pattern of A P, which contains
     // that of P (A has every diagonal block): the row of each block, the P
@@ -240,6 +328,8 @@ void build_level(HostLevel& L, const NbrView& nb, HostLevel& next, bool dense) {
   // ---- next level: upper half of P^T A P from the products, R3 per upper block ----
   std::vector<int> up_ptr, up_col, up_r3ptr;
   std::vector<int2> up_r3;
+  size_t n_r3 = 0;   // an upper bound of R3: the whole A P row per P^T entry
+  for (int t = 0; t < L.pt_ptr[nn]; ++t) n_r3 += (size_t)(L.ap_ptr[L.pt_row[t] + 1] - L.ap_ptr[L.pt_row[t]]);
   group_rows(
       nn, nn,
       [&](int c, auto emit) {
@@ -249,7 +339,7 @@ void build_level(HostLevel& L, const NbrView& nb, HostLevel& next, bool dense) {
             if (L.ap_col[k] >= c) emit(L.ap_col[k], pb, k);
         }
       },
-      [](int c) { return c; }, up_ptr, up_col, up_r3ptr, up_r3);
+      [](int c) { return c; }, up_ptr, up_col, up_r3ptr, up_r3, n_r3 / 2 + n_r3 / 8);
   // lower half by transposition (rows ascending, so each row's lower columns are ascending)
   std::vector<int> lo_ptr(nn + 1, 0);
   for (int c = 0; c < nn; ++c)
