@@ -515,8 +515,18 @@ void layout(Uploader& U, std::vector<HostLevel>& H, int L, int N, const std::vec
 
 }  // namespace
 
-AmgHost* amg_build(int N, int nseg, const int* seg_v0, const int* seg_nv, const int* seg_fixed, const int* inc_ptr,
-                   const int* inc_code, const int* inc_other, cudaStream_t s, const char** err) {
+// Host analysis of a hierarchy (no CUDA call): the levels' patterns and
+// recipes, ready for amg_upload.
+struct AmgPlan {
+  std::vector<HostLevel> H;
+  int L = 0, N = 0, nseg = 0;
+  std::vector<int> seg_off;
+};
+
+void amg_plan_free(AmgPlan* P) { delete P; }
+
+AmgPlan* amg_analyze(int N, int nseg, const int* seg_v0, const int* seg_nv, const int* seg_fixed, const int* inc_ptr,
+                     const int* inc_code, const int* inc_other, const char** err) {
   *err = nullptr;
   // Segments are independent graphs on consecutive vertex ranges (one for a
   // single graph; one per graph of a batch): aggregates never cross a
@@ -599,6 +609,22 @@ AmgHost* amg_build(int N, int nseg, const int* seg_v0, const int* seg_nv, const 
     }
     nxt.n_next = base;
   }
+  AmgPlan* P = new AmgPlan();
+  P->H = std::move(H);
+  P->L = L;
+  P->N = N;
+  P->nseg = nseg;
+  P->seg_off = std::move(seg_off);
+  return P;
+}
+
+// Device allocation and upload of an analysed hierarchy (the plan's host
+// arrays must live until this returns; it synchronises the stream).
+AmgHost* amg_upload(AmgPlan* P, cudaStream_t s, const char** err) {
+  *err = nullptr;
+  std::vector<HostLevel>& H = P->H;
+  const int L = P->L, N = P->N, nseg = P->nseg;
+  const std::vector<int>& seg_off = P->seg_off;
   AmgHost* A = new AmgHost();
   Uploader meas;
   layout(meas, H, L, N, seg_off, nseg, A->h);
@@ -623,6 +649,15 @@ AmgHost* amg_build(int N, int nseg, const int* seg_v0, const int* seg_nv, const 
     amg_free(A);
     return nullptr;
   }
+  return A;
+}
+
+AmgHost* amg_build(int N, int nseg, const int* seg_v0, const int* seg_nv, const int* seg_fixed, const int* inc_ptr,
+                   const int* inc_code, const int* inc_other, cudaStream_t s, const char** err) {
+  AmgPlan* P = amg_analyze(N, nseg, seg_v0, seg_nv, seg_fixed, inc_ptr, inc_code, inc_other, err);
+  if (!P) return nullptr;
+  AmgHost* A = amg_upload(P, s, err);
+  amg_plan_free(P);
   return A;
 }
 

@@ -15,7 +15,9 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <future>
 #include <map>
+#include <mutex>
 #include <numeric>
 #include <string>
 #include <vector>
@@ -124,6 +126,37 @@ namespace pgo {
 void set_last_error(const char* msg) { g_last_error = msg; }
 }  // namespace pgo
 
+// Small pinned host buffers (a graph's solver-state and options staging),
+// recycled across graphs for the life of the process: a cudaMallocHost /
+// cudaFreeHost pair per graph costs more than the rest of creating a small
+// graph.
+static std::mutex g_pinned_mu;
+static std::map<size_t, std::vector<void*>> g_pinned_free;
+
+static void* pinned_get(size_t bytes) {
+  {
+    std::lock_guard<std::mutex> lk(g_pinned_mu);
+    auto& v = g_pinned_free[bytes];
+    if (!v.empty()) {
+      void* p = v.back();
+      v.pop_back();
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+static void pinned_put(void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lk(g_pinned_mu);
+  g_pinned_free[bytes].push_back(p);
+}
+
 struct pgo_graph {
   int N = 0, E = 0, fixed = 0;
   cudaStream_t stream = nullptr;
@@ -141,9 +174,13 @@ struct pgo_graph {
   bool solved = false;
   bool has_info = false;
   bool lin_valid = false;
-  // multigrid hierarchy, analysed at the first solve that uses it
+  // multigrid hierarchy: its host analysis starts on a host thread at
+  // creation (it needs only the incidence lists), the upload happens at the
+  // first solve that uses it
   AmgHost* amg = nullptr;
   bool amg_failed = false;
+  std::future<AmgPlan*> amg_plan;
+  const char* amg_plan_err = nullptr;
   // direct block Cholesky structure, analysed at the first solve that asks for it
   DirectHost* direct = nullptr;
   bool direct_failed = false;
@@ -301,9 +338,18 @@ pgo_status ensure_amg(pgo_graph* G, int precond) {
     return PGO_OK;
   }
   const char* err = nullptr;
-  const int v0 = 0, nv = G->N, fx = G->fixed;
-  G->amg = amg_build(G->N, 1, &v0, &nv, &fx, G->h_inc_ptr.data(), G->h_inc_code.data(), G->h_inc_other.data(),
-                     G->stream, &err);
+  if (G->amg_plan.valid()) {
+    AmgPlan* P = G->amg_plan.get();   // waits for the analysis started at creation
+    err = G->amg_plan_err;
+    if (P) {
+      G->amg = amg_upload(P, G->stream, &err);
+      amg_plan_free(P);
+    }
+  } else {
+    const int v0 = 0, nv = G->N, fx = G->fixed;
+    G->amg = amg_build(G->N, 1, &v0, &nv, &fx, G->h_inc_ptr.data(), G->h_inc_code.data(), G->h_inc_other.data(),
+                       G->stream, &err);
+  }
   if (!G->amg) return fail(PGO_ERR_OOM, "multigrid set-up: %s", err ? err : "unknown error");
   G->g.amg = amg_device_desc(G->amg);
   return PGO_OK;
@@ -545,7 +591,7 @@ pgo_status pgo_default_options(pgo_solve_options* opt) {
   return PGO_OK;
 }
 
-pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
+static pgo_status graph_create(const pgo_graph_desc* d, pgo_graph** out, bool analyse_early) {
   if (!out) return fail(PGO_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!d) return fail(PGO_ERR_INVALID_ARG, "desc is NULL");
@@ -642,6 +688,20 @@ pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
   G->h_inc_ptr = inc_ptr;
   G->h_inc_code = inc_code;
   G->h_inc_other = inc_other;
+  if (analyse_early && N >= 2) {
+    // the multigrid analysis (the default preconditioner) runs beside the
+    // allocations and uploads below and whatever the caller does before its
+    // first solve; the graph owns the incidence arrays it reads
+    const int fx = d->fixed_vertex;
+    const int* ip = G->h_inc_ptr.data();
+    const int* ic = G->h_inc_code.data();
+    const int* io = G->h_inc_other.data();
+    const char** perr = &G->amg_plan_err;
+    G->amg_plan = std::async(std::launch::async, [=]() {
+      const int v0 = 0, nv = N, f = fx;
+      return amg_analyze(N, 1, &v0, &nv, &f, ip, ic, io, perr);
+    });
+  }
   G->fixed = d->fixed_vertex;
   G->stream = (cudaStream_t)d->stream;
   G->has_info = d->info != nullptr;
@@ -729,8 +789,8 @@ pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
   cudaStream_t s = G->stream;
   if (cudaStreamCreateWithFlags(&G->cap_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreate(&G->ev0) != cudaSuccess || cudaEventCreate(&G->ev1) != cudaSuccess ||
-      cudaMallocHost(&G->h_state, sizeof(SolverState)) != cudaSuccess ||
-      cudaMallocHost(&G->h_opt, sizeof(DevOptions)) != cudaSuccess)
+      !(G->h_state = static_cast<SolverState*>(pinned_get(sizeof(SolverState)))) ||
+      !(G->h_opt = static_cast<DevOptions*>(pinned_get(sizeof(DevOptions)))))
     return cleanup(fail(PGO_ERR_CUDA, "creating streams/events/pinned buffers failed"));
   bool ok = true;
   ok &= cudaMemsetAsync(A.base, 0, A.used, s) == cudaSuccess;
@@ -767,15 +827,18 @@ pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) {
   return PGO_OK;
 }
 
+pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) { return graph_create(d, out, true); }
+
 void pgo_graph_destroy(pgo_graph* G) {
   if (!G) return;
+  if (G->amg_plan.valid()) amg_plan_free(G->amg_plan.get());
   if (G->stream || G->arena.base) cudaStreamSynchronize(G->stream);
   for (auto& kv : G->execs) cudaGraphExecDestroy(kv.second);
   if (G->cap_stream) cudaStreamDestroy(G->cap_stream);
   if (G->ev0) cudaEventDestroy(G->ev0);
   if (G->ev1) cudaEventDestroy(G->ev1);
-  if (G->h_state) cudaFreeHost(G->h_state);
-  if (G->h_opt) cudaFreeHost(G->h_opt);
+  pinned_put(G->h_state, sizeof(SolverState));
+  pinned_put(G->h_opt, sizeof(DevOptions));
   if (G->arena.base) cudaFree(G->arena.base);
   amg_free(G->amg);
   direct_free(G->direct);
@@ -1315,7 +1378,7 @@ pgo_status pgo_batch_create(int32_t n_graphs, const pgo_graph_desc* descs, void*
   big.poses = poses.data();
   big.stream = stream;
   pgo_graph* G = nullptr;
-  pgo_status st = pgo_graph_create(&big, &G);
+  pgo_status st = graph_create(&big, &G, false);
   if (st != PGO_OK) return st;
   pgo_batch* B = new pgo_batch();
   B->G = G;

@@ -252,6 +252,13 @@ cudaError_t launch_amg_setup(const DevGraph& g, const AmgDev& amg, int mixed, in
 // Symbolic multigrid hierarchy of a graph (host analysis + one device
 // allocation); returns the host copy of the device descriptor.
 struct AmgHost;
+// The same in two steps: the host analysis (no CUDA call; may run on another
+// host thread) and the device allocation and upload.
+struct AmgPlan;
+AmgPlan* amg_analyze(int N, int nseg, const int* seg_v0, const int* seg_nv, const int* seg_fixed, const int* inc_ptr,
+                     const int* inc_code, const int* inc_other, const char** err);
+AmgHost* amg_upload(AmgPlan* P, cudaStream_t s, const char** err);
+void amg_plan_free(AmgPlan* P);
 AmgHost* amg_build(int N, int nseg, const int* seg_v0, const int* seg_nv, const int* seg_fixed, const int* inc_ptr,
                    const int* inc_code, const int* inc_other, cudaStream_t s, const char** err);
 void amg_free(AmgHost* h);
