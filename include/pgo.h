@@ -267,6 +267,40 @@ pgo_status pgo_graph_report(pgo_graph* g, pgo_report* report);
 pgo_status pgo_graph_multigrid_info(pgo_graph* g, int32_t* n_levels, int32_t* nodes, int64_t* a_blocks,
                                     int64_t* p_blocks, int64_t* ap_blocks);
 
+/* Arrays of the multigrid hierarchy (pgo_graph_multigrid_export). */
+typedef enum {
+  PGO_MG_A_PTR = 0,   /* levels >= 1: Galerkin operator P^T A P, block-CSR row pointers (n + 1, int32) */
+  PGO_MG_A_COL = 1,   /*   its block columns, full rows with the diagonal first (int32) */
+  PGO_MG_A = 2,       /*   its blocks */
+  PGO_MG_P_PTR = 3,   /* levels < L: smoothed prolongation P (n x n_next), row pointers (int32) */
+  PGO_MG_P_COL = 4,   /*   its block columns (int32) */
+  PGO_MG_P = 5,       /*   its blocks */
+  PGO_MG_AP_PTR = 6,  /* levels < L: pattern of A P, row pointers (int32) */
+  PGO_MG_AP_COL = 7,  /*   its block columns (int32) */
+  PGO_MG_Q = 8,       /* levels < L: Q = (I - D^-1 A / rho) P in the pattern of A P */
+  PGO_MG_DINV = 9,    /* every level: D^-1 per node (level 0: (H_vv + lambda I)^-1, zero at the gauge vertex) */
+  PGO_MG_T = 10,      /* levels < L: tentative prolongation block per node */
+  PGO_MG_AGG = 11,    /* levels < L: next-level node of each node, -1 for the gauge vertex (int32) */
+  PGO_MG_RHO = 12,    /* levels < L: the rho(D^-1 A) that P (4 / (3 rho)) and Q (1 / rho) use (1 value) */
+  PGO_MG_W = 13       /* level L - 1: dense W = Q C^-1 Q^T, n x n blocks, block (v, u) at v n + u */
+} pgo_mg_array;
+
+/* Copies array `which` (pgo_mg_array) of level `level` of the graph's
+ * multigrid hierarchy, as left by its last numeric set-up in `precision`
+ * (PGO_FP64 or PGO_MIXED, the FP32 set-up), to the host buffer dst of
+ * `capacity` bytes.  *count (nullable) receives the array's element count;
+ * dst NULL only queries it.  Integer arrays are int32; numeric arrays are
+ * float64, a 7x7 block as 49 row-major values.  L is the coarsest level
+ * (pgo_graph_multigrid_info's n_levels - 1).  Test and introspection only
+ * (no counterpart in the paper): it lets a test check the set-up's products
+ * (Sec. IV-F's damped system, preconditioned) against a plain construction.
+ * PGO_ERR_STATE if the hierarchy has not been set up in that precision
+ * (a multigrid solve, damped step or pgo_graph_precondition does it);
+ * PGO_ERR_INVALID_ARG for an array the level does not have or a buffer
+ * smaller than the array.  Synchronises the graph's stream. */
+pgo_status pgo_graph_multigrid_export(pgo_graph* g, int32_t level, int32_t which, int32_t precision, void* dst,
+                                      int64_t capacity, int64_t* count);
+
 /* Run Levenberg-Marquardt from the current estimate (Sec. IV-F, Sec. VI) and
  * keep the result as the new current estimate.  opt NULL = defaults.
  * report (host, nullable) is filled after synchronising.  poses_out

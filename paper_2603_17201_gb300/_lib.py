@@ -39,7 +39,7 @@ EXPORTED = [
     "pgo_graph_set_poses", "pgo_graph_set_measurements", "pgo_graph_get_poses", "pgo_graph_cost", "pgo_graph_linearize",
     "pgo_graph_damped_step", "pgo_graph_resolve", "pgo_graph_report", "pgo_solve", "pgo_backward", "pgo_batch_create", "pgo_batch_destroy",
     "pgo_batch_solve", "pgo_batch_schedule", "pgo_evaluate_cost", "pgo_evaluate_cost_noalloc",
-    "pgo_graph_multigrid_info", "pgo_graph_precondition", "pgo_propagate_correction", "pgo_correct_points",
+    "pgo_graph_multigrid_info", "pgo_graph_multigrid_export", "pgo_graph_precondition", "pgo_propagate_correction", "pgo_correct_points",
     "pgo_frames_create", "pgo_frames_destroy", "pgo_project_match",
 ]
 
@@ -140,6 +140,8 @@ def load(build_if_missing: bool = True):
                                           vp, vp, vp]
         lib.pgo_graph_precondition.argtypes = [vp, ctypes.POINTER(SolveOptions), c_double]
         lib.pgo_graph_multigrid_info.argtypes = [vp, ctypes.POINTER(c_int32), vp, vp, vp, vp]
+        lib.pgo_graph_multigrid_export.argtypes = [vp, c_int32, c_int32, c_int32, vp, ctypes.c_int64,
+                                                   ctypes.POINTER(ctypes.c_int64)]
         lib.pgo_solve.argtypes = [vp, ctypes.POINTER(SolveOptions), ctypes.POINTER(Report), vp, c_int32]
         lib.pgo_backward.argtypes = [vp, ctypes.POINTER(SolveOptions), vp, c_int32, vp, vp, c_int32]
         lib.pgo_batch_create.argtypes = [c_int32, ctypes.POINTER(GraphDesc), vp, ctypes.POINTER(vp)]
@@ -180,3 +182,9 @@ def default_options(**overrides) -> SolveOptions:
             raise TypeError(f"unknown solve option {k!r}")
         setattr(o, k, v)
     return o
+
+
+# pgo_mg_array codes of pgo_graph_multigrid_export (integer arrays first)
+MG_ARRAYS = {"a_ptr": 0, "a_col": 1, "a": 2, "p_ptr": 3, "p_col": 4, "p": 5, "ap_ptr": 6, "ap_col": 7, "q": 8,
+             "dinv": 9, "t": 10, "agg": 11, "rho": 12, "w": 13}
+MG_INT_ARRAYS = {"a_ptr", "a_col", "p_ptr", "p_col", "ap_ptr", "ap_col", "agg"}

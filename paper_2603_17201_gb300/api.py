@@ -265,6 +265,22 @@ class PoseGraph:
         return [dict(nodes=int(nodes[k]), a_blocks=int(a[k]), p_blocks=int(p[k]), ap_blocks=int(ap[k]))
                 for k in range(n.value)]
 
+    def multigrid_export(self, level, name, precision="fp64"):
+        """One array of the multigrid hierarchy's last set-up in `precision`
+        (pgo_graph_multigrid_export): int32 arrays for patterns and
+        aggregates, float64 otherwise (7x7 blocks as (n, 7, 7))."""
+        which = L.MG_ARRAYS[name]
+        prec = L.PGO_MIXED if str(precision).lower() == "mixed" else L.PGO_FP64
+        cnt = ctypes.c_int64()
+        L.check(self._lib.pgo_graph_multigrid_export(self._h, int(level), which, prec, None, 0, ctypes.byref(cnt)))
+        is_int = name in L.MG_INT_ARRAYS
+        out = np.zeros(cnt.value, np.int32 if is_int else np.float64)
+        L.check(self._lib.pgo_graph_multigrid_export(self._h, int(level), which, prec, ctypes.c_void_p(out.ctypes.data),
+                                                     out.nbytes, ctypes.byref(cnt)))
+        if not is_int and name != "rho":
+            out = out.reshape(-1, 7, 7)
+        return out
+
     def solve_report(self):
         """Report of the last solve (synchronises the graph's stream)."""
         rep = L.Report()

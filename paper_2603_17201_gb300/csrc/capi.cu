@@ -1149,6 +1149,83 @@ pgo_status pgo_graph_multigrid_info(pgo_graph* G, int32_t* n_levels, int32_t* no
   return PGO_OK;
 }
 
+pgo_status pgo_graph_multigrid_export(pgo_graph* G, int32_t level, int32_t which, int32_t precision, void* dst,
+                                      int64_t capacity, int64_t* count) {
+  if (!G) return fail(PGO_ERR_INVALID_ARG, "graph is NULL");
+  if (precision != PGO_FP64 && precision != PGO_MIXED) return fail(PGO_ERR_INVALID_ARG, "bad precision");
+  if (!G->amg) return fail(PGO_ERR_STATE, "no multigrid hierarchy: run a multigrid solve or set-up first");
+  const AmgDev* D = amg_host_desc(G->amg);
+  if (level < 0 || level > D->L) return fail(PGO_ERR_INVALID_ARG, "level %d out of range [0, %d]", level, D->L);
+  const bool f64 = precision == PGO_FP64;
+  cudaStream_t s = G->stream;
+  int warm = 0;
+  CUDA_TRY(cudaMemcpyAsync(&warm, D->warm + (f64 ? 0 : 1), sizeof(int), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  if (!warm) return fail(PGO_ERR_STATE, "the hierarchy has not been set up in this precision");
+  const AmgLevel& a = D->lv[level];
+  const bool below = level < D->L;
+  const int* ints = nullptr;   // integer array on the device
+  const void* blocks = nullptr; // block array on the device (FP64 or FP32, padded)
+  const double* dbl = nullptr;  // plain doubles on the device
+  int64_t n = 0;                // integers, blocks or doubles
+  switch (which) {
+    case PGO_MG_A_PTR: if (level >= 1) { ints = a.a_ptr; n = a.n + 1; } break;
+    case PGO_MG_A_COL: if (level >= 1) { ints = a.a_col; n = a.nnz_a; } break;
+    case PGO_MG_A: if (level >= 1) { blocks = f64 ? (const void*)a.a64 : (const void*)a.a32; n = a.nnz_a; } break;
+    case PGO_MG_P_PTR: if (below) { ints = a.p_ptr; n = a.n + 1; } break;
+    case PGO_MG_P_COL: if (below) { ints = a.p_col; n = a.nnz_p; } break;
+    case PGO_MG_P: if (below) { blocks = f64 ? (const void*)a.p64 : (const void*)a.p32; n = a.nnz_p; } break;
+    case PGO_MG_AP_PTR: if (below) { ints = a.ap_ptr; n = a.n + 1; } break;
+    case PGO_MG_AP_COL: if (below) { ints = a.ap_col; n = a.nnz_ap; } break;
+    case PGO_MG_Q: if (below && D->dense) { blocks = f64 ? (const void*)a.q64 : (const void*)a.q32; n = a.nnz_ap; } break;
+    case PGO_MG_DINV:
+      if (level == 0) blocks = f64 ? (const void*)G->g.minv64 : (const void*)G->g.minv32;
+      else if (below) blocks = f64 ? (const void*)a.dinv64 : (const void*)a.dinv32;
+      n = a.n;
+      break;
+    case PGO_MG_T: if (below) { blocks = f64 ? (const void*)a.t64 : (const void*)a.t32; n = a.n; } break;
+    case PGO_MG_AGG: if (below) { ints = a.agg; n = a.n; } break;
+    case PGO_MG_RHO: if (below) { dbl = D->rho + level; n = 1; } break;
+    case PGO_MG_W:
+      if (D->dense && level == D->L - 1) {
+        blocks = f64 ? (const void*)D->w64 : (const void*)D->w32;
+        n = (int64_t)a.n * a.n;
+      }
+      break;
+    default: return fail(PGO_ERR_INVALID_ARG, "unknown array %d", which);
+  }
+  if (!ints && !blocks && !dbl) return fail(PGO_ERR_INVALID_ARG, "level %d has no array %d", level, which);
+  if (n < 0) return fail(PGO_ERR_INVALID_ARG, "level %d: array %d has a negative size", level, which);
+  const int64_t elems = blocks ? n * 49 : n;
+  const int64_t esize = ints ? (int64_t)sizeof(int32_t) : (int64_t)sizeof(double);
+  if (count) *count = elems;
+  if (!dst) return PGO_OK;
+  if (capacity < elems * esize) return fail(PGO_ERR_INVALID_ARG, "buffer of %lld bytes, the array needs %lld",
+                                            (long long)capacity, (long long)(elems * esize));
+  if (elems == 0) return PGO_OK;
+  if (ints) {
+    CUDA_TRY(cudaMemcpyAsync(dst, ints, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return PGO_OK;
+  }
+  if (dbl) {
+    CUDA_TRY(cudaMemcpyAsync(dst, dbl, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return PGO_OK;
+  }
+  // padded blocks: copy, then repack to 49 values per block as double
+  const size_t stride = f64 ? sizeof(double) * BLK64 : sizeof(float) * BLK32;
+  std::vector<char> tmp((size_t)n * stride);
+  CUDA_TRY(cudaMemcpyAsync(tmp.data(), blocks, tmp.size(), cudaMemcpyDeviceToHost, s));
+  CUDA_TRY(cudaStreamSynchronize(s));
+  double* out = static_cast<double*>(dst);
+  for (int64_t b = 0; b < n; ++b)
+    for (int k = 0; k < 49; ++k)
+      out[b * 49 + k] = f64 ? reinterpret_cast<const double*>(tmp.data())[b * BLK64 + k]
+                            : (double)reinterpret_cast<const float*>(tmp.data())[b * BLK32 + k];
+  return PGO_OK;
+}
+
 pgo_status pgo_graph_report(pgo_graph* G, pgo_report* report) {
   if (!G || !report) return fail(PGO_ERR_INVALID_ARG, "graph or report is NULL");
   if (!G->solved) return fail(PGO_ERR_STATE, "no solve has run on this graph");
