@@ -62,6 +62,7 @@ struct HostLevel {
   std::vector<int> ap_row, ap_pblk, apt_ptr, apt_row, apt_blk;   // single-graph hierarchies
   std::vector<int> r1_ptr, r2_ptr, r3_ptr;
   std::vector<int2> r1, r2, r3;
+  std::vector<int> ord1, ord2, ord1t, ord2t, ord3;   // output blocks by recipe length, longest first
 };
 
 // Neighbour terms (A reference, node) of row u, the diagonal first.
@@ -248,6 +249,45 @@ void group_rows(int n, int ncols, Gen gen, Diag diag_col, std::vector<int>& row_
   }
 }
 
+// Position `pos` of round k over a list walked `stride` entries per round,
+// forwards in even rounds and backwards in odd ones: with the list sorted
+// longest first, every worker gets a long and a short entry in turn.
+__device__ __forceinline__ int snake(int k, int stride, int pos) {
+  return k * stride + ((k & 1) ? stride - 1 - pos : pos);
+}
+
+// Block indices ordered by recipe length (ptr[b + 1] - ptr[b]), longest
+// first, ties in index order: over the whole list (window 0, a counting
+// sort), or within each window of `window` consecutive blocks, which keeps
+// the blocks of a row near each other (they share the row's operator blocks
+// in L1) while the four blocks a warp takes get similar lengths.
+void order_by_length(const std::vector<int>& ptr, std::vector<int>& ord, int window) {
+  const int nb = (int)ptr.size() - 1;
+  ord.assign(std::max(nb, 0), 0);
+  if (nb <= 0) return;
+  auto len = [&](int b) { return ptr[b + 1] - ptr[b]; };
+  if (window > 0) {
+    for (int b0 = 0; b0 < nb; b0 += window) {
+      const int b1 = std::min(nb, b0 + window);
+      for (int b = b0; b < b1; ++b) {   // stable insertion sort of the window
+        int k = b;
+        while (k > b0 && len(ord[k - 1]) < len(b)) {
+          ord[k] = ord[k - 1];
+          --k;
+        }
+        ord[k] = b;
+      }
+    }
+    return;
+  }
+  int mx = 0;
+  for (int b = 0; b < nb; ++b) mx = std::max(mx, len(b));
+  std::vector<int> pos(mx + 2, 0);
+  for (int b = 0; b < nb; ++b) pos[mx - len(b) + 1]++;
+  for (int k = 0; k <= mx; ++k) pos[k + 1] += pos[k];
+  for (int b = 0; b < nb; ++b) ord[pos[mx - len(b)]++] = b;
+}
+
 // Builds P, AP, the recipes and the pattern of the next level for `L`.
 // Recipe entries of an output block keep a fixed order: neighbours in
 // incidence order, then the blocks of their rows in column order.
@@ -393,6 +433,15 @@ void build_level(HostLevel& L, const NbrView& nb, HostLevel& next, bool dense) {
       L.r3_ptr[b + 1] = (int)L.r3.size();
     }
   }
+  // (measured per phase on 2,000- and 8,000-keyframe graphs: the
+  // eight-lane products of the P and A P phases gain most from windows of
+  // 32, the 64-thread teams and the P^T A P phase, whose mirrored blocks have
+  // no terms, from a full sort)
+  order_by_length(L.r1_ptr, L.ord1, 32);
+  order_by_length(L.r2_ptr, L.ord2, 32);
+  order_by_length(L.r1_ptr, L.ord1t, 0);
+  order_by_length(L.r2_ptr, L.ord2t, 0);
+  order_by_length(L.r3_ptr, L.ord3, 0);
 }
 
 struct Uploader {
@@ -489,6 +538,11 @@ void layout(Uploader& U, std::vector<HostLevel>& H, int L, int N, const std::vec
       a.r2 = U.put(h.r2);
       a.r3_ptr = U.put(h.r3_ptr);
       a.r3 = U.put(h.r3);
+      a.ord1 = U.put(h.ord1);
+      a.ord2 = U.put(h.ord2);
+      a.ord1t = U.put(h.ord1t);
+      a.ord2t = U.put(h.ord2t);
+      a.ord3 = U.put(h.ord3);
     }
   }
   // one dense coarsest inverse per segment (segment s at s * AMG_CMAX^2 blocks)
@@ -1276,9 +1330,11 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
         const float* Tb = Lv.t32;
         float* Pb = Lv.p32;
         const int lane = threadIdx.x & 31, r = lane & 7, gbase = lane & 24;
-        for (int w0 = (gtid >> 5) << 2; w0 < Lv.nnz_p; w0 += (gthreads >> 5) << 2) {
-          const int b = w0 + (lane >> 3);
-          const bool on = b < Lv.nnz_p && r < 7;
+        const int stride = (gthreads >> 5) << 2, pos = ((gtid >> 5) << 2) + (lane >> 3);
+        for (int k = 0; k * stride < Lv.nnz_p; ++k) {
+          const int bi = snake(k, stride, pos);
+          const bool on = bi < Lv.nnz_p && r < 7;
+          const int b = bi < Lv.nnz_p ? __ldg(Lv.ord1 + bi) : 0;
           float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
           int u = 0, c = -1;
           if (on) {
@@ -1303,9 +1359,11 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
       const bool lane_on = t < 49;
       const V* Tb = AV<V>::t(Lv);
       V* Pb = AV<V>::p(Lv);
-      for (int b0 = blockIdx.x * TEAMS; b0 < Lv.nnz_p; b0 += gridDim.x * TEAMS) {
-        const int b = b0 + slot;
-        const bool has = b < Lv.nnz_p;
+      const int stride = gridDim.x * TEAMS, pos = blockIdx.x * TEAMS + slot;
+      for (int k = 0; k * stride < Lv.nnz_p; ++k) {
+        const int bi = snake(k, stride, pos);
+        const bool has = bi < Lv.nnz_p;
+        const int b = has ? __ldg(Lv.ord1t + bi) : 0;
         int u = 0, c = 0;
         if (has && lane_on) {
           u = __ldg(Lv.p_row + b);
@@ -1343,9 +1401,11 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
         float* Qb = Lv.q32;
         const float wl = (float)rho_f[1];
         const int lane = threadIdx.x & 31, r = lane & 7, gbase = lane & 24;
-        for (int w0 = (gtid >> 5) << 2; w0 < Lv.nnz_ap; w0 += (gthreads >> 5) << 2) {
-          const int b = w0 + (lane >> 3);
-          const bool on = b < Lv.nnz_ap && r < 7;
+        const int stride = (gthreads >> 5) << 2, pos = ((gtid >> 5) << 2) + (lane >> 3);
+        for (int k = 0; k * stride < Lv.nnz_ap; ++k) {
+          const int bi = snake(k, stride, pos);
+          const bool on = bi < Lv.nnz_ap && r < 7;
+          const int b = bi < Lv.nnz_ap ? __ldg(Lv.ord2 + bi) : 0;
           float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
           if (on) {
             recipe_row_f32(g, Lv, l, (float)lam, Lv.r2, __ldg(Lv.r2_ptr + b), __ldg(Lv.r2_ptr + b + 1), Pb, r, acc);
@@ -1378,7 +1438,11 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
       const V* Dl = l == 0 ? AV<V>::minv(g) : AV<V>::dinv(Lv);
       V* Qb = AV<V>::q(Lv);
       const V wl = V(rho_f[1]);
-      for (int b = blockIdx.x * TEAMS + slot; b < Lv.nnz_ap; b += gridDim.x * TEAMS) {
+      const int stride = gridDim.x * TEAMS, pos = blockIdx.x * TEAMS + slot;
+      for (int k = 0; k * stride < Lv.nnz_ap; ++k) {
+        const int bi = snake(k, stride, pos);
+        if (bi >= Lv.nnz_ap) continue;
+        const int b = __ldg(Lv.ord2t + bi);
         V drow[7], pv = V(0);
         if (A.dense && lane_on) {
           const int u = __ldg(Lv.ap_row + b), pb = __ldg(Lv.ap_pblk + b);
@@ -1420,9 +1484,11 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
         const float* APb = Lv.ap32;
         float* An = Ln.a32;
         const int lane = threadIdx.x & 31, r = lane & 7;
-        for (int w0 = (gtid >> 5) << 2; w0 < Lv.nnz_next; w0 += (gthreads >> 5) << 2) {
-          const int b = w0 + (lane >> 3);
-          if (b >= Lv.nnz_next || r >= 7) continue;
+        const int stride = (gthreads >> 5) << 2, pos = ((gtid >> 5) << 2) + (lane >> 3);
+        for (int k = 0; k * stride < Lv.nnz_next; ++k) {
+          const int bi = snake(k, stride, pos);
+          if (bi >= Lv.nnz_next || r >= 7) continue;
+          const int b = __ldg(Lv.ord3 + bi);
           const int e0 = __ldg(Lv.r3_ptr + b), e1 = __ldg(Lv.r3_ptr + b + 1);
           if (e0 == e1) continue;   // mirrored block
           float acc[7] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
@@ -1442,8 +1508,11 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
       const V* Pb = AV<V>::p(Lv);
       const V* APb = AV<V>::ap(Lv);
       V* An = AV<V>::a(Ln);
-      for (int b = blockIdx.x * TEAMS + slot; b < Lv.nnz_next; b += gridDim.x * TEAMS) {
-        if (t >= 49) continue;
+      const int stride = gridDim.x * TEAMS, pos = blockIdx.x * TEAMS + slot;
+      for (int k = 0; k * stride < Lv.nnz_next; ++k) {
+        const int bi = snake(k, stride, pos);
+        if (bi >= Lv.nnz_next || t >= 49) continue;
+        const int b = __ldg(Lv.ord3 + bi);
         const int e0 = __ldg(Lv.r3_ptr + b), e1 = __ldg(Lv.r3_ptr + b + 1);
         if (e0 == e1) continue;   // mirrored block
         An[(size_t)b * BLK + i * 7 + j] = recipe_ptq<V>(Lv.r3, e0, e1, Pb, APb, i, j);

@@ -112,6 +112,14 @@ struct AmgLevel {
   const int2* r2;
   const int* r3_ptr;      // per next-level block (upper half): (P block, AP block)
   const int2* r3;
+  // processing order of the output blocks of the P, A P and P^T A P phases:
+  // by recipe length, longest first, so that the blocks that run side by side
+  // (a warp's four, a block's eight teams) have similar lengths
+  const int* ord1;        // P phase, eight lanes per block: sorted in windows of 32 blocks
+  const int* ord2;        // A P phase, eight lanes per block: the same
+  const int* ord1t;       // P and A P phases with 64-thread teams: sorted over the whole list
+  const int* ord2t;
+  const int* ord3;        // P^T A P phase: sorted over the whole list
   // V-cycle vectors (n x VEC): restricted residual, pre-smoothed iterate,
   // vs: the smoothing part f = x + w D^-1 (r - A x) of the single-graph cycle,
   // or the residual after pre-smoothing of the batch cycle; the result
