@@ -232,8 +232,15 @@ void group_rows(int n, int ncols, Gen gen, Diag diag_col, std::vector<int>& row_
   rec_ptr.clear();
   rec_ptr.reserve(nblk + 1);
   rec_ptr.push_back(0);
+  size_t ncol = 0, nrec = 0;
+  for (const Chunk& c : ch) {
+    ncol += c.col.size();
+    nrec += c.rec.size();
+  }
   col = std::move(ch[0].col);
   rec = std::move(ch[0].rec);
+  col.reserve(ncol);   // one reallocation at most, not one per appended chunk
+  rec.reserve(nrec);
   int u = 0;
   for (int t = 0; t < T; ++t) {
     const Chunk& c = ch[t];
@@ -437,11 +444,15 @@ void build_level(HostLevel& L, const NbrView& nb, HostLevel& next, bool dense) {
   // eight-lane products of the P and A P phases gain most from windows of
   // 32, the 64-thread teams and the P^T A P phase, whose mirrored blocks have
   // no terms, from a full sort)
-  order_by_length(L.r1_ptr, L.ord1, 32);
-  order_by_length(L.r2_ptr, L.ord2, 32);
-  order_by_length(L.r1_ptr, L.ord1t, 0);
-  order_by_length(L.r2_ptr, L.ord2t, 0);
-  order_by_length(L.r3_ptr, L.ord3, 0);
+  HostPool::get().run(5, [&](int k) {
+    switch (k) {
+      case 0: order_by_length(L.r1_ptr, L.ord1, 32); break;
+      case 1: order_by_length(L.r2_ptr, L.ord2, 32); break;
+      case 2: order_by_length(L.r1_ptr, L.ord1t, 0); break;
+      case 3: order_by_length(L.r2_ptr, L.ord2t, 0); break;
+      default: order_by_length(L.r3_ptr, L.ord3, 0); break;
+    }
+  });
 }
 
 struct Uploader {
