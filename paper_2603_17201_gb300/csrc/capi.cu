@@ -579,7 +579,7 @@ pgo_status pgo_default_options(pgo_solve_options* opt) {
   opt->lambda_init = 0.0;
   opt->ftol = 1e-14;
   opt->gtol = 1e-13;
-  opt->pcg_tol = 1e-10;
+  opt->pcg_tol = 1e-6;
   opt->pcg_max_iters = 5000;
   opt->refine_steps = 2;
   opt->refine_tol = 1e-6;
@@ -1001,11 +1001,17 @@ pgo_status pgo_graph_damped_step(pgo_graph* G, const pgo_solve_options* opt, dou
 // on noisy, ill-conditioned graphs; the implicit adjoint needs b(x*) ~ 0.  A
 // step that does not lower |b| is halved up to three times before polishing
 // stops.  FP64, host-driven: a few steps with a synchronisation each.
+// The Newton polish and the adjoint solve need accurate steps (they drive
+// b to zero and differentiate through it): their PCG runs to at most this
+// relative residual, whatever the LM's looser pcg_tol.
+constexpr double kExactPcgTol = 1e-10;
+
 static pgo_status run_polish(pgo_graph* G, const pgo_solve_options& o) {
   const DevGraph& g = G->g;
   cudaStream_t s = G->stream;
   fill_dev_options(o, G->h_opt);
   G->h_opt->lambda_fixed = 0.0;
+  G->h_opt->pcg_tol = std::min(o.pcg_tol, kExactPcgTol);
   CUDA_TRY(cudaMemcpyAsync(g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
   auto linearize_here = [&](double* b2, double* gmax) -> pgo_status {
     launch_state_ctl(g, 0, s);
@@ -1318,6 +1324,7 @@ pgo_status pgo_backward(pgo_graph* G, const pgo_solve_options* opt, const double
   }
   fill_dev_options(o, G->h_opt);
   G->h_opt->lambda_fixed = 0.0;
+  G->h_opt->pcg_tol = std::min(o.pcg_tol, kExactPcgTol);
   CUDA_TRY(cudaMemcpyAsync(g.opt, G->h_opt, sizeof(DevOptions), cudaMemcpyHostToDevice, s));
   launch_state_ctl(g, 0, s);          // done = 0, lambda = 0, tickets cleared
   launch_adj_hessian(g, 0, s);        // full-Hessian blocks of every edge
