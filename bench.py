@@ -210,12 +210,21 @@ def host_cores():
         return os.cpu_count()
 
 
-def oracle_reference(g, max_iters):
+def oracle_reference(g, max_iters, poses=False):
     import oracle
     og = oracle.OracleGraph.from_synthetic(g)
     t = time.perf_counter()
     p, rep = og.lm(g.poses_init, max_iters=max_iters)
-    return time.perf_counter() - t, rep
+    dt = time.perf_counter() - t
+    return (dt, rep, p) if poses else (dt, rep)
+
+
+def pose_error_summary(poses, ref):
+    """Max and RMS over vertices of |log(S_gpu S_oracle^-1)|."""
+    import numpy as np
+    import oracle
+    e = oracle.pose_error(poses, ref)
+    return {"max": float(e.max()), "rms": float(np.sqrt(np.mean(e * e)))}
 
 
 def roofline_leg(pg, N, E, stream, flush, torch, reps=5):
@@ -772,6 +781,7 @@ def run_ours(args):
         return ms, its, reps
 
     results = {}
+    final_poses = {}
     clocks = None
     launches = 0
     for precision in ("fp64", "mixed"):
@@ -782,6 +792,7 @@ def run_ours(args):
             barrier()
         if precision == "mixed":
             clocks = cs.summary()
+        final_poses[precision] = pg.get_poses()   # the last timed solve's result (host copy, untimed)
         tot_ms = max_over_ranks(sum(ms), world, dev)
         rep = reps[-1]
         results[precision] = dict(aggregate_replicas(world, E, its, tot_ms, args.steps),
@@ -805,10 +816,11 @@ def run_ours(args):
     # ---- correctness gate: final cost vs the FP64 oracle ----
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        dt, orep = oracle_reference(g, MAX_ITERS)
+        dt, orep, opos = oracle_reference(g, MAX_ITERS, poses=True)
         for precision in ("fp64", "mixed"):
             rel = abs(results[precision]["final_cost"] - orep["final_cost"]) / orep["final_cost"]
             results[precision]["rel_cost_err_vs_oracle"] = rel
+            results[precision]["pose_err_vs_oracle"] = pose_error_summary(final_poses[precision], opos)
         cpu = {"value": E * orep["iterations"] / dt, "unit": UNIT, "cores": 1, "host_cores": host_cores(),
                "kind": "oracle",
                "sample": f"one full LM solve of {args.workload} ({orep['iterations']} iterations, "

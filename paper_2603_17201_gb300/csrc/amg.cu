@@ -53,6 +53,30 @@ struct AmgHost {
 
 namespace {
 
+// Allocator whose value-less construct() leaves trivial elements
+// uninitialised: the recipe arrays (megabytes on large graphs) are filled by
+// the analysis threads in parallel, so zeroing them on resize would be a
+// serial pass over fresh pages.
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <class U>
+  NoInitAlloc(const NoInitAlloc<U>&) {}
+  template <class U>
+  void construct(U* p) noexcept {
+    ::new ((void*)p) U;
+  }
+  template <class U, class... Args>
+  void construct(U* p, Args&&... args) {
+    ::new ((void*)p) U(std::forward<Args>(args)...);
+  }
+};
+using Recipe = std::vector<int2, NoInitAlloc<int2>>;
+
 struct HostLevel {
   int n = 0, n_next = 0;
   std::vector<int> ref, refc, agg;
@@ -61,7 +85,7 @@ struct HostLevel {
   std::vector<int> ap_ptr, ap_col;
   std::vector<int> ap_row, ap_pblk, apt_ptr, apt_row, apt_blk;   // single-graph hierarchies
   std::vector<int> r1_ptr, r2_ptr, r3_ptr;
-  std::vector<int2> r1, r2, r3;
+  Recipe r1, r2, r3;
   std::vector<int> ord1, ord2, ord1t, ord2t, ord3;   // output blocks by recipe length, longest first
 };
 
@@ -170,15 +194,26 @@ class HostPool {
 // result does not depend on the thread count.
 template <class Gen, class Diag>
 void group_rows(int n, int ncols, Gen gen, Diag diag_col, std::vector<int>& row_ptr, std::vector<int>& col,
-                std::vector<int>& rec_ptr, std::vector<int2>& rec, size_t n_terms = 0) {
+                std::vector<int>& rec_ptr, Recipe& rec, size_t n_terms = 0) {
   struct Chunk {
     std::vector<int> row_len, col, blk_len;
-    std::vector<int2> rec;
+    Recipe rec;
   };
   HostPool& pool = HostPool::get();
   int T = std::min(pool.width(), 16);
   if (n < 128) T = 1;
-  std::vector<Chunk> ch(T);
+  // the chunk buffers of the calling thread are kept between calls: their
+  // pages stay mapped, so later products and later graphs do not fault them
+  // in again
+  static thread_local std::vector<Chunk> cache;
+  if ((int)cache.size() < T) cache.resize(T);
+  Chunk* ch = cache.data();
+  for (int t = 0; t < T; ++t) {
+    ch[t].row_len.clear();
+    ch[t].col.clear();
+    ch[t].blk_len.clear();
+    ch[t].rec.clear();
+  }
   auto work = [&](int t) {
     const int r0 = (int)((long long)n * t / T), r1 = (int)((long long)n * (t + 1) / T);
     Chunk& c = ch[t];
@@ -225,35 +260,34 @@ void group_rows(int n, int ncols, Gen gen, Diag diag_col, std::vector<int>& row_
     }
   };
   pool.run(T, work);
-  // concatenate in chunk order; the first chunk's arrays are moved, not copied
-  row_ptr.assign(n + 1, 0);
-  size_t nblk = 0;
-  for (const Chunk& c : ch) nblk += c.blk_len.size();
-  rec_ptr.clear();
-  rec_ptr.reserve(nblk + 1);
-  rec_ptr.push_back(0);
-  size_t ncol = 0, nrec = 0;
-  for (const Chunk& c : ch) {
-    ncol += c.col.size();
-    nrec += c.rec.size();
-  }
-  col = std::move(ch[0].col);
-  rec = std::move(ch[0].rec);
-  col.reserve(ncol);   // one reallocation at most, not one per appended chunk
-  rec.reserve(nrec);
-  int u = 0;
+  // concatenate in chunk order: offsets from the chunk sizes, then every
+  // chunk copies itself into place on its own thread
+  std::vector<size_t> blk0(T + 1, 0), rec0(T + 1, 0);
   for (int t = 0; t < T; ++t) {
-    const Chunk& c = ch[t];
-    for (int len : c.row_len) {
-      row_ptr[u + 1] = row_ptr[u] + len;
-      ++u;
-    }
-    for (int len : c.blk_len) rec_ptr.push_back(rec_ptr.back() + len);
-    if (t > 0) {
-      col.insert(col.end(), c.col.begin(), c.col.end());
-      rec.insert(rec.end(), c.rec.begin(), c.rec.end());
-    }
+    blk0[t + 1] = blk0[t] + ch[t].blk_len.size();
+    rec0[t + 1] = rec0[t] + ch[t].rec.size();
   }
+  row_ptr.assign(n + 1, 0);
+  col.resize(blk0[T]);
+  rec_ptr.resize(blk0[T] + 1);
+  rec_ptr[0] = 0;
+  rec.resize(rec0[T]);
+  pool.run(T, [&](int t) {
+    const Chunk& c = ch[t];
+    const int r0 = (int)((long long)n * t / T);
+    int nb = (int)blk0[t];
+    for (size_t i = 0; i < c.row_len.size(); ++i) {
+      nb += c.row_len[i];
+      row_ptr[r0 + i + 1] = nb;
+    }
+    int nr = (int)rec0[t];
+    for (size_t k = 0; k < c.blk_len.size(); ++k) {
+      nr += c.blk_len[k];
+      rec_ptr[blk0[t] + k + 1] = nr;
+    }
+    std::copy(c.col.begin(), c.col.end(), col.begin() + blk0[t]);
+    std::copy(c.rec.begin(), c.rec.end(), rec.begin() + rec0[t]);
+  });
 }
 
 // Position `pos` of round k over a list walked `stride` entries per round,
@@ -267,22 +301,28 @@ __device__ __forceinline__ int snake(int k, int stride, int pos) {
 // first, ties in index order: over the whole list (window 0, a counting
 // sort), or within each window of `window` consecutive blocks, which keeps
 // the blocks of a row near each other (they share the row's operator blocks
-// in L1) while the four blocks a warp takes get similar lengths.
-void order_by_length(const std::vector<int>& ptr, std::vector<int>& ord, int window) {
+// in L1) while the four blocks a warp takes get similar lengths.  The
+// windowed form orders windows [w0, w1) of the list only (parts of one list
+// run on several threads); the caller sizes `ord` first.
+void order_by_length(const std::vector<int>& ptr, std::vector<int>& ord, int window, int w0 = 0,
+                     int w1 = 0x7fffffff) {
   const int nb = (int)ptr.size() - 1;
-  ord.assign(std::max(nb, 0), 0);
   if (nb <= 0) return;
   auto len = [&](int b) { return ptr[b + 1] - ptr[b]; };
   if (window > 0) {
-    for (int b0 = 0; b0 < nb; b0 += window) {
+    for (int b0 = w0 * window; b0 < nb && b0 / window < w1; b0 += window) {
       const int b1 = std::min(nb, b0 + window);
+      int key[64];   // window <= 64
       for (int b = b0; b < b1; ++b) {   // stable insertion sort of the window
+        const int lb = len(b);
         int k = b;
-        while (k > b0 && len(ord[k - 1]) < len(b)) {
+        while (k > b0 && key[k - 1 - b0] < lb) {
           ord[k] = ord[k - 1];
+          key[k - b0] = key[k - 1 - b0];
           --k;
         }
         ord[k] = b;
+        key[k - b0] = lb;
       }
     }
     return;
@@ -374,7 +414,7 @@ void build_level(HostLevel& L, const NbrView& nb, HostLevel& next, bool dense) {
   }
   // ---- next level: upper half of P^T A P from the products, R3 per upper block ----
   std::vector<int> up_ptr, up_col, up_r3ptr;
-  std::vector<int2> up_r3;
+  Recipe up_r3;
   size_t n_r3 = 0;   // an upper bound of R3: the whole A P row per P^T entry
   for (int t = 0; t < L.pt_ptr[nn]; ++t) n_r3 += (size_t)(L.ap_ptr[L.pt_row[t] + 1] - L.ap_ptr[L.pt_row[t]]);
   group_rows(
@@ -426,31 +466,39 @@ void build_level(HostLevel& L, const NbrView& nb, HostLevel& next, bool dense) {
       next.a_src[b] = up_blk[lo_src[x]];
     }
   }
-  // R3 per block of the next level: upper blocks carry their entries, lower blocks none
+  // R3 per block of the next level: upper blocks carry their entries, lower
+  // blocks none.  Row c lists the diagonal, its lower blocks, then its upper
+  // columns, and the upper blocks keep their order, so the terms are those of
+  // the upper half in the same sequence: only the pointers change.
   L.r3_ptr.assign(nnz_next + 1, 0);
-  L.r3.clear();
-  L.r3.reserve(up_r3.size());
   for (int c = 0; c < nn; ++c) {
     int k = up_ptr[c];
     for (int b = next.a_ptr[c]; b < next.a_ptr[c + 1]; ++b) {
-      if (next.a_src[b] < 0) {
-        for (int e = up_r3ptr[k]; e < up_r3ptr[k + 1]; ++e) L.r3.push_back(up_r3[e]);
-        ++k;
-      }
-      L.r3_ptr[b + 1] = (int)L.r3.size();
+      if (next.a_src[b] < 0) ++k;
+      L.r3_ptr[b + 1] = up_r3ptr[k];
     }
   }
+  L.r3 = std::move(up_r3);
   // (measured per phase on 2,000- and 8,000-keyframe graphs: the
   // eight-lane products of the P and A P phases gain most from windows of
   // 32, the 64-thread teams and the P^T A P phase, whose mirrored blocks have
   // no terms, from a full sort)
-  HostPool::get().run(5, [&](int k) {
-    switch (k) {
-      case 0: order_by_length(L.r1_ptr, L.ord1, 32); break;
-      case 1: order_by_length(L.r2_ptr, L.ord2, 32); break;
-      case 2: order_by_length(L.r1_ptr, L.ord1t, 0); break;
-      case 3: order_by_length(L.r2_ptr, L.ord2t, 0); break;
-      default: order_by_length(L.r3_ptr, L.ord3, 0); break;
+  // (the windowed sorts in parts of their windows, one job each)
+  constexpr int kWin = 32, kParts = 6;
+  for (std::vector<int>* o : {&L.ord1, &L.ord1t}) o->assign(std::max((int)L.r1_ptr.size() - 1, 0), 0);
+  for (std::vector<int>* o : {&L.ord2, &L.ord2t}) o->assign(std::max((int)L.r2_ptr.size() - 1, 0), 0);
+  L.ord3.assign(std::max((int)L.r3_ptr.size() - 1, 0), 0);
+  const int nw1 = ((int)L.r1_ptr.size() - 1 + kWin - 1) / kWin, nw2 = ((int)L.r2_ptr.size() - 1 + kWin - 1) / kWin;
+  HostPool::get().run(3 + 2 * kParts, [&](int k) {
+    if (k == 0) order_by_length(L.r1_ptr, L.ord1t, 0);
+    else if (k == 1) order_by_length(L.r2_ptr, L.ord2t, 0);
+    else if (k == 2) order_by_length(L.r3_ptr, L.ord3, 0);
+    else if (k < 3 + kParts) {
+      const int p = k - 3;
+      order_by_length(L.r1_ptr, L.ord1, kWin, (int)((long long)nw1 * p / kParts), (int)((long long)nw1 * (p + 1) / kParts));
+    } else {
+      const int p = k - 3 - kParts;
+      order_by_length(L.r2_ptr, L.ord2, kWin, (int)((long long)nw2 * p / kParts), (int)((long long)nw2 * (p + 1) / kParts));
     }
   });
 }
@@ -466,8 +514,8 @@ struct Uploader {
     used += bytes;
     return p;
   }
-  template <class T>
-  const T* put(const std::vector<T>& v) {
+  template <class T, class A>
+  const T* put(const std::vector<T, A>& v) {
     T* p = take<T>(v.size() > 0 ? v.size() : 1);
     if (base && !v.empty()) copies.push_back({p, {v.data(), v.size() * sizeof(T)}});
     return p;

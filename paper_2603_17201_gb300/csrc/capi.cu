@@ -633,14 +633,22 @@ static pgo_status graph_create(const pgo_graph_desc* d, pgo_graph** out, bool an
         return fail(PGO_ERR_INVALID_ARG, "edge %d: information matrix is not symmetric positive definite", e);
   }
 
-  // internal edge order: by (min endpoint, max endpoint, caller index)
+  // internal edge order: by (min endpoint, max endpoint, caller index), as
+  // two stable counting sorts (by the max endpoint, then by the min)
   std::vector<int> perm(E);
-  std::iota(perm.begin(), perm.end(), 0);
-  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) {
-    const int la = std::min(ei[a], ej[a]), lb = std::min(ei[b], ej[b]);
-    if (la != lb) return la < lb;
-    return std::max(ei[a], ej[a]) < std::max(ei[b], ej[b]);
-  });
+  {
+    std::vector<int> tmp(E), cnt((size_t)N + 1);
+    auto pass = [&](const std::vector<int>& src, std::vector<int>& dst, bool by_min) {
+      std::fill(cnt.begin(), cnt.end(), 0);
+      auto key = [&](int e) { return by_min ? std::min(ei[e], ej[e]) : std::max(ei[e], ej[e]); };
+      for (int k = 0; k < E; ++k) cnt[key(src[k]) + 1]++;
+      for (int v = 0; v < N; ++v) cnt[v + 1] += cnt[v];
+      for (int k = 0; k < E; ++k) dst[cnt[key(src[k])]++] = src[k];
+    };
+    std::iota(perm.begin(), perm.end(), 0);
+    pass(perm, tmp, false);
+    pass(tmp, perm, true);
+  }
   std::vector<int> sei(E), sej(E);
   std::vector<D4> zq(E), zt(E);
   std::vector<double> sw(E), szqn(E), sL(d->info ? (size_t)E * 28 : 0);
