@@ -116,7 +116,12 @@ typedef struct {
                              1e-3; pgo_graph_damped_step callers that want
                              an exact step pass a smaller value */
   int32_t pcg_max_iters;  /* PCG iteration cap per linear solve (5000) */
-  int32_t refine_steps;   /* PGO_MIXED: FP64 iterative-refinement passes (2) */
+  int32_t refine_steps;   /* PGO_MIXED: FP64 iterative-refinement passes (2):
+                             the first solves with FP32 PCG to refine_tol;
+                             a later pass whose FP64 residual is within 1000x
+                             of pcg_tol |b| applies one multigrid cycle to it
+                             (block-Jacobi: PCG), a pass further away runs
+                             PCG to the tolerance it needs */
   double refine_tol;      /* PGO_MIXED: inner FP32 PCG relative tolerance (1e-6) */
   int32_t polish_iters;   /* undamped Newton steps after LM on the full
                              Hessian (second-order residual terms included),

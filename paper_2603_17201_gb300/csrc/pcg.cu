@@ -172,6 +172,16 @@ __device__ __forceinline__ void write_partial(S (&v)[K], S* partial, S* sh) {
   __syncthreads();
 }
 
+// Inner tolerance from which a refinement pass of the mixed solve takes one
+// multigrid cycle instead of CG: the FP32 PCG of the first pass leaves an
+// FP64 residual of about 1e-4 of |b| (its own recurrence reaches refine_tol,
+// the true residual carries the FP32 rounding of the products), and an LM
+// step needs no more (the final cost and the LM iteration count were the
+// same for linear tolerances up to 1e-3), so a correction pass whose target
+// is within 1000x of its residual is one cycle; tighter targets (an exact
+// damped step) keep CG.
+constexpr double kOneCycleTol = 1e-3;
+
 struct PcgArgs {
   int from_residual;   // 0: rhs = -b; 1: rhs = res64 (refinement)
   int inner;           // tolerance: 0 -> pcg_tol, 1 -> refine_tol
@@ -784,6 +794,21 @@ __global__ void __launch_bounds__(sizeof(V) == 8 ? 256 : 512) k_pcg(DevGraph g, 
     loc[1] += S(rv) * S(rv);
   }
   if (a.amg && !vcycle_rest<V, S, G>(g, sA, c0, r, q, z, loc[0], counter, abort_flag, target)) goto timeout;
+  if (a.amg && a.from_residual && tol >= kOneCycleTol) {
+    // a correction pass of the mixed refinement whose FP64 residual is within
+    // 1 / kOneCycleTol of the target: one multigrid cycle, x = B r (a
+    // preconditioned Richardson step), instead of CG, whose first iteration
+    // alone applies the cycle twice
+    __syncthreads();
+    for (int v0 = row0; v0 < row1; v0 += nslots) {
+      const int v = v0 + slot;
+      if (v < row1 && act) x[(size_t)v * VEC + c7] = __ldcg(z + (size_t)v * VEC + c7);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      st->pcg_total += 1;
+      st->pcg_iter = 1;
+    }
+  } else {
   write_partial<S, 2>(loc, partial, sh.red);
   if (!grid_sync(counter, abort_flag, target)) goto timeout;
   S rz, bb;
@@ -902,6 +927,7 @@ __global__ void __launch_bounds__(sizeof(V) == 8 ? 256 : 512) k_pcg(DevGraph g, 
       st->pcg_total += it;
       st->pcg_iter = it;
     }
+  }
   }
   // leave the counter at zero for the next launch: the last block to get here
   // resets it (all blocks have passed their last barrier).
