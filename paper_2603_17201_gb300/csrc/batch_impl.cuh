@@ -124,6 +124,17 @@ __device__ int cta_pcg(const DevGraph& g, int v0, int v1, int fixed, double lam,
     }
     __syncthreads();
     cta_vcycle<V, G>(g, *A, sg, fixed, vl, r, q, z);
+    if (from_res && tol >= kOneCycleTol) {
+      // a correction pass within 1 / kOneCycleTol of its target: one cycle,
+      // x = B r, as in the single-graph solver
+      for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
+        const size_t b = (size_t)v * VEC;
+#pragma unroll
+        for (int k = 0; k < 7; ++k) x[b + k] = (v == fixed) ? V(0) : z[b + k];
+      }
+      __syncthreads();
+      return 1;
+    }
     for (int v = v0 + threadIdx.x; v < v1; v += blockDim.x) {
       const size_t b = (size_t)v * VEC;
       V lrz = V(0), lrr = V(0);

@@ -172,15 +172,6 @@ __device__ __forceinline__ void write_partial(S (&v)[K], S* partial, S* sh) {
   __syncthreads();
 }
 
-// Inner tolerance from which a refinement pass of the mixed solve takes one
-// multigrid cycle instead of CG: the FP32 PCG of the first pass leaves an
-// FP64 residual of about 1e-4 of |b| (its own recurrence reaches refine_tol,
-// the true residual carries the FP32 rounding of the products), and an LM
-// step needs no more (the final cost and the LM iteration count were the
-// same for linear tolerances up to 1e-3), so a correction pass whose target
-// is within 1000x of its residual is one cycle; tighter targets (an exact
-// damped step) keep CG.
-constexpr double kOneCycleTol = 1e-3;
 
 struct PcgArgs {
   int from_residual;   // 0: rhs = -b; 1: rhs = res64 (refinement)
