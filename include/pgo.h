@@ -122,7 +122,12 @@ typedef struct {
                              of pcg_tol |b| applies one multigrid cycle to it
                              (block-Jacobi: PCG), a pass further away runs
                              PCG to the tolerance it needs */
-  double refine_tol;      /* PGO_MIXED: inner FP32 PCG relative tolerance (1e-6) */
+  double refine_tol;      /* PGO_MIXED: inner FP32 PCG relative tolerance (1e-5:
+                             on the 2,000- and 4,000-keyframe graphs an inner
+                             solve to 1e-5 left the same FP64 residual, about
+                             7e-6 of |b|, as one to 1e-6, with one iteration
+                             fewer; the FP32 recurrence no longer tracks the
+                             FP64 residual below that) */
   int32_t polish_iters;   /* undamped Newton steps after LM on the full
                              Hessian (second-order residual terms included),
                              each kept only while it lowers |b|_2 (0; use > 0

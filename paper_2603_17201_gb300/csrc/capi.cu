@@ -582,7 +582,7 @@ pgo_status pgo_default_options(pgo_solve_options* opt) {
   opt->pcg_tol = 1e-6;
   opt->pcg_max_iters = 5000;
   opt->refine_steps = 2;
-  opt->refine_tol = 1e-6;
+  opt->refine_tol = 1e-5;
   opt->polish_iters = 0;
   opt->schedule = -1;
   opt->preconditioner = PGO_PRECOND_MULTIGRID;

@@ -64,12 +64,13 @@ constexpr int AMG_MAXL = 12;
 
 // Inner tolerance from which a refinement pass of the mixed solve takes one
 // multigrid cycle instead of CG: the FP32 PCG of the first pass leaves an
-// FP64 residual of about 1e-4 of |b| (its own recurrence reaches refine_tol,
-// the true residual carries the FP32 rounding of the products), and an LM
-// step needs no more (the final cost and the LM iteration count were the
-// same for linear tolerances up to 1e-3), so a correction pass whose target
-// is within 1000x of its residual is one cycle; tighter targets (an exact
-// damped step) keep CG.
+// FP64 residual of 5e-6 to 1e-3 of |b| (its own recurrence reaches
+// refine_tol, the true residual carries the FP32 rounding of the products;
+// the worst at the small damping of the last LM iterations), one cycle
+// lowers it about tenfold, and an LM step needs no more (the final cost and
+// the LM iteration count were the same for linear tolerances up to 1e-3), so
+// a correction pass whose target is within 1000x of its residual is one
+// cycle; tighter targets (an exact damped step) keep CG.
 constexpr double kOneCycleTol = 1e-3;
 
 constexpr int AMG_POWER_ITS = 12;       // first set-up of a graph
