@@ -1282,12 +1282,20 @@ __global__ void __launch_bounds__(SetupShape<V>::THREADS, 1) k_amg_setup(DevGrap
   // ---- tentative prolongation blocks T = Adj(S_ref S_refc^-1), all levels ----
   // one node per thread over the levels' nodes in sequence, node
   // q * gridDim.x + b to block b: each node is a chain of a few hundred
-  // dependent FP64 operations, so no thread takes two and every SM takes some
+  // dependent FP64 operations, so no thread takes two and every SM takes some.
+  // The threads after them form the level-0 smoother blocks
+  // D0^-1 = (H_vv + lambda I)^-1, one vertex each (the block-Jacobi
+  // preconditioner's kernel is not launched before a multigrid set-up).
   {
     const int nlev = lagged ? 1 : A.L;
     int total = 0;
     for (int l = 0; l < nlev; ++l) total += A.lv[l].n;
-    for (int q = threadIdx.x * gridDim.x + blockIdx.x; q < total; q += gthreads) {
+    for (int q = threadIdx.x * gridDim.x + blockIdx.x; q < total + g.N; q += gthreads) {
+      if (q >= total) {
+        const int v = q - total;
+        precond_vertex<V>(g, v, g.fixed, st->lambda, const_cast<V*>(AV<V>::minv(g)) + (size_t)v * BLK);
+        continue;
+      }
       int l = 0, u = q;
       while (u >= A.lv[l].n) {
         u -= A.lv[l].n;

@@ -253,8 +253,10 @@ void enqueue_pcg(const DevGraph& g, int mixed, const AmgDev* amg, int from_resid
   if (e != cudaSuccess && *err == cudaSuccess) *err = e;
 }
 
+// The block-Jacobi blocks (H_vv + lambda I)^-1, or the multigrid set-up,
+// whose first phase forms the same blocks as its level-0 smoother.
 void enqueue_precond(const DevGraph& g, int mixed, const AmgDev* amg, cudaStream_t s, cudaError_t* err, int lm = 0) {
-  launch_precond(g, mixed, s);
+  if (!amg) launch_precond(g, mixed, s);
   if (amg) {
     cudaError_t e = launch_amg_setup(g, *amg, mixed, lm, s);
     if (e != cudaSuccess && *err == cudaSuccess) *err = e;

@@ -50,8 +50,8 @@ def test_aggregate_replicas_and_launch_count():
     assert one["ms_per_solve"] == 100.0 and one["edges_per_s"] == 1000 * 20 / 0.2
     assert two["edges_per_s"] == 2 * one["edges_per_s"]   # weak scaling: twice the work in the same time
     assert bench.max_over_ranks(3.5, 1, "cpu") == 3.5
-    assert bench.launches_per_solve("fp64", 11) == 3 + 11 * 7
-    assert bench.launches_per_solve("mixed", 11) == 3 + 11 * 12
+    assert bench.launches_per_solve("fp64", 11) == 3 + 11 * 6
+    assert bench.launches_per_solve("mixed", 11) == 3 + 11 * 11
 
 
 def test_vcycle_bytes_per_iteration_counts_each_operator_read():
