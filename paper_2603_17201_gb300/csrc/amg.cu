@@ -503,22 +503,58 @@ void build_level(HostLevel& L, const NbrView& nb, HostLevel& next, bool dense) {
   });
 }
 
+// Device arrays of the hierarchy in two regions of one allocation: the
+// arrays uploaded from the host first (put: index lists, recipes), then the
+// ones the device fills (take: blocks, vectors), so that the uploads are one
+// contiguous range.
 struct Uploader {
   char* base = nullptr;
-  size_t used = 0;
-  std::vector<std::pair<void*, std::pair<const void*, size_t>>> copies;
+  size_t put_region = 0;   // bytes of the put region (from a measuring pass)
+  size_t put_used = 0, take_used = 0;
+  std::vector<std::pair<size_t, std::pair<const void*, size_t>>> copies;   // (offset, (host, bytes))
+  static size_t padded(size_t bytes) { return (bytes + 255) & ~size_t(255); }
+  size_t used() const { return std::max(put_region, put_used) + take_used; }   // (a measuring pass has no region yet)
   template <class T>
   T* take(size_t count) {
-    const size_t bytes = (count * sizeof(T) + 255) & ~size_t(255);
-    T* p = reinterpret_cast<T*>(base ? base + used : nullptr);
-    used += bytes;
+    const size_t bytes = padded(count * sizeof(T));
+    T* p = reinterpret_cast<T*>(base ? base + put_region + take_used : nullptr);
+    take_used += bytes;
     return p;
   }
   template <class T, class A>
   const T* put(const std::vector<T, A>& v) {
-    T* p = take<T>(v.size() > 0 ? v.size() : 1);
-    if (base && !v.empty()) copies.push_back({p, {v.data(), v.size() * sizeof(T)}});
+    const size_t count = v.size() > 0 ? v.size() : 1;
+    T* p = reinterpret_cast<T*>(base ? base + put_used : nullptr);
+    if (base && !v.empty()) copies.push_back({put_used, {v.data(), v.size() * sizeof(T)}});
+    put_used += padded(count * sizeof(T));
     return p;
+  }
+};
+
+// Pinned host staging of the hierarchy upload, kept for the life of the
+// process and grown on demand: the put region is packed into it by the
+// analysis worker pool and sent in one copy (one pageable copy per array cost
+// a few microseconds each, over a hundred arrays per graph).
+struct PinnedStage {
+  std::mutex mu;
+  char* p = nullptr;
+  size_t n = 0;
+  static PinnedStage& get() {
+    static PinnedStage* s = new PinnedStage();   // never freed: reused by later graphs
+    return *s;
+  }
+  bool reserve(size_t bytes) {
+    if (bytes <= n) return true;
+    if (p) cudaFreeHost(p);
+    p = nullptr;
+    n = 0;
+    if (cudaHostAlloc(reinterpret_cast<void**>(&p), bytes, cudaHostAllocDefault) != cudaSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+      return false;
+    }
+    n = bytes;
+    return true;
   }
 };
 
@@ -741,7 +777,7 @@ AmgHost* amg_upload(AmgPlan* P, cudaStream_t s, const char** err) {
   AmgHost* A = new AmgHost();
   Uploader meas;
   layout(meas, H, L, N, seg_off, nseg, A->h);
-  A->bytes = meas.used + 256;
+  A->bytes = meas.used() + 256;
   if (cudaMalloc(&A->mem, A->bytes) != cudaSuccess ||
       cudaMalloc(&A->d, sizeof(AmgDev)) != cudaSuccess) {
     cudaGetLastError();
@@ -751,12 +787,39 @@ AmgHost* amg_upload(AmgPlan* P, cudaStream_t s, const char** err) {
   }
   Uploader up;
   up.base = A->mem;
+  up.put_region = meas.put_used;
   layout(up, H, L, N, seg_off, nseg, A->h);
-  bool ok = cudaMemsetAsync(A->mem, 0, up.used, s) == cudaSuccess;
-  for (auto& c : up.copies)
-    ok = ok && cudaMemcpyAsync(c.first, c.second.first, c.second.second, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  const size_t nput = up.put_used;
+  bool ok = cudaMemsetAsync(A->mem, 0, up.used(), s) == cudaSuccess;
+  PinnedStage& stage = PinnedStage::get();
+  std::unique_lock<std::mutex> lk(stage.mu);
+  if (ok && nput > 0 && stage.reserve(nput)) {
+    // pack the put region (arrays at their offsets, the gaps zero as the
+    // memset leaves them), in slices of at most 256 KB over the worker pool
+    std::vector<std::pair<size_t, size_t>> gaps;   // (offset, bytes) not covered by a copy
+    std::vector<std::pair<size_t, std::pair<const char*, size_t>>> slices;
+    size_t at = 0;
+    for (auto& c : up.copies) {
+      if (c.first > at) gaps.push_back({at, c.first - at});
+      const char* src = static_cast<const char*>(c.second.first);
+      for (size_t o = 0; o < c.second.second; o += (size_t)256 << 10)
+        slices.push_back({c.first + o, {src + o, std::min(c.second.second - o, (size_t)256 << 10)}});
+      at = c.first + c.second.second;
+    }
+    if (nput > at) gaps.push_back({at, nput - at});
+    for (auto& gp : gaps) std::memset(stage.p + gp.first, 0, gp.second);
+    HostPool::get().run((int)slices.size(), [&](int k) {
+      std::memcpy(stage.p + slices[k].first, slices[k].second.first, slices[k].second.second);
+    });
+    ok = cudaMemcpyAsync(A->mem, stage.p, nput, cudaMemcpyHostToDevice, s) == cudaSuccess;
+  } else {
+    for (auto& c : up.copies)
+      ok = ok && cudaMemcpyAsync(A->mem + c.first, c.second.first, c.second.second, cudaMemcpyHostToDevice, s) ==
+                     cudaSuccess;
+  }
   ok = ok && cudaMemcpyAsync(A->d, &A->h, sizeof(AmgDev), cudaMemcpyHostToDevice, s) == cudaSuccess;
-  ok = ok && cudaStreamSynchronize(s) == cudaSuccess;   // the host vectors die on return
+  ok = ok && cudaStreamSynchronize(s) == cudaSuccess;   // the host vectors (and the stage) are free again
+  lk.unlock();
   if (!ok) {
     *err = "uploading the multigrid hierarchy failed";
     amg_free(A);
