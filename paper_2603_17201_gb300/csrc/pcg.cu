@@ -172,7 +172,6 @@ __device__ __forceinline__ void write_partial(S (&v)[K], S* partial, S* sh) {
   __syncthreads();
 }
 
-
 struct PcgArgs {
   int from_residual;   // 0: rhs = -b; 1: rhs = res64 (refinement)
   int inner;           // tolerance: 0 -> pcg_tol, 1 -> refine_tol
@@ -799,7 +798,8 @@ __global__ void __launch_bounds__(sizeof(V) == 8 ? 256 : 512) k_pcg(DevGraph g, 
       st->pcg_total += 1;
       st->pcg_iter = 1;
     }
-  } else {
+    goto finish;
+  }
   write_partial<S, 2>(loc, partial, sh.red);
   if (!grid_sync(counter, abort_flag, target)) goto timeout;
   S rz, bb;
@@ -919,7 +919,7 @@ __global__ void __launch_bounds__(sizeof(V) == 8 ? 256 : 512) k_pcg(DevGraph g, 
       st->pcg_iter = it;
     }
   }
-  }
+finish:
   // leave the counter at zero for the next launch: the last block to get here
   // resets it (all blocks have passed their last barrier).
   __syncthreads();
