@@ -256,11 +256,12 @@ void enqueue_pcg(const DevGraph& g, int mixed, const AmgDev* amg, int from_resid
 // The block-Jacobi blocks (H_vv + lambda I)^-1, or the multigrid set-up,
 // whose first phase forms the same blocks as its level-0 smoother.
 void enqueue_precond(const DevGraph& g, int mixed, const AmgDev* amg, cudaStream_t s, cudaError_t* err, int lm = 0) {
-  if (!amg) launch_precond(g, mixed, s);
-  if (amg) {
-    cudaError_t e = launch_amg_setup(g, *amg, mixed, lm, s);
-    if (e != cudaSuccess && *err == cudaSuccess) *err = e;
+  if (!amg) {
+    launch_precond(g, mixed, s);
+    return;
   }
+  cudaError_t e = launch_amg_setup(g, *amg, mixed, lm, s);
+  if (e != cudaSuccess && *err == cudaSuccess) *err = e;
 }
 
 // The linear-solve part of one LM iteration.  PCG: the preconditioner
@@ -1003,6 +1004,11 @@ pgo_status pgo_graph_damped_step(pgo_graph* G, const pgo_solve_options* opt, dou
   return PGO_OK;
 }
 
+// The Newton polish and the adjoint solve need accurate steps (they drive
+// b to zero and differentiate through it): their PCG runs to at most this
+// relative residual, whatever the LM's looser pcg_tol.
+constexpr double kExactPcgTol = 1e-10;
+
 // Newton steps after LM on the full Hessian (second-order residual terms
 // included, the same exact nested-dual Hessian as the adjoint), each kept
 // only while it lowers the gradient norm |b|_2.  LM's cost-based stop cannot
@@ -1011,11 +1017,6 @@ pgo_status pgo_graph_damped_step(pgo_graph* G, const pgo_solve_options* opt, dou
 // on noisy, ill-conditioned graphs; the implicit adjoint needs b(x*) ~ 0.  A
 // step that does not lower |b| is halved up to three times before polishing
 // stops.  FP64, host-driven: a few steps with a synchronisation each.
-// The Newton polish and the adjoint solve need accurate steps (they drive
-// b to zero and differentiate through it): their PCG runs to at most this
-// relative residual, whatever the LM's looser pcg_tol.
-constexpr double kExactPcgTol = 1e-10;
-
 static pgo_status run_polish(pgo_graph* G, const pgo_solve_options& o) {
   const DevGraph& g = G->g;
   cudaStream_t s = G->stream;
