@@ -615,25 +615,13 @@ static pgo_status graph_create(const pgo_graph_desc* d, pgo_graph** out, bool an
   if (d->weight && !fetch(w, d->weight, E, ms)) return fail(PGO_ERR_CUDA, "reading weights failed");
   if (d->info && !fetch(info, d->info, (size_t)E * 49, ms)) return fail(PGO_ERR_CUDA, "reading info failed");
   if (d->poses && !fetch(poses, d->poses, (size_t)N * 8, ms)) return fail(PGO_ERR_CUDA, "reading poses failed");
+  // the endpoints first: the edge order, the incidence lists and the
+  // multigrid analysis need only them, and the analysis then runs beside the
+  // checks of the values below
   for (int e = 0; e < E; ++e) {
     if (ei[e] < 0 || ei[e] >= N || ej[e] < 0 || ej[e] >= N)
       return fail(PGO_ERR_INVALID_ARG, "edge %d: endpoint out of range (%d, %d), n_vertices %d", e, ei[e], ej[e], N);
     if (ei[e] == ej[e]) return fail(PGO_ERR_INVALID_ARG, "edge %d is a self-edge (%d, %d)", e, ei[e], ej[e]);
-    if (!finite_pose(&meas[(size_t)e * 8]))
-      return fail(PGO_ERR_INVALID_ARG, "edge %d: measurement not finite, zero quaternion or scale <= 0", e);
-    if (d->weight && !(std::isfinite(w[e]) && w[e] >= 0.0))
-      return fail(PGO_ERR_INVALID_ARG, "edge %d: weight must be finite and >= 0", e);
-  }
-  if (d->poses)
-    for (int v = 0; v < N; ++v)
-      if (!finite_pose(&poses[(size_t)v * 8]))
-        return fail(PGO_ERR_INVALID_ARG, "vertex %d: pose not finite, zero quaternion or scale <= 0", v);
-  std::vector<double> Lpack;
-  if (d->info) {
-    Lpack.resize((size_t)E * 28);
-    for (int e = 0; e < E; ++e)
-      if (!chol_pack(&info[(size_t)e * 49], &Lpack[(size_t)e * 28]))
-        return fail(PGO_ERR_INVALID_ARG, "edge %d: information matrix is not symmetric positive definite", e);
   }
 
   // internal edge order: by (min endpoint, max endpoint, caller index), as
@@ -653,19 +641,9 @@ static pgo_status graph_create(const pgo_graph_desc* d, pgo_graph** out, bool an
     pass(tmp, perm, true);
   }
   std::vector<int> sei(E), sej(E);
-  std::vector<D4> zq(E), zt(E);
-  std::vector<double> sw(E), szqn(E), sL(d->info ? (size_t)E * 28 : 0);
   for (int k = 0; k < E; ++k) {
-    const int e = perm[k];
-    sei[k] = ei[e];
-    sej[k] = ej[e];
-    const double* m = &meas[(size_t)e * 8];
-    const double n = std::sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2] + m[3] * m[3]);
-    zq[k] = D4{m[0] / n, m[1] / n, m[2] / n, m[3] / n};
-    szqn[k] = n;
-    zt[k] = D4{m[4], m[5], m[6], m[7]};
-    sw[k] = d->weight ? w[e] : 1.0;
-    if (d->info) std::memcpy(&sL[(size_t)k * 28], &Lpack[(size_t)e * 28], sizeof(double) * 28);
+    sei[k] = ei[perm[k]];
+    sej[k] = ej[perm[k]];
   }
   // incidence lists: for each vertex its side-0 entries (vertex is i), then
   // its side-1 entries (vertex is j), each group in edge order
@@ -712,6 +690,42 @@ static pgo_status graph_create(const pgo_graph_desc* d, pgo_graph** out, bool an
       const int v0 = 0, nv = N, f = fx;
       return amg_analyze(N, 1, &v0, &nv, &f, ip, ic, io, perr);
     });
+  }
+  // the values: measurements, weights, poses, information matrices (a
+  // rejected input ends the graph, and with it the analysis started above)
+  auto reject = [&](pgo_status st) {
+    pgo_graph_destroy(G);
+    return st;
+  };
+  for (int e = 0; e < E; ++e) {
+    if (!finite_pose(&meas[(size_t)e * 8]))
+      return reject(fail(PGO_ERR_INVALID_ARG, "edge %d: measurement not finite, zero quaternion or scale <= 0", e));
+    if (d->weight && !(std::isfinite(w[e]) && w[e] >= 0.0))
+      return reject(fail(PGO_ERR_INVALID_ARG, "edge %d: weight must be finite and >= 0", e));
+  }
+  if (d->poses)
+    for (int v = 0; v < N; ++v)
+      if (!finite_pose(&poses[(size_t)v * 8]))
+        return reject(fail(PGO_ERR_INVALID_ARG, "vertex %d: pose not finite, zero quaternion or scale <= 0", v));
+  std::vector<double> Lpack;
+  if (d->info) {
+    Lpack.resize((size_t)E * 28);
+    for (int e = 0; e < E; ++e)
+      if (!chol_pack(&info[(size_t)e * 49], &Lpack[(size_t)e * 28]))
+        return reject(
+            fail(PGO_ERR_INVALID_ARG, "edge %d: information matrix is not symmetric positive definite", e));
+  }
+  std::vector<D4> zq(E), zt(E);
+  std::vector<double> sw(E), szqn(E), sL(d->info ? (size_t)E * 28 : 0);
+  for (int k = 0; k < E; ++k) {
+    const int e = perm[k];
+    const double* m = &meas[(size_t)e * 8];
+    const double n = std::sqrt(m[0] * m[0] + m[1] * m[1] + m[2] * m[2] + m[3] * m[3]);
+    zq[k] = D4{m[0] / n, m[1] / n, m[2] / n, m[3] / n};
+    szqn[k] = n;
+    zt[k] = D4{m[4], m[5], m[6], m[7]};
+    sw[k] = d->weight ? w[e] : 1.0;
+    if (d->info) std::memcpy(&sL[(size_t)k * 28], &Lpack[(size_t)e * 28], sizeof(double) * 28);
   }
   G->fixed = d->fixed_vertex;
   G->stream = (cudaStream_t)d->stream;

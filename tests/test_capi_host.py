@@ -40,7 +40,7 @@ def test_version_and_defaults(lib):
     assert o.pcg_tol == 1e-6 and o.refine_steps >= 1
 
 
-def _desc(n, ei, ej, meas, fixed=0, weight=None):
+def _desc(n, ei, ej, meas, fixed=0, weight=None, poses=None, info=None):
     keep = []
     d = L.GraphDesc()
     d.n_vertices = n
@@ -58,14 +58,23 @@ def _desc(n, ei, ej, meas, fixed=0, weight=None):
         w = np.ascontiguousarray(weight, dtype=np.float64)
         keep.append(w)
         d.weight = w.ctypes.data
+    if poses is not None:
+        p = np.ascontiguousarray(poses, dtype=np.float64)
+        keep.append(p)
+        d.poses = p.ctypes.data
+    if info is not None:
+        om = np.ascontiguousarray(info, dtype=np.float64)
+        keep.append(om)
+        d.info = om.ctypes.data
     return d, keep
 
 
 @pytest.mark.parametrize("case", ["index", "self_edge", "nan_meas", "bad_scale", "zero_quat", "bad_fixed",
-                                  "neg_edges", "neg_weight"])
+                                  "neg_edges", "neg_weight", "nan_pose", "info_not_spd"])
 def test_create_rejects_bad_graphs(lib, case):
     g = syn.make_graph("circle", 20, seed=1)
     ei, ej, meas, fixed, n, w = g.edge_i.copy(), g.edge_j.copy(), g.meas.copy(), 0, g.n_vertices, None
+    poses, info = None, None
     if case == "index":
         ej[3] = n
     elif case == "self_edge":
@@ -81,7 +90,13 @@ def test_create_rejects_bad_graphs(lib, case):
     elif case == "neg_weight":
         w = np.ones(len(ei))
         w[0] = -1.0
-    d, keep = _desc(n, ei, ej, meas, fixed, w)
+    elif case == "nan_pose":
+        poses = g.poses_init.copy()
+        poses[7, 4] = np.inf
+    elif case == "info_not_spd":
+        info = np.tile(np.eye(7), (len(ei), 1, 1))
+        info[6, 3, 3] = -1.0
+    d, keep = _desc(n, ei, ej, meas, fixed, w, poses, info)
     if case == "neg_edges":
         d.n_edges = -1
     h = ctypes.c_void_p()
