@@ -36,10 +36,14 @@ METRIC = "Sim(3) PGO ms/solve & edges/s at rel cost <=1e-6: mixed vs plain FP64,
 UNIT = "edges/s"
 # DRAM bytes (read + write) of one PCG iteration of the roofline kernel,
 # k_pcg<float,float,32> on the bench graph: one ncu capture of the 9-iteration
-# launch of `bench.py --roofline-only` read 21,229,568 B and wrote 19,712 B
+# launch of `bench.py --roofline-only` read 21,231,104 B and wrote 22,272 B
 # (profiles/k_pcg_float_c2_figure8_2k.md), amortised over its 9 iterations.
 # Set to None whenever the kernel changes until it is captured again.
-TRAFFIC_PER_ITERATION = (21229568 + 19712) / 9
+TRAFFIC_PER_ITERATION = (21231104 + 22272) / 9
+# DRAM bytes of one warm FP32 multigrid set-up (k_amg_setup<float>, with the
+# level-0 block-Jacobi blocks), the third set-up of the same command: 19,938,304 B
+# read, 300,544 B written (profiles/k_amg_setup_float_c2_figure8_2k.md).
+TRAFFIC_PER_SETUP = 19938304 + 300544
 
 
 def parse():
@@ -337,7 +341,7 @@ def setup_leg(pg, N, E, stream, flush, torch, reps=7):
     b = setup_bytes(info, N, E, 4)
     peak = peaks.get("hbm_gbs", 6800.0)
     return {"bound": "hbm", "achieved": b / (t * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
-            "frac": b / (t * 1e-3) / 1e9 / peak, "traffic": None,
+            "frac": b / (t * 1e-3) / 1e9 / peak, "traffic": TRAFFIC_PER_SETUP,
             "kernel": "k_amg_setup<float> (FP32 multigrid set-up with the level-0 block-Jacobi blocks, once per LM linearisation)",
             "achieved_kind": "compulsory bytes of the set-up / CUDA-event time",
             "limiter": "latency and instruction issue: grid-barrier phases of 7x7 block products",
