@@ -192,8 +192,15 @@ pgo_status pgo_default_options(pgo_solve_options* opt);
 /* Create a resident device copy of an essential graph (Sec. III-B, IV-E:
  * keep the data on the GPU and allocate once).  Validates the description,
  * sorts edges by endpoint, builds the block-sparse pattern of the normal
- * matrix and allocates every buffer a solve needs.  *out receives a handle
- * owned by the caller (free with pgo_graph_destroy).  On error *out is NULL. */
+ * matrix and allocates every buffer a solve needs.  The host analysis of the
+ * multigrid hierarchy starts on a host thread here (pool threads of the
+ * library, created on first use) and is uploaded by the first multigrid
+ * solve.  *out receives a handle owned by the caller (free with
+ * pgo_graph_destroy).  On error *out is NULL.
+ * Process-wide resources, kept until exit and reused by later graphs: the
+ * analysis worker threads, small pinned host buffers, and one pinned staging
+ * buffer for hierarchy uploads as large as the largest hierarchy's index
+ * lists and recipes so far (about 10 MB for 2,000 keyframes). */
 pgo_status pgo_graph_create(const pgo_graph_desc* desc, pgo_graph** out);
 
 /* Release every resource of a graph (NULL is ignored).  Synchronises the
