@@ -1,7 +1,8 @@
 """Host logic of bench.py without a GPU: the job time as the maximum over
 ranks with two gloo processes on the CPU (the N > 1 replicas path), the
-whole-job aggregation of replicas, the kernel-launch count of a solve and
-the algorithmic bytes of one multigrid PCG iteration."""
+whole-job aggregation of replicas, the kernel-launch count of a solve, the
+algorithmic bytes of one multigrid PCG iteration and the pose-error summary
+against the oracle."""
 import os
 import socket
 import sys
@@ -76,3 +77,30 @@ def test_vcycle_bytes_per_iteration_counts_each_operator_read():
     assert bench.vcycle_pcg_bytes_per_iter([lv0, crs], N, E, 4) == (2 * (E + N) + 2 * N + N * N) * blk + 18 * N * vec
     # FP64 doubles every byte
     assert bench.vcycle_pcg_bytes_per_iter([lv0, lv1, lv2, crs], N, E, 8) == 2 * want
+
+
+def test_pose_error_summary_is_the_rotation_angle():
+    """The bench's pose error per vertex is |log(S_gpu S_oracle^-1)|: a pose
+    against itself gives 0, a pose turned by a known angle about an axis gives
+    that angle (the rotation part of the Sim(3) log), a scale change s gives
+    |ln s|."""
+    import numpy as np
+
+    import bench
+
+    ref = np.array([[0.0, 0.0, 0.0, 1.0, 1.0, 2.0, 3.0, 1.0]] * 3)
+    assert bench.pose_error_summary(ref, ref)["max"] < 1e-15
+    turned = ref.copy()
+    ang = [0.0, 0.1, 0.3]
+    for v, a in enumerate(ang):
+        # left-multiply by a rotation of angle a about z: q = (0, 0, sin(a/2), cos(a/2))
+        qz = np.array([0.0, 0.0, np.sin(a / 2), np.cos(a / 2)])
+        turned[v, :4] = qz
+        turned[v, 4:7] = [np.cos(a) * 1.0 - np.sin(a) * 2.0, np.sin(a) * 1.0 + np.cos(a) * 2.0, 3.0]
+    e = bench.pose_error_summary(turned, ref)
+    assert abs(e["max"] - 0.3) < 1e-12
+    assert abs(e["rms"] - np.sqrt((0.1 ** 2 + 0.3 ** 2) / 3)) < 1e-12
+    scaled = ref.copy()
+    scaled[:, 4:7] *= 2.0
+    scaled[:, 7] = 2.0
+    assert abs(bench.pose_error_summary(scaled, ref)["max"] - np.log(2.0)) < 1e-12
