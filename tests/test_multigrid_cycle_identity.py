@@ -8,8 +8,10 @@ with Q_l = (I - w_l D_l^-1 A_l) P_l, and on the level next to the coarsest
 z = f + W r with W = Q C^-1 Q^T.  These tests pin that this is the same
 operator as the cycle in its textbook order (pre-smoothing, residual,
 restriction, coarse solve, prolongation, post-smoothing), that it is
-symmetric positive definite, and that the set-up's Q, taken in the pattern
-of A P, agrees with (I - w D^-1 A) P.
+symmetric positive definite, that the set-up's Q, taken in the pattern of
+A P, agrees with (I - w D^-1 A) P, and that one cycle applied to a residual
+(the one-cycle correction pass of the mixed refinement) never increases the
+error's A-norm.
 """
 import numpy as np
 import pytest
@@ -114,3 +116,23 @@ def test_q_in_the_pattern_of_a_p():
                 assert not np.any(P[0][blk]) and not np.any(Q[blk])
             Du = Dinv[0][7 * u:7 * u + 7, 7 * u:7 * u + 7]
             assert np.allclose(Q[blk], P[0][blk] - w[0] * Du @ AP[blk], rtol=1e-12, atol=1e-12 * np.abs(Q).max())
+
+
+@pytest.mark.parametrize("n0,levels", [(40, 1), (40, 2), (64, 3)])
+def test_one_cycle_correction_contracts(n0, levels):
+    """The mixed refinement's correction pass may apply one cycle, x = B r,
+    to its residual (a preconditioned Richardson step).  The error after it
+    is (I - B A) e, and with the symmetric cycle every eigenvalue of B A lies
+    in (0, 1]: the step never increases the A-norm of the error, and it
+    shrinks it by the factor 1 - lambda_min(B A) < 1."""
+    rng = np.random.default_rng(100 + n0 + levels)
+    A, Dinv, w, P = _hierarchy(n0, levels, rng)
+    m = 7 * n0
+    B = np.column_stack([_cycle_one_map(A, Dinv, w, P, e) for e in np.eye(m)])
+    lam = np.sort(np.linalg.eigvals(B @ A[0]).real)
+    assert lam[0] > 0.0 and lam[-1] <= 1.0 + 1e-9
+    # the same on a residual: the A-norm of the error drops after x = B r
+    e = rng.standard_normal(m)
+    r = A[0] @ e
+    e1 = e - B @ r
+    assert e1 @ A[0] @ e1 <= (1.0 - lam[0]) ** 2 * (e @ A[0] @ e) * (1 + 1e-9)
