@@ -674,6 +674,37 @@ struct AmgPlan {
 
 void amg_plan_free(AmgPlan* P) { delete P; }
 
+// One integer array of level `level` of an analysed plan, for the host tests:
+// 0 the node count of every level (level ignored), 1 aggregates, 2 / 3 the
+// CSR of P's pattern, 4 / 5 the CSR of A P's pattern, 6 / 7 the CSR of the
+// level's operator pattern (levels >= 1).  Returns the length and points
+// *data at the values (valid while the plan lives; the node counts until the
+// next call on this thread), or -1 for a level or array that does not exist.
+long long amg_plan_array(const AmgPlan* P, int level, int what, const int** data) {
+  static thread_local std::vector<int> counts;
+  if (what == 0) {
+    counts.clear();
+    for (const HostLevel& h : P->H) counts.push_back(h.n);
+    *data = counts.data();
+    return (long long)counts.size();
+  }
+  if (level < 0 || level >= (int)P->H.size()) return -1;
+  const HostLevel& h = P->H[level];
+  const std::vector<int>* v = nullptr;
+  switch (what) {
+    case 1: v = &h.agg; break;
+    case 2: v = &h.p_ptr; break;
+    case 3: v = &h.p_col; break;
+    case 4: v = &h.ap_ptr; break;
+    case 5: v = &h.ap_col; break;
+    case 6: v = &h.a_ptr; break;
+    case 7: v = &h.a_col; break;
+    default: return -1;
+  }
+  *data = v->data();
+  return (long long)v->size();
+}
+
 AmgPlan* amg_analyze(int N, int nseg, const int* seg_v0, const int* seg_nv, const int* seg_fixed, const int* inc_ptr,
                      const int* inc_code, const int* inc_other, const char** err) {
   *err = nullptr;

@@ -594,6 +594,66 @@ pgo_status pgo_default_options(pgo_solve_options* opt) {
   return PGO_OK;
 }
 
+// The internal edge order, by (min endpoint, max endpoint, caller index), as
+// two stable counting sorts (by the max endpoint, then by the min), and the
+// incidence lists over it: for each vertex its side-0 entries (vertex is i),
+// then its side-1 entries (vertex is j), each group in edge order.  The
+// endpoints must be in range.
+struct EdgeOrder {
+  std::vector<int> perm, sei, sej, inc_ptr, inc_split, inc_code, inc_other;
+};
+
+static void order_edges(int N, int E, const int32_t* ei, const int32_t* ej, EdgeOrder& o) {
+  std::vector<int>& perm = o.perm;
+  perm.resize(E);
+  {
+    std::vector<int> tmp(E), cnt((size_t)N + 1);
+    auto pass = [&](const std::vector<int>& src, std::vector<int>& dst, bool by_min) {
+      std::fill(cnt.begin(), cnt.end(), 0);
+      auto key = [&](int e) { return by_min ? std::min(ei[e], ej[e]) : std::max(ei[e], ej[e]); };
+      for (int k = 0; k < E; ++k) cnt[key(src[k]) + 1]++;
+      for (int v = 0; v < N; ++v) cnt[v + 1] += cnt[v];
+      for (int k = 0; k < E; ++k) dst[cnt[key(src[k])]++] = src[k];
+    };
+    std::iota(perm.begin(), perm.end(), 0);
+    pass(perm, tmp, false);
+    pass(tmp, perm, true);
+  }
+  std::vector<int>& sei = o.sei;
+  std::vector<int>& sej = o.sej;
+  sei.resize(E);
+  sej.resize(E);
+  for (int k = 0; k < E; ++k) {
+    sei[k] = ei[perm[k]];
+    sej[k] = ej[perm[k]];
+  }
+  o.inc_ptr.assign(N + 1, 0);
+  o.inc_split.resize(N);
+  o.inc_code.resize((size_t)2 * E);
+  o.inc_other.resize((size_t)2 * E);
+  std::vector<int>& inc_ptr = o.inc_ptr;
+  std::vector<int> deg0(N, 0);
+  for (int k = 0; k < E; ++k) {
+    inc_ptr[sei[k] + 1]++;
+    inc_ptr[sej[k] + 1]++;
+    deg0[sei[k]]++;
+  }
+  for (int v = 0; v < N; ++v) inc_ptr[v + 1] += inc_ptr[v];
+  std::vector<int> fill0(N), fill1(N);
+  for (int v = 0; v < N; ++v) {
+    fill0[v] = inc_ptr[v];
+    o.inc_split[v] = fill1[v] = inc_ptr[v] + deg0[v];
+  }
+  for (int k = 0; k < E; ++k) {
+    const int a = fill0[sei[k]]++;
+    o.inc_code[a] = 2 * k;
+    o.inc_other[a] = sej[k];
+    const int b2 = fill1[sej[k]]++;
+    o.inc_code[b2] = 2 * k + 1;
+    o.inc_other[b2] = sei[k];
+  }
+}
+
 static pgo_status graph_create(const pgo_graph_desc* d, pgo_graph** out, bool analyse_early) {
   if (!out) return fail(PGO_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
@@ -624,59 +684,19 @@ static pgo_status graph_create(const pgo_graph_desc* d, pgo_graph** out, bool an
     if (ei[e] == ej[e]) return fail(PGO_ERR_INVALID_ARG, "edge %d is a self-edge (%d, %d)", e, ei[e], ej[e]);
   }
 
-  // internal edge order: by (min endpoint, max endpoint, caller index), as
-  // two stable counting sorts (by the max endpoint, then by the min)
-  std::vector<int> perm(E);
-  {
-    std::vector<int> tmp(E), cnt((size_t)N + 1);
-    auto pass = [&](const std::vector<int>& src, std::vector<int>& dst, bool by_min) {
-      std::fill(cnt.begin(), cnt.end(), 0);
-      auto key = [&](int e) { return by_min ? std::min(ei[e], ej[e]) : std::max(ei[e], ej[e]); };
-      for (int k = 0; k < E; ++k) cnt[key(src[k]) + 1]++;
-      for (int v = 0; v < N; ++v) cnt[v + 1] += cnt[v];
-      for (int k = 0; k < E; ++k) dst[cnt[key(src[k])]++] = src[k];
-    };
-    std::iota(perm.begin(), perm.end(), 0);
-    pass(perm, tmp, false);
-    pass(tmp, perm, true);
-  }
-  std::vector<int> sei(E), sej(E);
-  for (int k = 0; k < E; ++k) {
-    sei[k] = ei[perm[k]];
-    sej[k] = ej[perm[k]];
-  }
-  // incidence lists: for each vertex its side-0 entries (vertex is i), then
-  // its side-1 entries (vertex is j), each group in edge order
-  std::vector<int> inc_ptr(N + 1, 0), inc_split(N), inc_code((size_t)2 * E), inc_other((size_t)2 * E);
-  std::vector<int> deg0(N, 0);
-  for (int k = 0; k < E; ++k) {
-    inc_ptr[sei[k] + 1]++;
-    inc_ptr[sej[k] + 1]++;
-    deg0[sei[k]]++;
-  }
-  for (int v = 0; v < N; ++v) inc_ptr[v + 1] += inc_ptr[v];
-  {
-    std::vector<int> fill0(N), fill1(N);
-    for (int v = 0; v < N; ++v) {
-      fill0[v] = inc_ptr[v];
-      inc_split[v] = fill1[v] = inc_ptr[v] + deg0[v];
-    }
-    for (int k = 0; k < E; ++k) {
-      const int a = fill0[sei[k]]++;
-      inc_code[a] = 2 * k;
-      inc_other[a] = sej[k];
-      const int b2 = fill1[sej[k]]++;
-      inc_code[b2] = 2 * k + 1;
-      inc_other[b2] = sei[k];
-    }
-  }
+  EdgeOrder eo;
+  order_edges(N, E, ei.data(), ej.data(), eo);
+  const std::vector<int>& perm = eo.perm;
+  const std::vector<int>& sei = eo.sei;
+  const std::vector<int>& sej = eo.sej;
+  const std::vector<int>& inc_split = eo.inc_split;
 
   pgo_graph* G = new pgo_graph();
   G->N = N;
   G->E = E;
-  G->h_inc_ptr = inc_ptr;
-  G->h_inc_code = inc_code;
-  G->h_inc_other = inc_other;
+  G->h_inc_ptr = std::move(eo.inc_ptr);
+  G->h_inc_code = std::move(eo.inc_code);
+  G->h_inc_other = std::move(eo.inc_other);
   if (analyse_early && N >= 2) {
     // the multigrid analysis (the default preconditioner) runs beside the
     // allocations and uploads below and whatever the caller does before its
@@ -826,10 +846,10 @@ static pgo_status graph_create(const pgo_graph_desc* d, pgo_graph** out, bool an
   ok &= copy_in(d_w, sw.data(), sizeof(double) * E, PGO_MEM_HOST, s);
   ok &= copy_in(d_zqn, szqn.data(), sizeof(double) * E, PGO_MEM_HOST, s);
   if (d->info) ok &= copy_in(d_L, sL.data(), sizeof(double) * 28 * E, PGO_MEM_HOST, s);
-  ok &= copy_in(d_ptr, inc_ptr.data(), sizeof(int) * (N + 1), PGO_MEM_HOST, s);
+  ok &= copy_in(d_ptr, G->h_inc_ptr.data(), sizeof(int) * (N + 1), PGO_MEM_HOST, s);
   ok &= copy_in(d_split, inc_split.data(), sizeof(int) * N, PGO_MEM_HOST, s);
-  ok &= copy_in(d_code, inc_code.data(), sizeof(int) * 2 * E, PGO_MEM_HOST, s);
-  ok &= copy_in(d_other, inc_other.data(), sizeof(int) * 2 * E, PGO_MEM_HOST, s);
+  ok &= copy_in(d_code, G->h_inc_code.data(), sizeof(int) * 2 * E, PGO_MEM_HOST, s);
+  ok &= copy_in(d_other, G->h_inc_other.data(), sizeof(int) * 2 * E, PGO_MEM_HOST, s);
   ok &= copy_in(G->d_perm, perm.data(), sizeof(int) * E, PGO_MEM_HOST, s);
   if (!ok) return cleanup(fail(PGO_ERR_CUDA, "uploading the graph failed"));
   // identity poses by default, then the caller's initial estimate
@@ -853,6 +873,42 @@ static pgo_status graph_create(const pgo_graph_desc* d, pgo_graph** out, bool an
 }
 
 pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) { return graph_create(d, out, true); }
+
+// Test hook (not in the public header; no device needed): the host analysis
+// of the multigrid hierarchy for a graph given by its edge list, over the
+// edge order and incidence lists graph creation builds, and one integer
+// array of one level of the plan (what: 0 the node count of every level,
+// 1 aggregates, 2 / 3 the CSR of P's pattern, 4 / 5 of A P's, 6 / 7 of the
+// level's operator pattern).  out == NULL: *count receives the length;
+// otherwise at most *count values are copied and *count receives the length.
+pgo_status pgo_test_multigrid_plan(int32_t n_vertices, int32_t n_edges, const int32_t* edge_i,
+                                   const int32_t* edge_j, int32_t fixed_vertex, int32_t level, int32_t what,
+                                   int32_t* out, int64_t* count) {
+  if (!count) return fail(PGO_ERR_INVALID_ARG, "count is NULL");
+  const int N = n_vertices, E = n_edges;
+  if (N < 2 || E < 0 || (E > 0 && (!edge_i || !edge_j)) || fixed_vertex < 0 || fixed_vertex >= N)
+    return fail(PGO_ERR_INVALID_ARG, "bad graph description");
+  for (int e = 0; e < E; ++e)
+    if (edge_i[e] < 0 || edge_i[e] >= N || edge_j[e] < 0 || edge_j[e] >= N || edge_i[e] == edge_j[e])
+      return fail(PGO_ERR_INVALID_ARG, "edge %d: endpoint out of range or a self-edge", e);
+  EdgeOrder eo;
+  order_edges(N, E, edge_i, edge_j, eo);
+  const char* err = nullptr;
+  const int v0 = 0, nv = N, fx = fixed_vertex;
+  AmgPlan* P = amg_analyze(N, 1, &v0, &nv, &fx, eo.inc_ptr.data(), eo.inc_code.data(), eo.inc_other.data(), &err);
+  if (!P) return fail(PGO_ERR_INVALID_ARG, "multigrid analysis: %s", err ? err : "failed");
+  const int* data = nullptr;
+  const long long n = amg_plan_array(P, level, what, &data);
+  pgo_status st = PGO_OK;
+  if (n < 0) {
+    st = fail(PGO_ERR_INVALID_ARG, "no array %d at level %d", what, level);
+  } else {
+    if (out) std::memcpy(out, data, sizeof(int32_t) * (size_t)std::max<long long>(0, std::min<long long>(n, *count)));
+    *count = n;
+  }
+  amg_plan_free(P);
+  return st;
+}
 
 void pgo_graph_destroy(pgo_graph* G) {
   if (!G) return;

@@ -279,6 +279,7 @@ AmgPlan* amg_analyze(int N, int nseg, const int* seg_v0, const int* seg_nv, cons
                      const int* inc_code, const int* inc_other, const char** err);
 AmgHost* amg_upload(AmgPlan* P, cudaStream_t s, const char** err);
 void amg_plan_free(AmgPlan* P);
+long long amg_plan_array(const AmgPlan* P, int level, int what, const int** data);
 AmgHost* amg_build(int N, int nseg, const int* seg_v0, const int* seg_nv, const int* seg_fixed, const int* inc_ptr,
                    const int* inc_code, const int* inc_other, cudaStream_t s, const char** err);
 void amg_free(AmgHost* h);
