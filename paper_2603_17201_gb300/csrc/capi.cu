@@ -879,8 +879,11 @@ pgo_status pgo_graph_create(const pgo_graph_desc* d, pgo_graph** out) { return g
 // edge order and incidence lists graph creation builds, and one integer
 // array of one level of the plan (what: 0 the node count of every level,
 // 1 aggregates, 2 / 3 the CSR of P's pattern, 4 / 5 of A P's, 6 / 7 of the
-// level's operator pattern).  out == NULL: *count receives the length;
-// otherwise at most *count values are copied and *count receives the length.
+// level's operator pattern), or of the graph's edge order (what: 8 the
+// caller's index of each internal edge, 9 inc_ptr, 10 inc_split, 11
+// inc_code, 12 inc_other; level ignored).  out == NULL: *count receives the
+// length; otherwise at most *count values are copied and *count receives the
+// length.
 pgo_status pgo_test_multigrid_plan(int32_t n_vertices, int32_t n_edges, const int32_t* edge_i,
                                    const int32_t* edge_j, int32_t fixed_vertex, int32_t level, int32_t what,
                                    int32_t* out, int64_t* count) {
@@ -893,6 +896,20 @@ pgo_status pgo_test_multigrid_plan(int32_t n_vertices, int32_t n_edges, const in
       return fail(PGO_ERR_INVALID_ARG, "edge %d: endpoint out of range or a self-edge", e);
   EdgeOrder eo;
   order_edges(N, E, edge_i, edge_j, eo);
+  auto give = [&](const std::vector<int>& v) {
+    const long long n = std::max<long long>(0, std::min<long long>((long long)v.size(), *count));
+    if (out) std::memcpy(out, v.data(), sizeof(int32_t) * (size_t)n);
+    *count = (int64_t)v.size();
+    return PGO_OK;
+  };
+  switch (what) {
+    case 8: return give(eo.perm);
+    case 9: return give(eo.inc_ptr);
+    case 10: return give(eo.inc_split);
+    case 11: return give(eo.inc_code);
+    case 12: return give(eo.inc_other);
+    default: break;
+  }
   const char* err = nullptr;
   const int v0 = 0, nv = N, fx = fixed_vertex;
   AmgPlan* P = amg_analyze(N, 1, &v0, &nv, &fx, eo.inc_ptr.data(), eo.inc_code.data(), eo.inc_other.data(), &err);

@@ -1,6 +1,7 @@
-"""Host logic of the multigrid hierarchy, without a GPU: the library's host
-analysis (through a test hook of the C library) against a plain Python
-construction of the same patterns from their definitions.
+"""Host logic of graph creation and of the multigrid hierarchy, without a
+GPU: the library's internal edge order, incidence lists and host analysis
+(through a test hook of the C library) against a plain Python construction
+of the same arrays from their definitions.
 
   - level 0: the vertices; aggregates of 4 consecutive free vertices (the
     gauge vertex has none); level l + 1: one node per aggregate, 4 consecutive
@@ -125,3 +126,34 @@ def test_hook_rejects_bad_input(lib):
     ej[1] = 2
     st = lib.pgo_test_multigrid_plan(4, 2, ei.ctypes.data, ej.ctypes.data, 0, 9, AGG, None, ctypes.byref(cnt))
     assert st == L.PGO_ERR_INVALID_ARG   # no level 9
+
+
+PERM, INC_PTR, INC_SPLIT, INC_CODE, INC_OTHER = range(8, 13)
+
+
+@pytest.mark.parametrize("case", graphs(), ids=lambda c: c[0])
+def test_edge_order_and_incidence(lib, case):
+    """Graph creation's internal edge order is by (min endpoint, max endpoint,
+    caller index); each vertex lists the edges where it is i (side 0), then
+    those where it is j (side 1), each group in internal edge order, as codes
+    2 k + side with the other endpoint beside them."""
+    _, n, ei, ej, fixed = case
+    ei, ej = np.asarray(ei, np.int64), np.asarray(ej, np.int64)
+    E = len(ei)
+    order = sorted(range(E), key=lambda e: (min(ei[e], ej[e]), max(ei[e], ej[e]), e))
+    assert list(plan_array(lib, n, ei, ej, fixed, 0, PERM)) == order
+    rows = [([], []) for _ in range(n)]
+    for k, e in enumerate(order):
+        rows[ei[e]][0].append((2 * k, ej[e]))
+        rows[ej[e]][1].append((2 * k + 1, ei[e]))
+    ptr, split, code, other = [0], [], [], []
+    for side0, side1 in rows:
+        split.append(ptr[-1] + len(side0))
+        for c, o in side0 + side1:
+            code.append(c)
+            other.append(o)
+        ptr.append(len(code))
+    assert list(plan_array(lib, n, ei, ej, fixed, 0, INC_PTR)) == ptr
+    assert list(plan_array(lib, n, ei, ej, fixed, 0, INC_SPLIT)) == split
+    assert list(plan_array(lib, n, ei, ej, fixed, 0, INC_CODE)) == code
+    assert list(plan_array(lib, n, ei, ej, fixed, 0, INC_OTHER)) == other
